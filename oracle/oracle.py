@@ -1,0 +1,206 @@
+"""ctypes wrapper around the FP64 CPU oracle (lbsc_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Callers: the test suite, the package smoke check
+and the benchmark's CPU-baseline leg.  No product code imports this module.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("G", C.c_double), ("tau", C.c_double), ("kT", C.c_double),
+        ("psi_kind", C.c_int), ("psi_p1", C.c_double), ("psi_p2", C.c_double),
+        ("stencil", C.c_int),
+        ("rho0", C.c_double),
+        ("seed", C.c_uint64),
+        ("replica", C.c_uint32),
+    ]
+
+
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_I = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+_U64 = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    """Load (building if needed) the oracle library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.or_philox4x32_10.argtypes = [_U32, _U32, _U32]
+        L.or_philox4x64_10.argtypes = [_U64, _U64, _U64]
+        L.or_psi.argtypes = [C.POINTER(OrParams), C.c_double]
+        L.or_psi.restype = C.c_double
+        L.or_create.argtypes = [C.POINTER(OrParams)]
+        L.or_create.restype = C.c_void_p
+        L.or_destroy.argtypes = [C.c_void_p]
+        L.or_init.argtypes = [C.c_void_p, C.c_double, C.c_uint64, C.c_double]
+        L.or_set_replica.argtypes = [C.c_void_p, C.c_uint32]
+        L.or_set_step.argtypes = [C.c_void_p, C.c_longlong]
+        L.or_get_step.argtypes = [C.c_void_p]
+        L.or_get_step.restype = C.c_longlong
+        L.or_set_density.argtypes = [C.c_void_p, _D]
+        L.or_set_populations.argtypes = [C.c_void_p, _D]
+        L.or_get_populations.argtypes = [C.c_void_p, _D]
+        L.or_density.argtypes = [C.c_void_p, _D]
+        L.or_conserved.argtypes = [C.c_void_p, _D]
+        L.or_force_field.argtypes = [C.c_void_p, _D, _D]
+        L.or_sk_config.argtypes = [C.c_void_p, C.c_int, C.c_longlong]
+        L.or_sk_reset.argtypes = [C.c_void_p]
+        L.or_sk_sample_now.argtypes = [C.c_void_p]
+        L.or_sk_get.argtypes = [C.c_void_p, _D]
+        L.or_sk_get.restype = C.c_longlong
+        L.or_step.argtypes = [C.c_void_p, C.c_int]
+        L.or_step.restype = C.c_int
+        L.or_step_sites.argtypes = [C.POINTER(OrParams), C.c_longlong, _D, C.c_int,
+                                    _I, _I, _D]
+        L.or_step_sites.restype = C.c_int
+        L.or_lattice_constants.argtypes = [_I, _I, _D, C.POINTER(C.c_double)]
+        L.or_moment_basis.argtypes = [_D, _D]
+        L.or_stencil.argtypes = [C.c_int, _I, _I, _D]
+        L.or_stencil.restype = C.c_int
+        L.or_normals.argtypes = [C.POINTER(OrParams), C.c_uint32, C.c_uint32, _D]
+        _lib = L
+    return _lib
+
+
+def philox4x32(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def philox4x64(ctr, key):
+    out = np.zeros(4, np.uint64)
+    lib().or_philox4x64_10(np.asarray(ctr, np.uint64), np.asarray(key, np.uint64), out)
+    return out
+
+
+def lattice_constants():
+    cx = np.zeros(9, np.int32); cy = np.zeros(9, np.int32); w = np.zeros(9)
+    cs2 = C.c_double()
+    lib().or_lattice_constants(cx, cy, w, C.byref(cs2))
+    return cx, cy, w, cs2.value
+
+
+def moment_basis():
+    m = np.zeros(81); b = np.zeros(9)
+    lib().or_moment_basis(m, b)
+    return m.reshape(9, 9), b
+
+
+def stencil(order):
+    ex = np.zeros(32, np.int32); ey = np.zeros(32, np.int32); w = np.zeros(32)
+    n = lib().or_stencil(order, ex, ey, w)
+    return ex[:n].copy(), ey[:n].copy(), w[:n].copy()
+
+
+def make_params(nx, ny, G, tau, kT, psi_kind=0, psi_p1=0.0, psi_p2=0.0, stencil=4,
+                rho0=0.0, seed=0, replica=0):
+    return OrParams(nx, ny, G, tau, kT, psi_kind, psi_p1, psi_p2, stencil, rho0,
+                    seed, replica)
+
+
+class OracleLattice:
+    """One periodic nx x ny lattice held by the FP64 oracle."""
+
+    def __init__(self, nx, ny, G, tau, kT, psi_kind=0, stencil=4, psi_p1=0.0,
+                 psi_p2=0.0, replica=0):
+        self.p = make_params(nx, ny, G, tau, kT, psi_kind, psi_p1, psi_p2, stencil,
+                             replica=replica)
+        self.nx, self.ny = nx, ny
+        self._h = lib().or_create(C.byref(self.p))
+        if not self._h:
+            raise ValueError("oracle: invalid parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_destroy(h)
+            self._h = None
+
+    def init(self, rho0, seed=0, init_amp=0.0):
+        self.p.rho0 = rho0
+        self.p.seed = seed
+        lib().or_init(self._h, rho0, seed, init_amp)
+
+    def set_step(self, t):
+        lib().or_set_step(self._h, t)
+
+    @property
+    def t(self):
+        return lib().or_get_step(self._h)
+
+    def set_density(self, rho):
+        lib().or_set_density(self._h, np.ascontiguousarray(rho, np.float64).ravel())
+
+    def set_populations(self, f):
+        lib().or_set_populations(self._h, np.ascontiguousarray(f, np.float64).ravel())
+
+    def populations(self):
+        f = np.zeros(9 * self.nx * self.ny)
+        lib().or_get_populations(self._h, f)
+        return f.reshape(9, self.ny, self.nx)
+
+    def density(self):
+        r = np.zeros(self.nx * self.ny)
+        lib().or_density(self._h, r)
+        return r.reshape(self.ny, self.nx)
+
+    def conserved(self):
+        out = np.zeros(3)
+        lib().or_conserved(self._h, out)
+        return out
+
+    def force(self):
+        fx = np.zeros(self.nx * self.ny); fy = np.zeros(self.nx * self.ny)
+        lib().or_force_field(self._h, fx, fy)
+        return fx.reshape(self.ny, self.nx), fy.reshape(self.ny, self.nx)
+
+    def step(self, n=1):
+        lib().or_step(self._h, int(n))
+
+    def sk_config(self, every, start):
+        lib().or_sk_config(self._h, int(every), int(start))
+
+    def sk_reset(self):
+        lib().or_sk_reset(self._h)
+
+    def sk_sample_now(self):
+        lib().or_sk_sample_now(self._h)
+
+    def structure_factor(self):
+        """Mean S(k) over the samples on the half plane [ny][nx/2+1]."""
+        out = np.zeros((self.nx // 2 + 1) * self.ny)
+        n = lib().or_sk_get(self._h, out)
+        return out.reshape(self.ny, self.nx // 2 + 1), n
+
+
+def step_sites(params, t, f_full, xs, ys):
+    """One oracle step evaluated at the sites (xs[i], ys[i]) of a full-lattice
+    input state f_full ([9][ny][nx], full populations). Returns [n][9]."""
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    out = np.zeros(9 * len(xs))
+    rc = lib().or_step_sites(C.byref(params), int(t),
+                             np.ascontiguousarray(f_full, np.float64).ravel(),
+                             len(xs), xs, ys, out)
+    if rc != 0:
+        raise ValueError("oracle: site out of range")
+    return out.reshape(len(xs), 9)
+
+
+def normals(params, site, t):
+    z = np.zeros(6)
+    lib().or_normals(C.byref(params), site, t, z)
+    return z

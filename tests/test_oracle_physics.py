@@ -1,0 +1,166 @@
+"""Physics pins of the FP64 oracle: what the paper fixes about the model.
+
+- Eq. (14): the lattice normal pressure P_N(x) is constant across a flat
+  interface at mechanical equilibrium, to machine precision.
+- Bulk coexistence: the two bulk phases of that slab sit at equal EoS
+  pressure (Eq. (2)), outside the spinodal interval.
+- Laplace law for droplets (Delta p ~ sigma / R, vanishing for R -> infinity).
+- Eq. (16): the static structure factor S(k) = n0 kT / c_s^2(k) on lattice
+  axes, for a supercritical and a metastable state, both pseudopotential
+  forms, E4 and E8; and S(k) = rho0 kT / c_s^2 flat in k for G = 0
+  (fluctuation-dissipation check of the noise amplitude).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import theory as T
+from paper_2212_07848_gb300 import inputs
+
+LN2 = float(np.log(2.0))
+
+
+def _relax(o, chunk, tol, max_chunks):
+    prev = o.density()
+    for _ in range(max_chunks):
+        o.step(chunk)
+        d = o.density()
+        ch = np.abs(d - prev).max()
+        prev = d
+        if ch < tol:
+            return d, ch
+    return d, ch
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_flat_interface_normal_pressure_is_constant(tau):
+    """Eq. (14) on a converged slab at G = -5 (T_hat = 0.8).  The side is odd
+    so the lattice carries no k = pi momentum mode (with an even side that
+    undamped checkerboard mode can survive the transient and add O(u^2)
+    terms)."""
+    G = -5.0
+    nx, ny = 65, 4
+    rg, rl = T.coexistence(G, eps=0.0)
+    o = O.OracleLattice(nx, ny, G=G, tau=tau, kT=0.0)
+    o.init(LN2)
+    o.set_density(inputs.slab_density(nx, ny, rg, rl, 32, smooth=1.5))
+    spread = []
+    for _ in range(40):
+        o.step(1000)
+        d = o.density()
+        pn = T.pn_lattice(d[0], G)
+        spread.append((pn.max() - pn.min()) / abs(pn.mean()))
+        if spread[-1] < 1e-13:
+            break
+    assert np.abs(d - d[0]).max() == 0.0            # flat in y
+    assert spread[-1] < 1e-13, spread[-5:]
+    # interface really present: density contrast across the slab
+    assert d[0].max() - d[0].min() > 1.5
+    # bulk coexistence: both bulk phases at the same EoS pressure (to the
+    # uniformity a 16-site bulk reaches), outside the spinodal interval, and
+    # between the eps = 0 and eps = 1 integral rules
+    rho_g, rho_l = d[0][0], d[0][nx // 2]
+    pg, pl = T.pressure(rho_g, G), T.pressure(rho_l, G)
+    assert abs(pl - pg) / abs(pg) < 1e-7
+    sg, sl = T.spinodal(G)
+    assert rho_g < sg and rho_l > sl
+    rg1, rl1 = T.coexistence(G, eps=1.0)
+    assert min(rg, rg1) - 1e-3 < rho_g < max(rg, rg1) + 1e-3
+    assert min(rl, rl1) - 1e-3 < rho_l < max(rl, rl1) + 1e-3
+
+
+def test_laplace_law():
+    G, L = -5.0, 95
+    rg, rl = T.coexistence(G, eps=0.0)
+    R_eq, dp = [], []
+    for R in (10, 14, 18, 22):
+        o = O.OracleLattice(L, L, G=G, tau=1.0, kT=0.0)
+        o.init(LN2)
+        o.set_density(inputs.droplet_density(L, L, R, rl, rg, smooth=1.5))
+        d, ch = _relax(o, 250, 1e-11, 60)
+        rin, rout = d[L // 2, L // 2], d[0, 0]
+        R_eq.append(np.sqrt((d - rout).sum() / (rin - rout) / np.pi))   # equimolar radius
+        dp.append(T.pressure(rin, G) - T.pressure(rout, G))
+    R_eq, dp = np.array(R_eq), np.array(dp)
+    A = np.vstack([1 / R_eq, np.ones_like(R_eq)]).T
+    coef = np.linalg.lstsq(A, dp, rcond=None)[0]
+    pred = A @ coef
+    r2 = 1 - ((dp - pred) ** 2).sum() / ((dp - dp.mean()) ** 2).sum()
+    assert r2 > 0.999 and coef[0] > 0
+    # with the first curvature correction the flat-interface limit is Delta p = 0
+    A2 = np.vstack([1 / R_eq, 1 / R_eq ** 2, np.ones_like(R_eq)]).T
+    c2 = np.linalg.lstsq(A2, dp, rcond=None)[0]
+    assert abs(c2[2]) < 0.01 * dp.min()
+
+
+def _sk_batches(o, steps, every, nb):
+    out = []
+    per = steps // nb
+    for _ in range(nb):
+        o.sk_reset()
+        o.sk_config(every, o.t + every)
+        o.step(per)
+        S, n = o.structure_factor()
+        assert n == per // every
+        out.append(S)
+    return np.array(out)
+
+
+def test_ideal_gas_structure_factor_is_flat():
+    """G = 0: S(k) = rho0 kT / c_s^2 for every k (the noise amplitude obeys
+    fluctuation-dissipation at every wavelength)."""
+    L, rho0, kT = 32, LN2, 1e-4
+    o = O.OracleLattice(L, L, G=0.0, tau=0.8, kT=kT)
+    o.init(rho0, seed=7)
+    o.step(500)
+    B = _sk_batches(o, 6000, 2, 10)
+    ref = rho0 * kT * 3.0
+    S = B.mean(0) / ref
+    S[0, 0] = np.nan
+    assert abs(np.nanmean(S) - 1.0) < 0.01
+    ky = np.fft.fftfreq(L) * L
+    kk = np.hypot(*np.meshgrid(np.arange(L // 2 + 1), ky))
+    for lo, hi in [(0.5, 5), (5, 10), (10, 30)]:
+        sel = (kk >= lo) & (kk < hi)
+        assert abs(np.nanmean(S[sel]) - 1.0) < 0.03
+
+
+SK_CASES = [
+    # (G, rho0, kT, stencil, psi_kind, p1, p2): supercritical (T_hat = 1.11)
+    (-3.6, LN2, 1e-5, 4, 0, 0.0, 0.0),
+    # metastable gas branch at T_hat = 0.889 (between coexistence and spinodal)
+    (-4.5, 0.33, 1e-6, 4, 0, 0.0, 0.0),
+    # supercritical with the longer-range E8 stencil
+    (-3.6, LN2, 1e-5, 8, 0, 0.0, 0.0),
+    # the paper's critical-scaled psi, Eq. (5), with G = -1/c_s^2 so p is
+    # Eq. (6) at T = 1/3; T_c chosen for T_hat = 0.8, metastable liquid
+    (-3.0, 1.9, 1e-6, 4, 1, 1.0 / 3.0 / 0.8, 1.0),
+]
+
+
+@pytest.mark.parametrize("G,rho0,kT,stencil,kind,p1,p2", SK_CASES)
+def test_structure_factor_matches_exact_theory_on_axes(G, rho0, kT, stencil, kind, p1, p2):
+    L, nb = 32, 10
+    if kind == 1:
+        sg, sl = T.spinodal(G, kind, p1, p2)
+        assert rho0 > sl                             # liquid side, stable to small noise
+        assert T.dpressure(rho0, G, kind, p1, p2) > 0
+    o = O.OracleLattice(L, L, G=G, tau=1.0, kT=kT, stencil=stencil, psi_kind=kind,
+                        psi_p1=p1, psi_p2=p2)
+    o.init(rho0, seed=7)
+    o.step(2000)
+    B = _sk_batches(o, 30000, 5, nb)
+    z, ratios = [], []
+    for m in range(2, L // 2 + 1):
+        vals = (B[:, 0, m] + B[:, m, 0]) / 2.0       # (m, 0) and (0, m)
+        th = T.sk_axis(2 * np.pi * m / L, rho0, G, kT, stencil, kind, p1, p2)
+        err = vals.std(ddof=1) / np.sqrt(nb)
+        ratios.append(vals.mean() / th)
+        z.append((vals.mean() - th) / err)
+    z, ratios = np.array(z), np.array(ratios)
+    assert np.all(np.abs(z) < 5.0)
+    assert abs(ratios.mean() - 1.0) < 0.01
+    # the pin has power: the theory differs from the ideal gas by far more
+    ideal = rho0 * kT * 3.0
+    th_low = T.sk_axis(2 * np.pi * 2 / L, rho0, G, kT, stencil, kind, p1, p2)
+    assert abs(th_low / ideal - 1.0) > 0.3
