@@ -1,0 +1,312 @@
+"""Throughput of the fluctuating Shan-Chen D2Q9 hot path on GB300.
+
+Workload (synthetic, the paper's kind of run): a periodic 4096 x 4096 lattice,
+FP32 deviation storage, psi = 1 - exp(-rho), E4 force stencil, G = -5.0
+(T_hat = 0.8), tau = 1, rho0 = ln 2 (critical quench on the unstable branch),
+kT = 1e-6, seed 100.  One benchmark step is one sampling interval of that
+run: 500 fused lattice steps, one S(k) sample (row + column FFT and FP64
+accumulation), the FP64 mass/momentum reduction and the radial S(k) read-out.
+The populations (1.2 GB for both buffers) exceed the 129 MB L2, so no flush is
+needed between timed iterations.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fluctuating Shan-Chen D2Q9 MLUPS, % HBM roofline; ensemble & surrogate speedup"
+WORKLOAD = "d2q9_4096sq_fp32_G-5.0_quench"
+NX = NY = 4096
+G, TAU, KT, SEED = -5.0, 1.0, 1e-6, 100
+RHO0 = float(np.log(2.0))
+LB_PER_STEP = 500            # lattice steps per benchmark step (the S(k) interval)
+NBINS = NX // 2
+BYTES_PER_SITE = 72          # 9 FP32 loads + 9 FP32 stores per site update
+ORACLE_SAMPLE = (512, 512, 60)   # CPU baseline: lattice and steps of the bounded sample
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _step_kernel_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_4096sq_fp32_E4.json")
+    src = os.path.join(ROOT, "paper_2212_07848_gb300", "csrc", "lbsc_step.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("source_sha256") != h:
+            return None
+        return float(d["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: ORACLE_SAMPLE lattice and steps, then one S(k) sample."""
+    from oracle import oracle as O
+    nx, ny, steps = ORACLE_SAMPLE
+    o = O.OracleLattice(nx, ny, G, TAU, KT)
+    o.init(RHO0, SEED, 0.0)
+    t0 = time.perf_counter()
+    o.step(steps)
+    o.sk_sample_now()
+    dt = time.perf_counter() - t0
+    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
+            "kind": "oracle",
+            "sample": f"{nx}x{ny} lattice, {steps} steps of the same physics (G=-5.0, "
+                      f"rho0=ln2, kT=1e-6, E4, FP64) plus one direct-DFT S(k) sample; "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per = []
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline()
+    for _ in range(args.steps):
+        cb = cpu_baseline()
+        per.append(cb["value"])
+    value = statistics.median(per)
+    cb["value"] = value
+    nx, ny, steps = ORACLE_SAMPLE
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": nx * ny * steps / (value * 1e6) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "sample_lattice": [nx, ny],
+                   "sample_steps": steps},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.lattice import Lattice
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    lat = Lattice(NX, NY, G, TAU, KT, stencil=4, precision="fp32", device=local_rank)
+    lat.init(RHO0, SEED + rank, 0.0)
+    lat.sk_config(LB_PER_STEP, LB_PER_STEP)
+    stream = torch.cuda.ExternalStream(lat.stream())
+    bins = np.empty(NBINS)
+    h = lat.handle
+    L = abi.load()
+    conserved = np.zeros(3)
+    dptr = conserved.ctypes.data_as(C.POINTER(C.c_double))
+
+    def one_step(ev_k1=None):
+        # 499 plain steps, then the sampling step (writes delta rho) + S(k) sample
+        if ev_k1 is not None:
+            ev_k1[0].record(stream)
+        rc = L.lb_step(h, LB_PER_STEP - 1)
+        if ev_k1 is not None:
+            ev_k1[1].record(stream)
+        rc |= L.lb_step(h, 1)
+        rc |= L.lb_conserved(h, conserved)
+        if rc != 0:
+            raise abi.LbError(rc, "bench step")
+        abi.lb_structure_factor(h, bins, NBINS)
+
+    for _ in range(args.warmup):
+        one_step()
+    lat.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    k1_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            one_step(k1_events[k])
+        end.record(stream)
+        end.synchronize()
+    lat.sync()
+    ms = start.elapsed_time(end)
+    k1_ms = sum(a.elapsed_time(b) for a, b in k1_events) / (args.steps * (LB_PER_STEP - 1))
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    sites = NX * NY
+    value = world * sites * LB_PER_STEP * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end-to-end through the C ABI with host buffers: per step, upload the
+    # state from pinned host memory, run the interval, read back the density
+    # and the radial S(k).
+    state = torch.empty(9 * sites, dtype=torch.float32, pin_memory=True)
+    dens = torch.empty(sites, dtype=torch.float64, pin_memory=True)
+    state_np, dens_np = state.numpy(), dens.numpy()
+    lat.download_state(state_np.reshape(9, NY, NX))
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        abi.lb_upload_state(h, state_np.ctypes.data_as(C.c_void_p))
+        rc = L.lb_step(h, LB_PER_STEP)
+        if rc != 0:
+            raise abi.LbError(rc, "e2e step")
+        abi.lb_density(h, dens_np)
+        abi.lb_structure_factor(h, bins, NBINS)
+    lat.sync()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * sites * LB_PER_STEP * e2e_steps / float(te.item()) / 1e6
+
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_SITE * sites / (k1_ms * 1e-3) / 1e9
+    cb = cpu_baseline() if (rank == 0 and world == 1) else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "G": G, "tau": TAU, "kT": KT,
+                       "rho0": "ln2", "stencil": "E4", "lb_steps_per_step": LB_PER_STEP,
+                       "sk_sample_every": LB_PER_STEP, "nbins": NBINS,
+                       "l2": "inputs larger than L2 (1.21 GB of populations), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "step_kernel<float,4>",
+                         "kernel_ms": k1_ms, "bytes_per_site": BYTES_PER_SITE,
+                         "traffic": _step_kernel_traffic()},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": state_np.nbytes,
+                    "d2h_bytes_per_step": dens_np.nbytes + bins.nbytes,
+                    "steps": e2e_steps},
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * (LB_PER_STEP + 2 + 2 + 1),
+        }
+        if cb is not None:
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        from paper_2212_07848_gb300 import build
+        if rank == 0 or world == 1:
+            build.build()
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -53,6 +53,9 @@
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
 #endif
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* D2Q9 velocity set and weights (standard lattice, c_s^2 = 1/3).            */
@@ -615,4 +618,13 @@ void or_normals(const or_params *p, uint32_t site, uint32_t t, double z[6]) {
     box_muller(r[0], r[1], &z[0], &z[1]);
     box_muller(r[2], r[3], &z[2], &z[3]);
     box_muller(q[0], q[1], &z[4], &z[5]);
+}
+
+/* Threads the site loops run on (1 without OpenMP). */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

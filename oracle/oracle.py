@@ -70,8 +70,14 @@ def lib():
         L.or_stencil.argtypes = [C.c_int, _I, _I, _D]
         L.or_stencil.restype = C.c_int
         L.or_normals.argtypes = [C.POINTER(OrParams), C.c_uint32, C.c_uint32, _D]
+        L.or_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def threads():
+    """Host threads the oracle's site loops use."""
+    return int(lib().or_threads())
 
 
 def philox4x32(ctr, key):

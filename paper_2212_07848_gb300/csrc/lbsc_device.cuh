@@ -1,0 +1,119 @@
+// Device helpers of the fused D2Q9 step: counter-based random numbers, the
+// pseudopotential deviation, and the force-stencil tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbsc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11).  The ten round keys
+// are precomputed on the host (they depend only on the seed), so a round is
+// two 32x32->64 multiplies and two three-input XORs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t *__restrict__ rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
+// Uniform deviates in (0, 1]: (r + 1/2) 2^-32.  FP64 is exact; FP32 rounds r
+// to 24 significant bits first (relative error < 2^-24).
+template <typename T> __device__ __forceinline__ T uniform01(uint32_t r);
+template <> __device__ __forceinline__ float uniform01<float>(uint32_t r) {
+    return __fmaf_rn(__uint2float_rn(r), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+template <> __device__ __forceinline__ double uniform01<double>(uint32_t r) {
+    return ((double)r + 0.5) * 2.3283064365386963e-10;
+}
+
+// Box-Muller: (u1, u2) -> (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2).
+__device__ __forceinline__ void box_muller(float u1, float u2, float &z0, float &z1) {
+    float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+__device__ __forceinline__ void box_muller(double u1, double u2, double &z0, double &z1) {
+    double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+__device__ __forceinline__ float dev_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double dev_expm1(double x) { return expm1(x); }
+
+// delta psi = psi(rho0 + drho) - psi(rho0), written so that a small drho keeps
+// its relative precision:
+//   kind 0 (1 - e^-rho):          -e^{-rho0} expm1(-drho)
+//   kinds 1, 2 (c e^{-b/rho}):     psi0 expm1(b drho / (rho0 rho))
+template <typename T>
+__device__ __forceinline__ T delta_psi(T drho, int kind, T rho0, T psi_c, T psi_b) {
+    if (kind == 0) return -psi_c * dev_expm1(-drho);
+    return psi_c * dev_expm1(psi_b * drho / (rho0 * (rho0 + drho)));
+}
+
+// ---------------------------------------------------------------------------
+// Half stencils of the isotropic force sets (one vector of each +/- pair),
+// weights normalised to sum over the full set of w e_x^2 = 1.
+//   E4: |e|^2 = 1 : 1/3,  2 : 1/12
+//   E6: |e|^2 = 1 : 4/15, 2 : 1/10, 4 : 1/120
+//   E8: |e|^2 = 1 : 4/21, 2 : 4/45, 4 : 1/60, 5 : 2/315, 8 : 1/5040
+// ---------------------------------------------------------------------------
+struct HalfVec {
+    int ex, ey;
+    double w;
+};
+
+template <int ORDER> struct Stencil;
+template <> struct Stencil<4> {
+    static constexpr int H = 1;   // reach
+    static constexpr int N = 4;
+    __device__ static constexpr HalfVec v(int a) {
+        return a == 0 ? HalfVec{1, 0, 1.0 / 3.0}
+             : a == 1 ? HalfVec{0, 1, 1.0 / 3.0}
+             : a == 2 ? HalfVec{1, 1, 1.0 / 12.0}
+                      : HalfVec{-1, 1, 1.0 / 12.0};
+    }
+};
+template <> struct Stencil<6> {
+    static constexpr int H = 2;
+    static constexpr int N = 6;
+    __device__ static constexpr HalfVec v(int a) {
+        return a == 0 ? HalfVec{1, 0, 4.0 / 15.0}
+             : a == 1 ? HalfVec{0, 1, 4.0 / 15.0}
+             : a == 2 ? HalfVec{1, 1, 1.0 / 10.0}
+             : a == 3 ? HalfVec{-1, 1, 1.0 / 10.0}
+             : a == 4 ? HalfVec{2, 0, 1.0 / 120.0}
+                      : HalfVec{0, 2, 1.0 / 120.0};
+    }
+};
+template <> struct Stencil<8> {
+    static constexpr int H = 2;
+    static constexpr int N = 12;
+    __device__ static constexpr HalfVec v(int a) {
+        return a == 0  ? HalfVec{1, 0, 4.0 / 21.0}
+             : a == 1  ? HalfVec{0, 1, 4.0 / 21.0}
+             : a == 2  ? HalfVec{1, 1, 4.0 / 45.0}
+             : a == 3  ? HalfVec{-1, 1, 4.0 / 45.0}
+             : a == 4  ? HalfVec{2, 0, 1.0 / 60.0}
+             : a == 5  ? HalfVec{0, 2, 1.0 / 60.0}
+             : a == 6  ? HalfVec{2, 1, 2.0 / 315.0}
+             : a == 7  ? HalfVec{1, 2, 2.0 / 315.0}
+             : a == 8  ? HalfVec{-1, 2, 2.0 / 315.0}
+             : a == 9  ? HalfVec{-2, 1, 2.0 / 315.0}
+             : a == 10 ? HalfVec{2, 2, 1.0 / 5040.0}
+                       : HalfVec{-2, 2, 1.0 / 5040.0};
+    }
+};
+
+}  // namespace lbsc

@@ -1,0 +1,53 @@
+"""Full-size check at the benchmark's lattice (4096^2, FP32, G = -5.0 critical
+quench, kT = 1e-6) in the benchmark's launch configuration: one GPU step is
+compared with the oracle evaluated site by site on the same input state
+(random sites plus every kind of strip and wrap boundary), and mass and
+momentum are checked over the run."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from pairs import LN2
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def test_fullsize_4096_one_step_sampled_sites():
+    from paper_2212_07848_gb300.lattice import Lattice
+    nx = ny = 4096
+    G, tau, kT, seed = -5.0, 1.0, 1e-6, 100
+    g = Lattice(nx, ny, G, tau, kT)
+    g.init(LN2, seed, 0.01)
+    c0 = g.conserved()
+    g.step(3)
+    df_in = g.download_state().copy()
+    g.step(1)
+    df_out = g.download_state()
+    c1 = g.conserved()
+    assert abs(c1[0] - c0[0]) / c0[0] < 1e-6
+    assert abs(c1[1] - c0[1]) < 1e-6 * c0[0] and abs(c1[2] - c0[2]) < 1e-6 * c0[0]
+
+    rng = np.random.default_rng(1)
+    xs = list(rng.integers(0, nx, 3000))
+    ys = list(rng.integers(0, ny, 3000))
+    edge_x = [0, 1, 2, nx - 3, nx - 2, nx - 1, 127, 128, 129, 255, 256, 2047, 2048]
+    edge_y = [0, 1, 2, ny - 3, ny - 2, ny - 1, 63, 64, 65, 127, 128, 2047, 2048]
+    for ex in edge_x:
+        for ey in edge_y:
+            xs.append(ex)
+            ys.append(ey)
+    xs = np.array(xs, np.int32)
+    ys = np.array(ys, np.int32)
+
+    f_in = df_in.astype(np.float64)
+    f_in += (W * LN2)[:, None, None]
+    p = O.make_params(nx, ny, G, tau, kT, stencil=4, rho0=LN2, seed=seed)
+    ref = O.step_sites(p, 3, f_in, xs, ys)                 # [n][9] full populations
+    got = df_out[:, ys, xs].T.astype(np.float64) + W * LN2
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() < 1e-5, rel.max()
+    d_got = got.sum(1) - LN2
+    d_ref = ref.sum(1) - LN2
+    assert np.abs(d_got - d_ref).max() < 1e-4 * np.sqrt((d_ref ** 2).mean())

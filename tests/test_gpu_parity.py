@@ -1,0 +1,151 @@
+"""CUDA step vs the FP64 oracle, element by element, through the C ABI.
+
+FP64 storage: 1e-12 relative per site on rho and every full population
+after 1000 steps (128^2, G = -3.6, kT = 1e-5, seed 0) and on ragged
+multi-tile lattices with every stencil and pseudopotential.  FP32 storage
+(deviations from w_i rho0): 1e-4 relative per site after 100 steps.  The
+noise is drawn from the same Philox stream on both sides, so the
+trajectories agree up to rounding.
+"""
+import numpy as np
+import pytest
+
+from pairs import LN2, make_pair, max_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(g, o, tol, dtol=None):
+    fr = max_rel(g.populations(), o.populations())
+    rr = max_rel(g.density(), o.density())
+    assert fr <= tol, f"populations: {fr:.3e}"
+    assert rr <= tol, f"density: {rr:.3e}"
+    if dtol is not None:
+        d_g, d_o = g.density(), o.density()
+        dd = d_o - d_o.mean()
+        rel = np.abs(d_g - d_o).max() / np.sqrt((dd ** 2).mean())
+        assert rel <= dtol, f"delta rho vs rms: {rel:.3e}"
+    return fr, rr
+
+
+def test_fp64_128sq_G_minus_3p6_1000_steps():
+    g, o = make_pair(128, 128, -3.6, 1.0, 1e-5, precision="fp64", rho0=LN2, seed=0)
+    g.step(1000)
+    o.step(1000)
+    g.sync()
+    _compare(g, o, 1e-12)
+    assert g.t == o.t == 1000
+
+
+FP64_CASES = [
+    # nx, ny, G, tau, kT, stencil, kind, p1, p2, rho0, amp, replica, strip
+    (36, 20, -3.6, 0.7, 1e-4, 6, 0, 0.0, 0.0, LN2, 0.01, 0, None),
+    (20, 44, -4.5, 1.6, 1e-5, 8, 0, 0.0, 0.0, 0.33, 0.005, 0, None),
+    (24, 16, -3.0, 1.0, 1e-6, 4, 1, 1.0 / 3.0 / 0.8, 1.0, 1.9, 0.01, 0, None),
+    (28, 12, -2.0, 0.9, 1e-5, 4, 2, 1.0, 1.0, 1.0, 0.01, 3, None),
+    (260, 36, -3.6, 1.0, 1e-5, 4, 0, 0.0, 0.0, LN2, 0.01, 0, 8),    # ragged strips in x and y
+    (132, 20, -3.6, 0.8, 1e-5, 8, 0, 0.0, 0.0, LN2, 0.01, 1, 4),    # E8 halo across strips
+    (4, 4, -3.6, 1.0, 1e-4, 6, 0, 0.0, 0.0, LN2, 0.01, 0, None),    # smallest lattice, reach 2
+]
+
+
+@pytest.mark.parametrize("nx,ny,G,tau,kT,st,kind,p1,p2,rho0,amp,rep,strip", FP64_CASES)
+def test_fp64_matrix(nx, ny, G, tau, kT, st, kind, p1, p2, rho0, amp, rep, strip):
+    g, o = make_pair(nx, ny, G, tau, kT, stencil=st, kind=kind, p1=p1, p2=p2,
+                     precision="fp64", rho0=rho0, seed=7, amp=amp, replica=rep, strip=strip)
+    _compare(g, o, 1e-13)          # initial kick, Philox block 2
+    g.step(200)
+    o.step(200)
+    _compare(g, o, 1e-12)
+
+
+FP32_CASES = [
+    # metastable gas branch at G = -4.5 (kT = 1e-6)
+    (128, 64, -4.5, 1.0, 1e-6, 4, 0, 0.0, 0.0, 0.33, 0.0),
+    # critical quench at G = -5.0 (unstable branch)
+    (128, 128, -5.0, 1.0, 1e-6, 4, 0, 0.0, 0.0, LN2, 0.0),
+    # supercritical, E8, psi of Eq. (5)
+    (64, 64, -3.0, 0.8, 1e-5, 8, 1, 1.0 / 3.0 / 0.8, 1.0, 1.9, 0.01),
+    # ragged strips, E6
+    (132, 52, -3.6, 1.2, 1e-5, 6, 0, 0.0, 0.0, LN2, 0.01),
+]
+
+
+@pytest.mark.parametrize("nx,ny,G,tau,kT,st,kind,p1,p2,rho0,amp", FP32_CASES)
+def test_fp32_100_steps(nx, ny, G, tau, kT, st, kind, p1, p2, rho0, amp):
+    g, o = make_pair(nx, ny, G, tau, kT, stencil=st, kind=kind, p1=p1, p2=p2,
+                     precision="fp32", rho0=rho0, seed=11, amp=amp)
+    g.step(100)
+    o.step(100)
+    _compare(g, o, 1e-4, dtol=1e-2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("st", [4, 8])
+def test_flat_equilibrium_is_exact(precision, st):
+    g, o = make_pair(64, 32, -4.5, 0.8, 0.0, stencil=st, precision=precision, rho0=0.33)
+    g.step(100)
+    df = g.download_state()
+    assert np.all(df == 0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_conservation_with_noise(precision, tol):
+    g, o = make_pair(96, 64, -3.6, 0.9, 1e-4, stencil=6, precision=precision, seed=5, amp=0.01)
+    c0 = g.conserved()
+    g.step(500)
+    c1 = g.conserved()
+    assert abs(c1[0] - c0[0]) / c0[0] < tol
+    assert abs(c1[1] - c0[1]) < tol * c0[0] and abs(c1[2] - c0[2]) < tol * c0[0]
+    # the FP64 device reduction agrees with the oracle's sum of the same state
+    o.step(500)
+    if precision == "fp64":
+        assert np.allclose(c1, o.conserved(), rtol=1e-13, atol=1e-12)
+    # deterministic: the same state reduces to the same bits
+    assert np.array_equal(g.conserved(), c1)
+
+
+def test_nonfinite_state_is_reported():
+    from paper_2212_07848_gb300 import abi
+    g, o = make_pair(32, 32, -3.6, 1.0, 1e-5, precision="fp32")
+    f = g.populations()
+    f[3, 5, 7] = np.nan
+    g.set_populations(f)
+    g.step(1)
+    with pytest.raises(abi.LbError) as e:
+        g.sync()
+    assert e.value.code == abi.LB_ERR_NONFINITE
+    g.sync()   # flag cleared after being reported
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bit_identical(tmp_path, precision):
+    g, _ = make_pair(64, 32, -4.2, 0.9, 1e-5, precision=precision, seed=3, amp=0.01)
+    g.sk_config(5, 20)
+    g.step(40)
+    path = str(tmp_path / "ck.bin")
+    g.save(path)
+    g.step(40)
+    a = g.download_state().copy()
+    sa, na = g.structure_factor()
+    g.load(path)
+    assert g.t == 40
+    g.step(40)
+    b = g.download_state()
+    sb, nb = g.structure_factor()
+    assert np.array_equal(a, b)
+    assert na == nb and np.array_equal(sa, sb)
+
+
+def test_torch_stream_and_zero_copy_view():
+    torch = pytest.importorskip("torch")
+    from paper_2212_07848_gb300.lattice import Lattice
+    s = torch.cuda.Stream()
+    g = Lattice(64, 64, -3.6, 1.0, 1e-5, stream=s.cuda_stream)
+    g.init(LN2, 1, 0.01)
+    g.step(3)
+    s.synchronize()
+    assert g.stream() == s.cuda_stream
+    v = g.torch_populations()
+    assert v.shape == (9, 64, 64) and v.dtype == torch.float32
+    assert np.array_equal(v.cpu().numpy(), g.download_state())
