@@ -1,0 +1,43 @@
+"""Run one synthetic lattice for a number of steps (profiling and sizing).
+
+    python -m paper_2212_07848_gb300.workload --nx 2048 --ny 2048 --steps 5
+
+Defaults to the critical quench of the benchmark (G = -5.0, rho0 = ln 2,
+kT = 1e-6, E4, FP32) on a smaller square lattice.  Prints the wall time.
+"""
+import argparse
+import math
+import time
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--G", type=float, default=-5.0)
+    ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--kT", type=float, default=1e-6)
+    ap.add_argument("--rho0", type=float, default=math.log(2.0))
+    ap.add_argument("--stencil", type=int, default=4)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--sk-every", type=int, default=0)
+    ap.add_argument("--strip", type=int, default=0)
+    a = ap.parse_args()
+    from .lattice import Lattice
+    lat = Lattice(a.nx, a.ny, a.G, a.tau, a.kT, stencil=a.stencil, precision=a.precision)
+    if a.strip:
+        lat.set_strip_height(a.strip)
+    lat.init(a.rho0, 100, 0.0)
+    if a.sk_every:
+        lat.sk_config(a.sk_every, a.sk_every)
+    t0 = time.perf_counter()
+    lat.step(a.steps)
+    lat.sync()
+    dt = time.perf_counter() - t0
+    print(f"{a.nx}x{a.ny} {a.precision} E{a.stencil}: {a.steps} steps in {dt * 1e3:.2f} ms")
+    lat.close()
+
+
+if __name__ == "__main__":
+    main()

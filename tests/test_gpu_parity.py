@@ -100,7 +100,12 @@ def test_conservation_with_noise(precision, tol):
     # the FP64 device reduction agrees with the oracle's sum of the same state
     o.step(500)
     if precision == "fp64":
-        assert np.allclose(c1, o.conserved(), rtol=1e-13, atol=1e-12)
+        co = o.conserved()
+        assert abs(c1[0] - co[0]) <= 1e-13 * co[0]
+        # the oracle sums full populations (~0.1 each), so its momentum total
+        # carries ~1e-12 of FP64 rounding at this size; the deviations summed
+        # on the device are ~1e3 times smaller
+        assert np.abs(c1[1:] - co[1:]).max() < 1e-11
     # deterministic: the same state reduces to the same bits
     assert np.array_equal(g.conserved(), c1)
 
