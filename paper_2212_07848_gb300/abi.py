@@ -67,7 +67,12 @@ def load(path=LIB_PATH):
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is not built: call "
                            "paper_2212_07848_gb300.build.build() (no CPU fallback)")
-    L = C.CDLL(path)
+    _lib = bind(C.CDLL(path))
+    return _lib
+
+
+def bind(L):
+    """Declare the C signatures of include/lbsc.h on a loaded library."""
     P = C.c_void_p
     sig = {
         "lb_params_init": (C.c_int, [C.POINTER(lb_params)]),
@@ -104,7 +109,6 @@ def load(path=LIB_PATH):
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = L
     return L
 
 

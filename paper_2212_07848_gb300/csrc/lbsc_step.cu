@@ -56,6 +56,18 @@ __device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane, in
     g[8] = __ldg(src + 8 * plane + rp + xm);   // c = ( 1,-1)
 }
 
+// 1/rho and sqrt(rho) from one reciprocal square root (FP32); FP64 keeps the
+// correctly rounded operations.
+__device__ __forceinline__ void inv_and_sqrt(float rho, float &inv, float &sr) {
+    const float r = rsqrtf(rho);
+    inv = r * r;
+    sr = rho * r;
+}
+__device__ __forceinline__ void inv_and_sqrt(double rho, double &inv, double &sr) {
+    inv = 1.0 / rho;
+    sr = sqrt(rho);
+}
+
 template <typename T>
 __device__ __forceinline__ T sum9(const T g[9]) {
     return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
@@ -104,23 +116,36 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
         for (int i = 0; i < 9; ++i) q[r][i] = T(0);
 
     const int it_end = (y1 - y0) + 2 * H;
-    for (int it = 0; it < it_end; ++it) {
-        const int yy = y0 - H + it;
-        const int yc = wrap_once(yy, ny);
+    // Register prefetch: the loads of row it+1 are issued before row it is
+    // collided, so they are in flight during the collision arithmetic.
+    T gn[9], ghn[9];
+    {
+        const int yc = wrap_once(y0 - H, ny);
         const int ym = yc == 0 ? ny - 1 : yc - 1;
         const int yp = yc == ny - 1 ? 0 : yc + 1;
+        if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+        if (halo) pull(p.src, plane, nx, hcol, hxm, hxp, yc, ym, yp, ghn);
+    }
+    for (int it = 0; it < it_end; ++it) {
         const int slot = it & (RING - 1);
-
-        T g[9];
-        if (active) {
-            pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, g);
+        T g[9], gh[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            g[i] = gn[i];
+            gh[i] = ghn[i];
+        }
+        if (it + 1 < it_end) {
+            const int yc = wrap_once(y0 - H + it + 1, ny);
+            const int ym = yc == 0 ? ny - 1 : yc - 1;
+            const int yp = yc == ny - 1 ? 0 : yc + 1;
+            if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+            if (halo) pull(p.src, plane, nx, hcol, hxm, hxp, yc, ym, yp, ghn);
+        }
+        const int yy = y0 - H + it;
+        if (active)
             s_dpsi[slot][tx + H] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
-        }
-        if (halo) {
-            T gh[9];
-            pull(p.src, plane, nx, hcol, hxm, hxp, yc, ym, yp, gh);
+        if (halo)
             s_dpsi[slot][hslot] = delta_psi<T>(sum9(gh), p.psi_kind, rho0, p.psi_c, p.psi_b);
-        }
 #pragma unroll
         for (int r = 0; r < H; ++r)
 #pragma unroll
@@ -172,7 +197,8 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
 
         // Guo forcing: u = (j + F/2) / rho; post-collision momentum j + F.
         const T rho = rho0 + drho;
-        const T inv_rho = T(1) / rho;
+        T inv_rho, sr;
+        inv_and_sqrt(rho, inv_rho, sr);
         const T ux = (m1 + T(0.5) * Fx) * inv_rho;
         const T uy = (m2 + T(0.5) * Fy) * inv_rho;
         const T gam = p.gamma, hs = p.src_scale;
@@ -195,7 +221,6 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
             box_muller(uniform01<T>(r0.x), uniform01<T>(r0.y), z3, z4);
             box_muller(uniform01<T>(r0.z), uniform01<T>(r0.w), z5, z6);
             box_muller(uniform01<T>(r1.x), uniform01<T>(r1.y), z7, z8);
-            const T sr = sqrt(rho);
             m3s += p.amp[0] * sr * z3;
             m4s += p.amp[1] * sr * z4;
             m5s += p.amp[2] * sr * z5;
