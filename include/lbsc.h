@@ -200,6 +200,28 @@ void *lb_device_ptr(lb_ctx *h, int which);
 /* The cudaStream_t the context runs on. */
 void *lb_stream(lb_ctx *h);
 
+/* Allocation-free mass and momentum sums, for callers that must not call
+ * cudaMalloc: a host application whose device memory all comes from its own
+ * pool, or a loop that cannot take the device-wide synchronisation an
+ * allocation brings.  The paper has no counterpart; this is a library
+ * service.  Inputs: d_df, device pointer to deviations [9][ny][nx] in the
+ * given precision (the layout of LB_PTR_POPULATIONS) and rho0, their
+ * reference density.  Output: d_out3, a caller-owned device array of 3
+ * doubles receiving (nx*ny*rho0 + sum delta rho, sum jx, sum jy), written
+ * asynchronously on `stream` (cudaStream_t, NULL for the default stream).
+ * Scratch: a fixed 96 KB device array inside the library (4096 partial
+ * triples), held on every GPU that loads the library until the process
+ * exits; lattices above 4096 x 4096 = 16,777,216 sites return
+ * LB_ERR_UNSUPPORTED.  Every call shares that array and leaves its partial
+ * sums there; each call rewrites every slot it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (make that first call before
+ * any stream capture).  Nothing here allocates device or host memory.
+ * Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_CUDA. */
+int lb_conserved_static(const void *d_df, int precision, int nx, int ny, double rho0,
+                        double *d_out3, void *stream);
+
 /* Static message for a status code. */
 const char *lb_strerror(int code);
 

@@ -34,7 +34,7 @@ EXPORTED = [
     "lb_set_density", "lb_upload_state", "lb_download_state", "lb_sk_config",
     "lb_sk_reset", "lb_sk_sample_now", "lb_structure_factor",
     "lb_structure_factor_counts", "lb_conserved", "lb_save", "lb_load",
-    "lb_device_ptr", "lb_stream", "lb_strerror",
+    "lb_device_ptr", "lb_stream", "lb_strerror", "lb_conserved_static",
 ]
 
 
@@ -104,6 +104,7 @@ def bind(L):
         "lb_device_ptr": (C.c_void_p, [P, C.c_int]),
         "lb_stream": (C.c_void_p, [P]),
         "lb_strerror": (C.c_char_p, [C.c_int]),
+        "lb_conserved_static": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -243,3 +244,10 @@ def lb_device_ptr(h, which):
 
 def lb_stream(h):
     return load().lb_stream(h)
+
+
+def lb_conserved_static(d_df, precision, nx, ny, rho0, d_out3, stream=None):
+    """Allocation-free mass/momentum sums of a device population buffer into a
+    caller-owned device array of 3 doubles (see include/lbsc.h)."""
+    _check(load().lb_conserved_static(d_df, precision, nx, ny, rho0, d_out3, stream),
+           "lb_conserved_static")

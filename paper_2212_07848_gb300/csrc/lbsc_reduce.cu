@@ -10,6 +10,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "lbsc.h"
 #include "lbsc_internal.cuh"
 
 namespace lbsc {
@@ -107,3 +110,105 @@ cudaError_t launch_conserved(int precision, const void *df, double *partials, in
 }
 
 }  // namespace lbsc
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant for callers that must not call cudaMalloc (for
+// example a host application whose device memory is all owned by its own
+// pool, or a loop that cannot accept the device-wide synchronisation an
+// allocation implies).  The per-block partial sums live in a fixed device
+// array inside this library instead of a context buffer.
+// ---------------------------------------------------------------------------
+namespace lbsc {
+
+constexpr int kStaticSitesPerBlock = kRedThreads * 16;      // 4096 sites per block
+constexpr int kStaticMaxBlocks = 4096;                      // up to 4096 x 4096 sites
+static __device__ __align__(256) double g_conserved_scratch[3 * kStaticMaxBlocks];
+
+// One block per contiguous chunk of kStaticSitesPerBlock sites; every block
+// writes its own partial triple, so no slot has to start at zero.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+conserved_chunk_kernel(const T *__restrict__ df, size_t plane, double *__restrict__ partials) {
+    double m = 0.0, jx = 0.0, jy = 0.0;
+    const size_t begin = (size_t)blockIdx.x * kStaticSitesPerBlock;
+    size_t end = begin + kStaticSitesPerBlock;
+    if (end > plane) end = plane;
+    for (size_t s = begin + threadIdx.x; s < end; s += kRedThreads) {
+        double g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = (double)df[i * plane + s];
+        m += ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+        jx += (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
+        jy += (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+    }
+    block_sum3(m, jx, jy);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = m;
+        partials[3 * blockIdx.x + 1] = jx;
+        partials[3 * blockIdx.x + 2] = jy;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+conserved_static_final_kernel(const double *__restrict__ partials, int nblocks, double mass0,
+                              double *__restrict__ out3) {
+    double m = 0.0, jx = 0.0, jy = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        m += partials[3 * b + 0];
+        jx += partials[3 * b + 1];
+        jy += partials[3 * b + 2];
+    }
+    block_sum3(m, jx, jy);
+    if (threadIdx.x == 0) {
+        out3[0] = mass0 + m;
+        out3[1] = jx;
+        out3[2] = jy;
+    }
+}
+
+namespace {
+// Device address of g_conserved_scratch, looked up once per device with that
+// device current (in host code the symbol names a host-side stand-in).
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double *g_scratch_addr[kMaxDevices] = {nullptr};
+
+int scratch_for_current_device(double **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LB_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_conserved_scratch) != cudaSuccess || !p) return LB_ERR_CUDA;
+        g_scratch_addr[dev] = (double *)p;
+    }
+    *out = g_scratch_addr[dev];
+    return LB_OK;
+}
+}  // namespace
+
+}  // namespace lbsc
+
+extern "C" int lb_conserved_static(const void *d_df, int precision, int nx, int ny, double rho0,
+                                   double *d_out3, void *stream) {
+    using namespace lbsc;
+    if (!d_df || !d_out3 || nx < 1 || ny < 1) return LB_ERR_ARG;
+    if (precision != LB_FP32 && precision != LB_FP64) return LB_ERR_ARG;
+    const size_t plane = (size_t)nx * (size_t)ny;
+    if (plane > (size_t)kStaticSitesPerBlock * kStaticMaxBlocks) return LB_ERR_UNSUPPORTED;
+    double *scratch = nullptr;
+    int rc = scratch_for_current_device(&scratch);
+    if (rc != LB_OK) return rc;
+    const int nblocks = (int)((plane + kStaticSitesPerBlock - 1) / kStaticSitesPerBlock);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == LB_FP32)
+        conserved_chunk_kernel<float><<<nblocks, kRedThreads, 0, s>>>((const float *)d_df, plane,
+                                                                      scratch);
+    else
+        conserved_chunk_kernel<double><<<nblocks, kRedThreads, 0, s>>>((const double *)d_df,
+                                                                       plane, scratch);
+    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    conserved_static_final_kernel<<<1, kRedThreads, 0, s>>>(scratch, nblocks,
+                                                           (double)plane * rho0, d_out3);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
