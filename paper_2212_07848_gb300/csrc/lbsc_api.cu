@@ -74,7 +74,8 @@ int cuda_status(cudaError_t e) {
 int validate(const lb_params *p) {
     if (!p) return LB_ERR_ARG;
     if (p->nx < 4 || p->ny < 4 || p->nx % 4 || p->ny % 4) return LB_ERR_ARG;
-    if ((double)p->nx * (double)p->ny > 2147483647.0) return LB_ERR_ARG;
+    // 32-bit element indices in the kernels: 9 nx ny < 2^32
+    if (9.0 * (double)p->nx * (double)p->ny >= 4294967296.0) return LB_ERR_ARG;
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return LB_ERR_ARG;
     if (!(p->kT >= 0.0) || !isfinite(p->kT)) return LB_ERR_ARG;
     if (!isfinite(p->G)) return LB_ERR_ARG;
@@ -92,7 +93,7 @@ int default_strip(int nx, int ny) {
     const long gx = (nx + kStepTX - 1) / kStepTX;
     long target = (long)ny * gx / (152 * 4);
     int h = 8;
-    while (h < 64 && h * 2 <= target) h *= 2;
+    while (h < 32 && h * 2 <= target) h *= 2;
     if (h > ny) h = ny;
     return h;
 }

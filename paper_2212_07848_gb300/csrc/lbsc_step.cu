@@ -10,7 +10,7 @@
 //
 // Work decomposition: a CTA owns a strip of kStepTX columns and sweeps
 // strip_h rows downwards.  Each iteration pulls one new row (one thread per
-// column, plus 2H threads for the halo columns), writes the pseudopotential
+// column, plus one extra warp for the 2H halo columns), writes the pseudopotential
 // deviation of that row into a shared-memory ring of rows, and collides the
 // row H above it, whose 2H+1 pseudopotential rows are then complete.  The
 // pulled populations of the last H+1 rows stay in registers, so every
@@ -31,7 +31,8 @@ template <typename T> struct KParams {
     int *__restrict__ flag;
     int nx, ny, strip_h, psi_kind, noise;
     uint32_t step, replica;
-    T rho0, force_pref, psi_c, psi_b, psi0, gamma, src_scale;
+    T rho0, force_pref, psi_c, psi_b, psi0, gamma;
+    T c3a, c3b, c4a, c4b, c5a, c5b;   // folded relaxation/source constants
     T amp[6];
     uint32_t rk[20];
 };
@@ -40,20 +41,22 @@ __device__ __forceinline__ int wrap_once(int a, int n) {
     return a < 0 ? a + n : (a >= n ? a - n : a);
 }
 
-// Pull streaming of one site: g_i(x) = f*_i(x - c_i).
+// Pull streaming of one site: g_i(x) = f*_i(x - c_i).  32-bit element
+// indices (the context requires 9 nx ny < 2^32).
 template <typename T>
-__device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane, int nx, int xc,
+__device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane_, int nx, int xc,
                                      int xm, int xp, int yc, int ym, int yp, T g[9]) {
-    const size_t rc = (size_t)yc * nx, rm = (size_t)ym * nx, rp = (size_t)yp * nx;
-    g[0] = __ldg(src + 0 * plane + rc + xc);
-    g[1] = __ldg(src + 1 * plane + rc + xm);   // c = ( 1, 0)
-    g[2] = __ldg(src + 2 * plane + rm + xc);   // c = ( 0, 1)
-    g[3] = __ldg(src + 3 * plane + rc + xp);   // c = (-1, 0)
-    g[4] = __ldg(src + 4 * plane + rp + xc);   // c = ( 0,-1)
-    g[5] = __ldg(src + 5 * plane + rm + xm);   // c = ( 1, 1)
-    g[6] = __ldg(src + 6 * plane + rm + xp);   // c = (-1, 1)
-    g[7] = __ldg(src + 7 * plane + rp + xp);   // c = (-1,-1)
-    g[8] = __ldg(src + 8 * plane + rp + xm);   // c = ( 1,-1)
+    const uint32_t plane = (uint32_t)plane_;
+    const uint32_t rc = (uint32_t)yc * nx, rm = (uint32_t)ym * nx, rp = (uint32_t)yp * nx;
+    g[0] = __ldg(src + (0u * plane + rc + xc));
+    g[1] = __ldg(src + (1u * plane + rc + xm));
+    g[2] = __ldg(src + (2u * plane + rm + xc));
+    g[3] = __ldg(src + (3u * plane + rc + xp));
+    g[4] = __ldg(src + (4u * plane + rp + xc));
+    g[5] = __ldg(src + (5u * plane + rm + xm));
+    g[6] = __ldg(src + (6u * plane + rm + xp));
+    g[7] = __ldg(src + (7u * plane + rp + xp));
+    g[8] = __ldg(src + (8u * plane + rp + xm));
 }
 
 // 1/rho and sqrt(rho) from one reciprocal square root (FP32); FP64 keeps the
@@ -73,8 +76,86 @@ __device__ __forceinline__ T sum9(const T g[9]) {
     return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
 }
 
+// Collision of one site in the Hermite moment basis, Eq. (12):
+// moments of the pulled deviations g -> Guo velocity u = (j + F/2)/rho ->
+// BGK relaxation of the stress modes towards rho u u with the Guo source
+// (1 - 1/2tau)(u F + F u), ghost modes relaxed towards zero, momentum j + F
+// -> noise sqrt(mu rho b_k (1 - gamma^2)) z_k on modes 3..8 -> inverse
+// transform delta f_i = w_i sum_k e_ki m_k / b_k.  The inverse is factored
+// into symmetric sums and differences with the weights folded in.
+template <typename T>
+__device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<T> &p,
+                                        uint32_t site, T f[9]) {
+    // forward transform (integer coefficients, shared subexpressions)
+    const T e13 = g[1] - g[3], e24 = g[2] - g[4];
+    const T s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const T d57 = g[5] - g[7], d86 = g[8] - g[6];
+    const T s57 = g[5] + g[7], s68 = g[6] + g[8];
+    const T sa = s13 + s24, sd = s57 + s68;
+    const T drho = g[0] + (sa + sd);
+    const T t1 = d57 + d86, t2 = d57 - d86;
+    const T m1 = e13 + t1;                                   // j_x
+    const T m2 = e24 + t2;                                   // j_y
+    const T m3 = fma(T(4), sd, fma(T(-2), g[0], sa));        // 3c^2 - 2
+    const T m4 = s13 - s24;                                  // cx^2 - cy^2
+    const T m5 = s57 - s68;                                  // cx cy
+    const T m6 = fma(T(2), t1, -e13);                        // (3c^2 - 4) cx
+    const T m7 = fma(T(2), t2, -e24);                        // (3c^2 - 4) cy
+    const T m8 = fma(T(8), sd, fma(T(-4), sa, g[0] + g[0])); // 9c^4 - 15c^2 + 2
+
+    T inv_rho, sr;
+    inv_and_sqrt(p.rho0 + drho, inv_rho, sr);
+    const T jxh = fma(T(0.5), Fx, m1), jyh = fma(T(0.5), Fy, m2);   // rho u
+    const T ux = jxh * inv_rho, uy = jyh * inv_rho;
+    const T qxx = jxh * ux, qyy = jyh * uy, qxy = jxh * uy;          // rho u u
+    const T pxx = ux * Fx, pyy = uy * Fy, pxy = fma(ux, Fy, uy * Fx);
+    const T gam = p.gamma;
+    T m3s = fma(gam, m3, fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy)));
+    T m4s = fma(gam, m4, fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy)));
+    T m5s = fma(gam, m5, fma(p.c5a, qxy, p.c5b * pxy));
+    T m6s = gam * m6, m7s = gam * m7, m8s = gam * m8;
+    const T jxs = m1 + Fx, jys = m2 + Fy;
+
+    if (p.noise) {
+        const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), p.rk);
+        const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), p.rk);
+        T c, sn, rad;
+        box_muller_polar(uniform01<T>(r0.x), uniform01<T>(r0.y), rad, c, sn);
+        rad *= sr;
+        m3s = fma(p.amp[0] * rad, c, m3s);
+        m4s = fma(p.amp[1] * rad, sn, m4s);
+        box_muller_polar(uniform01<T>(r0.z), uniform01<T>(r0.w), rad, c, sn);
+        rad *= sr;
+        m5s = fma(p.amp[2] * rad, c, m5s);
+        m6s = fma(p.amp[3] * rad, sn, m6s);
+        box_muller_polar(uniform01<T>(r1.x), uniform01<T>(r1.y), rad, c, sn);
+        rad *= sr;
+        m7s = fma(p.amp[4] * rad, c, m7s);
+        m8s = fma(p.amp[5] * rad, sn, m8s);
+    }
+
+    // inverse transform
+    f[0] = fma(T(1.0 / 18.0), m8s, fma(T(-2.0 / 9.0), m3s, T(4.0 / 9.0) * drho));
+    const T B = fma(T(1.0 / 36.0), m3s - m8s, T(1.0 / 9.0) * drho);
+    const T P = fma(T(0.25), m4s, B), R = fma(T(-0.25), m4s, B);
+    const T Q = fma(T(-1.0 / 6.0), m6s, T(1.0 / 3.0) * jxs);
+    const T Sq = fma(T(-1.0 / 6.0), m7s, T(1.0 / 3.0) * jys);
+    f[1] = P + Q;
+    f[3] = P - Q;
+    f[2] = R + Sq;
+    f[4] = R - Sq;
+    const T D = fma(T(1.0 / 72.0), m8s, T(1.0 / 36.0) * (drho + m3s));
+    const T U = fma(T(0.25), m5s, D), V = fma(T(-0.25), m5s, D);
+    const T A = T(1.0 / 12.0) * (jxs + m6s), Bd = T(1.0 / 12.0) * (jys + m7s);
+    const T X = A + Bd, Y = A - Bd;
+    f[5] = U + X;
+    f[7] = U - X;
+    f[6] = V - Y;
+    f[8] = V + Y;
+}
+
 template <typename T, int ORDER, bool SAMPLE>
-__global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
+__global__ void __launch_bounds__(kStepTX + 32) step_kernel(const KParams<T> p) {
     using S = Stencil<ORDER>;
     constexpr int H = S::H;
     constexpr int RING = (H == 1) ? 4 : 8;   // >= 2H + 2 rows, power of two
@@ -87,23 +168,27 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
     const int x0 = blockIdx.x * kStepTX;
     const int xe = min(x0 + kStepTX, nx);
     const int ncol = xe - x0;
-    const bool active = tx < ncol;
-    const int x = active ? x0 + tx : x0;
+
+    // Threads 0..kStepTX-1 own the strip's columns; the extra warp owns the
+    // 2H halo columns (left, then right) and only computes their
+    // pseudopotential, so every warp does the same pull-and-psi work per row.
+    const bool interior = tx < kStepTX;
+    const int hl = tx - kStepTX;
+    const bool active = interior ? (tx < ncol) : (hl < 2 * H);
+    int x, slot_col;
+    if (interior) {
+        x = active ? x0 + tx : x0;
+        slot_col = tx + H;
+    } else if (hl < H) {
+        x = wrap_once(x0 - H + hl, nx);
+        slot_col = hl;
+    } else {
+        x = wrap_once(xe + (min(hl, 2 * H - 1) - H), nx);
+        slot_col = ncol + H + (min(hl, 2 * H - 1) - H);
+    }
+    const bool collides = interior && active;
     const int xm = x == 0 ? nx - 1 : x - 1;
     const int xp = x == nx - 1 ? 0 : x + 1;
-
-    // Threads 0..2H-1 also own one halo column each (left, then right).
-    const bool halo = tx < 2 * H;
-    int hcol = 0, hslot = 0;
-    if (tx < H) {
-        hcol = wrap_once(x0 - H + tx, nx);
-        hslot = tx;
-    } else {
-        hcol = wrap_once(xe + (tx - H), nx);
-        hslot = ncol + H + (tx - H);
-    }
-    const int hxm = hcol == 0 ? nx - 1 : hcol - 1;
-    const int hxp = hcol == nx - 1 ? 0 : hcol + 1;
 
     const int y0 = blockIdx.y * p.strip_h;
     const int y1 = min(y0 + p.strip_h, ny);
@@ -118,44 +203,36 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
     const int it_end = (y1 - y0) + 2 * H;
     // Register prefetch: the loads of row it+1 are issued before row it is
     // collided, so they are in flight during the collision arithmetic.
-    T gn[9], ghn[9];
+    T gn[9];
     {
         const int yc = wrap_once(y0 - H, ny);
         const int ym = yc == 0 ? ny - 1 : yc - 1;
         const int yp = yc == ny - 1 ? 0 : yc + 1;
         if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
-        if (halo) pull(p.src, plane, nx, hcol, hxm, hxp, yc, ym, yp, ghn);
     }
+#pragma unroll 2
     for (int it = 0; it < it_end; ++it) {
         const int slot = it & (RING - 1);
-        T g[9], gh[9];
+        T g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            g[i] = gn[i];
-            gh[i] = ghn[i];
-        }
-        if (it + 1 < it_end) {
+        for (int i = 0; i < 9; ++i) g[i] = gn[i];
+        if (it + 1 < it_end && active) {
             const int yc = wrap_once(y0 - H + it + 1, ny);
             const int ym = yc == 0 ? ny - 1 : yc - 1;
             const int yp = yc == ny - 1 ? 0 : yc + 1;
-            if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
-            if (halo) pull(p.src, plane, nx, hcol, hxm, hxp, yc, ym, yp, ghn);
+            pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
         }
         const int yy = y0 - H + it;
         if (active)
-            s_dpsi[slot][tx + H] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
-        if (halo)
-            s_dpsi[slot][hslot] = delta_psi<T>(sum9(gh), p.psi_kind, rho0, p.psi_c, p.psi_b);
+            s_dpsi[slot][slot_col] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
 #pragma unroll
         for (int r = 0; r < H; ++r)
 #pragma unroll
             for (int i = 0; i < 9; ++i) q[r][i] = q[r + 1][i];
-        if (active) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) q[H][i] = g[i];
-        }
+        for (int i = 0; i < 9; ++i) q[H][i] = g[i];
         __syncthreads();
-        if (it < 2 * H || !active) continue;
+        if (it < 2 * H || !collides) continue;
 
         // ---- collide row yr = yy - H ------------------------------------
         const int yr = yy - H;
@@ -178,86 +255,21 @@ __global__ void __launch_bounds__(kStepTX) step_kernel(const KParams<T> p) {
         const T Fx = p.force_pref * psic * sx;
         const T Fy = p.force_pref * psic * sy;
 
-        const T *gq = q[0];
-        const T g0 = gq[0], g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4];
-        const T g5 = gq[5], g6 = gq[6], g7 = gq[7], g8 = gq[8];
+        T f[9];
+        collide(q[0], Fx, Fy, p, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
 
-        // Hermite moments of the deviations (integer-coefficient transform).
-        const T sa = (g1 + g3) + (g2 + g4);
-        const T sd = (g5 + g7) + (g6 + g8);
-        const T drho = g0 + sa + sd;
-        const T m1 = (g1 - g3) + (g5 - g7) + (g8 - g6);
-        const T m2 = (g2 - g4) + (g5 - g7) + (g6 - g8);
-        const T m3 = T(-2) * g0 + sa + T(4) * sd;
-        const T m4 = (g1 + g3) - (g2 + g4);
-        const T m5 = (g5 + g7) - (g6 + g8);
-        const T m6 = (g3 - g1) + T(2) * ((g5 - g7) + (g8 - g6));
-        const T m7 = (g4 - g2) + T(2) * ((g5 - g7) + (g6 - g8));
-        const T m8 = T(2) * g0 - T(4) * sa + T(8) * sd;
-
-        // Guo forcing: u = (j + F/2) / rho; post-collision momentum j + F.
-        const T rho = rho0 + drho;
-        T inv_rho, sr;
-        inv_and_sqrt(rho, inv_rho, sr);
-        const T ux = (m1 + T(0.5) * Fx) * inv_rho;
-        const T uy = (m2 + T(0.5) * Fy) * inv_rho;
-        const T gam = p.gamma, hs = p.src_scale;
-        const T eq3 = T(3) * rho * (ux * ux + uy * uy);
-        const T eq4 = rho * (ux * ux - uy * uy);
-        const T eq5 = rho * ux * uy;
-        const T S3 = T(6) * (ux * Fx + uy * Fy);
-        const T S4 = T(2) * (ux * Fx - uy * Fy);
-        const T S5 = ux * Fy + uy * Fx;
-        T m3s = eq3 + gam * (m3 - eq3) + hs * S3;
-        T m4s = eq4 + gam * (m4 - eq4) + hs * S4;
-        T m5s = eq5 + gam * (m5 - eq5) + hs * S5;
-        T m6s = gam * m6, m7s = gam * m7, m8s = gam * m8;
-
-        if (p.noise) {
-            const uint32_t site = (uint32_t)x + (uint32_t)nx * (uint32_t)yr;
-            const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), p.rk);
-            const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), p.rk);
-            T z3, z4, z5, z6, z7, z8;
-            box_muller(uniform01<T>(r0.x), uniform01<T>(r0.y), z3, z4);
-            box_muller(uniform01<T>(r0.z), uniform01<T>(r0.w), z5, z6);
-            box_muller(uniform01<T>(r1.x), uniform01<T>(r1.y), z7, z8);
-            m3s += p.amp[0] * sr * z3;
-            m4s += p.amp[1] * sr * z4;
-            m5s += p.amp[2] * sr * z5;
-            m6s += p.amp[3] * sr * z6;
-            m7s += p.amp[4] * sr * z7;
-            m8s += p.amp[5] * sr * z8;
-        }
-
-        // Inverse transform: delta f_i = w_i sum_k e_ki m_k / b_k.
-        const T a0 = drho, a1 = T(3) * (m1 + Fx), a2 = T(3) * (m2 + Fy);
-        const T a3 = T(0.25) * m3s, a4 = T(2.25) * m4s, a5 = T(9) * m5s;
-        const T a6 = T(1.5) * m6s, a7 = T(1.5) * m7s, a8 = T(0.0625) * m8s;
-        const T b0 = a0 + a3 - T(4) * a8;
-        const T d0 = a0 + T(4) * a3 + T(8) * a8;
-        const T w0 = T(4.0 / 9.0), w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
-        const T f0 = w0 * (a0 - T(2) * a3 + T(2) * a8);
-        const T f1 = w1 * (b0 + a1 + a4 - a6);
-        const T f2 = w1 * (b0 + a2 - a4 - a7);
-        const T f3 = w1 * (b0 - a1 + a4 + a6);
-        const T f4 = w1 * (b0 - a2 - a4 + a7);
-        const T f5 = w2 * (d0 + a1 + a2 + a5 + T(2) * (a6 + a7));
-        const T f6 = w2 * (d0 - a1 + a2 - a5 + T(2) * (a7 - a6));
-        const T f7 = w2 * (d0 - a1 - a2 + a5 - T(2) * (a6 + a7));
-        const T f8 = w2 * (d0 + a1 - a2 - a5 + T(2) * (a6 - a7));
-
-        T *__restrict__ o = p.dst + (size_t)yr * nx + x;
-        o[0 * plane] = f0;
-        o[1 * plane] = f1;
-        o[2 * plane] = f2;
-        o[3 * plane] = f3;
-        o[4 * plane] = f4;
-        o[5 * plane] = f5;
-        o[6 * plane] = f6;
-        o[7 * plane] = f7;
-        o[8 * plane] = f8;
-        if (SAMPLE) p.drho_out[(size_t)yr * nx + x] = drho;
-        if (!isfinite(f1 + f5)) *p.flag = 1;
+        const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
+        p.dst[o] = f[0];
+        p.dst[o + pl] = f[1];
+        p.dst[o + 2u * pl] = f[2];
+        p.dst[o + 3u * pl] = f[3];
+        p.dst[o + 4u * pl] = f[4];
+        p.dst[o + 5u * pl] = f[5];
+        p.dst[o + 6u * pl] = f[6];
+        p.dst[o + 7u * pl] = f[7];
+        p.dst[o + 8u * pl] = f[8];
+        if (SAMPLE) p.drho_out[o] = sum9(q[0]);
+        if (!isfinite(f[1] + f[5])) *p.flag = 1;
     }
 }
 
@@ -281,7 +293,14 @@ static KParams<T> make_params(const StepArgs &a) {
     k.psi_b = (T)a.psi_b;
     k.psi0 = (T)a.psi0;
     k.gamma = (T)a.gamma;
-    k.src_scale = (T)a.src_scale;
+    // m3: (1-gamma) * 3 rho u^2 + hs * 6 u.F ; m4: (1-gamma) rho (ux^2-uy^2) + hs * 2 (uxFx-uyFy)
+    // m5: (1-gamma) rho ux uy + hs (ux Fy + uy Fx), hs = 1 - 1/(2 tau)
+    k.c3a = (T)(3.0 * (1.0 - a.gamma));
+    k.c3b = (T)(6.0 * a.src_scale);
+    k.c4a = (T)(1.0 - a.gamma);
+    k.c4b = (T)(2.0 * a.src_scale);
+    k.c5a = (T)(1.0 - a.gamma);
+    k.c5b = (T)a.src_scale;
     for (int i = 0; i < 6; ++i) k.amp[i] = (T)a.noise_amp[i];
     for (int i = 0; i < 20; ++i) k.rk[i] = a.round_keys[i];
     return k;
@@ -292,9 +311,9 @@ static cudaError_t launch_t(const StepArgs &a, cudaStream_t s) {
     KParams<T> k = make_params<T>(a);
     dim3 grid((a.nx + kStepTX - 1) / kStepTX, (a.ny + a.strip_h - 1) / a.strip_h);
     if (a.drho_out)
-        step_kernel<T, ORDER, true><<<grid, kStepTX, 0, s>>>(k);
+        step_kernel<T, ORDER, true><<<grid, kStepTX + 32, 0, s>>>(k);
     else
-        step_kernel<T, ORDER, false><<<grid, kStepTX, 0, s>>>(k);
+        step_kernel<T, ORDER, false><<<grid, kStepTX + 32, 0, s>>>(k);
     return cudaGetLastError();
 }
 
