@@ -52,12 +52,14 @@ def _step_kernel_traffic():
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     valid only while the kernel source is unchanged (else None)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_4096sq_fp32_E4.json")
-    src = os.path.join(ROOT, "paper_2212_07848_gb300", "csrc", "lbsc_step.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("source_sha256") != h:
+        h = hashlib.sha256()
+        for name in d["source_files"]:
+            with open(os.path.join(ROOT, "paper_2212_07848_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if d.get("source_sha256") != h.hexdigest():
             return None
         return float(d["dram_bytes_per_launch_full_size"])
     except Exception:
@@ -134,6 +136,66 @@ def cpu_baseline():
             "sample": f"{nx}x{ny} lattice, {steps} steps of the same physics (G=-5.0, "
                       f"rho0=ln2, kT=1e-6, E4, FP64) plus one direct-DFT S(k) sample; "
                       f"{dt:.1f} s"}
+
+
+def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
+    """Batched ensemble vs the plain per-replica method on the same GPU: 256
+    replicas with sides drawn from {64, 128, 256, 512}, G ~ U[-4.8, -3.6],
+    rho0 = ln2 (1 + U[-0.1, 0.1]), kT = 1e-6, S(k) every 50 steps.  The
+    ensemble runs as one launch per step (captured graphs) with an autotuned
+    strip height; the plain method steps each replica's own context in turn
+    on one stream.  Both draw the same noise, so every replica's S(k) must
+    agree."""
+    import torch
+
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    from paper_2212_07848_gb300.lattice import Lattice
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([64, 128, 256, 512], size=nrep)
+    Gs = rng.uniform(-4.8, -3.6, nrep)
+    rhos = RHO0 * (1.0 + rng.uniform(-0.1, 0.1, nrep))
+    reps = [(int(n), int(n), float(g), 1.0, 1e-6, float(r)) for n, g, r in zip(sizes, Gs, rhos)]
+    sites = sum(r[0] * r[1] for r in reps)
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    ens = Ensemble(reps, seed=seed, stream=stream_ptr)
+    ens.init(0.0)
+    ens.sk_config(50, 50)
+    strip = ens.autotune(10)
+    ens.step(50)
+    ens.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ens.step(steps)
+    b.record(stream)
+    b.synchronize()
+    ens_ms = a.elapsed_time(b)
+    lats = []
+    for r, (nx, ny, g, tau, kT, rho0) in enumerate(reps):
+        lat = Lattice(nx, ny, g, tau, kT, stream=stream_ptr)
+        lat.set_replica(r)
+        lat.init(rho0, seed, 0.0)
+        lat.sk_config(50, 50)
+        lat.step(50)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for lat in lats:
+        lat.step(steps)
+    b.record(stream)
+    b.synchronize()
+    seq_ms = a.elapsed_time(b)
+    worst = 0.0
+    for r, lat in enumerate(lats):
+        se, _ = ens.structure_factor(r)
+        sq, _ = lat.structure_factor()
+        worst = max(worst, float(np.max(np.abs(se - sq) / (np.abs(sq) + 1e-300))))
+        lat.close()
+    ens.close()
+    return {"replicas": nrep, "sites": sites, "steps": steps, "strip_h": strip,
+            "ensemble_mlups": sites * steps / (ens_ms * 1e-3) / 1e6,
+            "sequential_mlups": sites * steps / (seq_ms * 1e-3) / 1e6,
+            "speedup": seq_ms / ens_ms, "sk_max_rel_diff": worst,
+            "sizes": "uniform {64,128,256,512}^2, G~U[-4.8,-3.6], rho0=ln2(1+U[-0.1,0.1])"}
 
 
 def run_reference(args, rank, world):
@@ -256,6 +318,9 @@ def run_gpu(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_SITE * sites / (k1_ms * 1e-3) / 1e9
     cb = cpu_baseline() if (rank == 0 and world == 1) else None
+    ens = None
+    if rank == 0 and world == 1 and not args.no_ensemble:
+        ens = ensemble_leg(lat.stream())
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -281,6 +346,8 @@ def run_gpu(args, rank, world, local_rank):
         }
         if cb is not None:
             line["cpu_baseline"] = cb
+        if ens is not None:
+            line["ensemble"] = ens
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
@@ -293,6 +360,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble vs per-replica leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -68,6 +68,12 @@ extern "C" {
 #define LB_FP32 0           /* deviations from w_i rho0 stored in FP32        */
 #define LB_FP64 1           /* deviations stored in FP64                      */
 
+/* ---- step kernel selection (lb_set_kernel) -------------------------------- */
+#define LB_KERNEL_AUTO 0    /* the faster kernel for this GPU (currently plain)   */
+#define LB_KERNEL_PLAIN 1   /* pulls with coalesced global loads                  */
+#define LB_KERNEL_TMA 2     /* rows staged in shared memory by cp.async.bulk.tensor
+                               (FP32 and nx a multiple of 128 only)               */
+
 /* ---- lb_device_ptr selectors -------------------------------------------- */
 #define LB_PTR_POPULATIONS 0   /* current deviations [9][ny][nx] (T)        */
 #define LB_PTR_DENSITY_SAMPLE 1/* last sampled delta rho [ny][nx] (T)       */
@@ -86,10 +92,17 @@ typedef struct lb_params {
     int precision;       /* LB_FP32 or LB_FP64                                */
     void *stream;        /* cudaStream_t to run on, or NULL for an owned one */
     int device;          /* CUDA device ordinal, or -1 for the current one   */
+    double tau_bulk;     /* relaxation time of the bulk mode 3 (> 1/2), or 0 for tau */
+    double tau_ghost;    /* relaxation time of the ghost modes 6-8 (> 1/2), or 0 for tau;
+                            tau itself relaxes the shear modes 4-5.  All equal: the BGK
+                            collision named after Eq. (12); otherwise the
+                            multiple-relaxation-time variant with the same forcing
+                            and fluctuation-dissipation noise per mode */
 } lb_params;
 
-/* Fill *p with defaults: 128x128, G = -3.6, tau = 1, kT = 0, LB_PSI_EXP,
- * E4, LB_FP32, own stream, current device.  Returns LB_ERR_ARG if p is NULL. */
+/* Fill *p with defaults: 128x128, G = -3.6, tau = 1 (BGK: tau_bulk =
+ * tau_ghost = 0), kT = 0, LB_PSI_EXP, E4, LB_FP32, own stream, current
+ * device.  Returns LB_ERR_ARG if p is NULL. */
 int lb_params_init(lb_params *p);
 
 /* Create a lattice context (FP32 storage, own stream, current device).
@@ -123,6 +136,13 @@ int lb_set_replica(lb_ctx *h, uint32_t replica);
  * not change results. */
 int lb_set_strip_height(lb_ctx *h, int rows);
 
+/* Choose the step kernel (LB_KERNEL_*).  Both kernels perform the same
+ * arithmetic per site and give the same results; they differ only in how rows
+ * reach the SM.  LB_ERR_UNSUPPORTED if LB_KERNEL_TMA is requested for a
+ * lattice it cannot serve.  lb_get_kernel returns the kernel lb_step uses. */
+int lb_set_kernel(lb_ctx *h, int mode);
+int lb_get_kernel(const lb_ctx *h);
+
 /* Advance n >= 0 time steps of Eq. (12), asynchronously on the context
  * stream.  Sampling steps (lb_sk_config) also run the S(k) transform and
  * accumulation.  Returns the launch status (LB_ERR_CUDA if a launch failed,
@@ -131,7 +151,8 @@ int lb_set_strip_height(lb_ctx *h, int rows);
 int lb_step(lb_ctx *h, int n);
 
 /* Wait for the context stream; LB_ERR_NONFINITE if any step since the last
- * check produced a non-finite value (the flag is then cleared). */
+ * check produced a non-finite value, LB_ERR_TIMEOUT if a bounded device wait
+ * of the staged kernel ran out (the flag is then cleared). */
 int lb_sync(lb_ctx *h);
 
 /* Completed steps since lb_init (or the value given to lb_set_step). */
@@ -179,6 +200,12 @@ int lb_sk_sample_now(lb_ctx *h);
 int lb_structure_factor(lb_ctx *h, double *host_out, int nbins,
                         long long *nsamples_out);
 
+/* First moments of the mean S(k) over the full plane, k = 0 excluded:
+ * out[0] = sum_k S(k), out[1] = sum_k |k| S(k).  The characteristic domain
+ * size of a coarsening quench is L = 2 pi out[0] / out[1] (a definition of
+ * this library; the paper does not define L).  Synchronises. */
+int lb_sk_moments(lb_ctx *h, double out[2]);
+
 /* Number of full-plane modes in each radial bin of lb_structure_factor. */
 int lb_structure_factor_counts(lb_ctx *h, long long *host_counts, int nbins);
 
@@ -221,6 +248,97 @@ void *lb_stream(lb_ctx *h);
  * Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_CUDA. */
 int lb_conserved_static(const void *d_df, int precision, int nx, int ny, double rho0,
                         double *d_out3, void *stream);
+
+/* ---- batched ensembles ---------------------------------------------------
+ * Many independent periodic lattices of uneven size, coupling and density
+ * advanced together (the ensembles behind the S(k) statistics near the
+ * critical point and the spinodal, Figs. 2-3 and the simulation paragraph).
+ * One launch per step covers every replica (a tile list over all of them);
+ * runs of steps are replayed from captured CUDA graphs.  FP32 storage.
+ * Replica r draws its noise from Philox with key = seed and counter word 2 =
+ * r, so it evolves exactly like a single lattice created with the same
+ * parameters, lb_init(rho0, seed, amp) and lb_set_replica(r). */
+typedef struct lb_ens lb_ens;
+
+typedef struct lb_replica {
+    int nx, ny;          /* multiples of 4 (powers of two for S(k))          */
+    double G, tau, kT;   /* coupling, relaxation time (> 1/2), k_B theta      */
+    double rho0;         /* homogeneous initial density (> 0)                 */
+} lb_replica;
+
+/* Create an ensemble of nrep (1..65536) replicas sharing the pseudopotential
+ * and force stencil.  Memory: 2 x 9 x 4 bytes per site of every replica.
+ * Errors: LB_ERR_ARG, LB_ERR_NOMEM, LB_ERR_CUDA. */
+int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, double psi_p1,
+                  double psi_p2, int stencil, uint64_t seed, void *stream);
+void lb_ens_destroy(lb_ens *e);
+/* Every replica to rho0_r at rest plus the optional Philox kick (block 2). */
+int lb_ens_init(lb_ens *e, double init_amp);
+/* Per-replica S(k) schedule, as lb_sk_config (all sizes powers of two). */
+int lb_ens_sk_config(lb_ens *e, int sample_every, long long start_step);
+/* Rows swept per CTA for every replica (tile shape). */
+int lb_ens_set_strip_height(lb_ens *e, int rows);
+/* Time candidate strip heights on a snapshot of the state (restored after),
+ * keep the fastest, and cache it in cache_path ("key strip" lines; may be
+ * NULL).  *chosen (may be NULL) receives the strip height. */
+int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *chosen);
+/* Advance every replica n steps (asynchronous). */
+int lb_ens_step(lb_ens *e, int n);
+int lb_ens_sync(lb_ens *e);
+long long lb_ens_get_step(const lb_ens *e);
+int lb_ens_num_tiles(const lb_ens *e);
+/* Read-outs of replica r, layouts as the single-lattice calls. */
+int lb_ens_populations(lb_ens *e, int r, double *host_out);
+int lb_ens_density(lb_ens *e, int r, double *host_out);
+int lb_ens_conserved(lb_ens *e, int r, double out[3]);
+int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
+                            long long *nsamples_out);
+
+/* ---- learned surrogate building blocks ---------------------------------------
+ * A small convolutional operator advances the 4x coarse-grained density of a
+ * quench by a fixed stride; it is trained on trajectories of the solver
+ * above, which stays its reference.  The paper has no such part.  All tensors
+ * are caller-owned device buffers; activations are BF16 NHWC
+ * [nb][h][w][c] with periodic boundaries, parameters FP32 with BF16 copies.
+ * Calls are asynchronous on `stream` (cudaStream_t or NULL).
+ *
+ * 3x3 convolution on tensor cores (BF16 inputs, FP32 accumulation):
+ *   dgrad = 0: y = act(bias + conv(x, w)), w [9][cout][cin] (tap-major,
+ *              tap = 3 (dy+1) + (dx+1)), bias [cout] or NULL, act = ReLU if relu;
+ *   dgrad = 1: the input gradient dx [..][cout] of a forward layer with
+ *              weights w [9][cin][cout] from dy [..][cin] (bias NULL, relu 0).
+ * Requires w % 128 == 0 and channel counts multiples of 16. */
+int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int w_,
+                  int cin, int cout, int relu, int dgrad, void *stream);
+/* Weight and bias gradients, accumulated (+=) into FP32 dw [9][cout][cin] and
+ * dbias [cout] (may be NULL): dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n]. */
+int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
+                        int w_, int cin, int cout, void *stream);
+/* dz = dy where y > 0, else 0 (ReLU backward through the layer output y). */
+int lb_nn_relu_mask(const void *dy, const void *y, void *dz, size_t n, void *stream);
+/* 2x2 average pooling of [nb][h][w][c] (backward: spread dy/4). */
+int lb_nn_pool2(const void *x, void *y, int nb, int h, int w_, int c, int backward, void *stream);
+/* Nearest 2x upsampling of [nb][h][w][c] (backward: sum of the 2x2 block). */
+int lb_nn_up2(const void *x, void *y, int nb, int h, int w_, int c, int backward, void *stream);
+/* y = a + b elementwise (n values). */
+int lb_nn_add(const void *a, const void *b, void *y, size_t n, void *stream);
+/* Channel 0 of out [ny/f][nx/f][c] = (block mean of rho - rho0) / scale over f x f
+ * blocks of FP32 deviations df [9][ny][nx]; channel 1 = gfeat; others 0. */
+int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, double gfeat,
+                       void *out, int c, void *stream);
+/* Residual MSE on channel 0 of n pixels: *loss += mean((base + y - target)^2);
+ * dy (may be NULL) = 2 (base + y - target) / n on channel 0, 0 elsewhere. */
+int lb_nn_mse(const void *y, int c, const void *target, int ct, const void *base, int cb, size_t n,
+              float *loss, void *dy, void *stream);
+/* next channel 0 = base + y, other channels copied from base. */
+int lb_nn_residual(const void *base, const void *y, int c, void *next, int cn, size_t n,
+                   void *stream);
+/* Adam step (bias-corrected, `step` >= 1) on FP32 w with gradient g and moments
+ * m, v; w_bf16 (may be NULL) receives the BF16 copy. */
+int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_t n, double lr,
+               double b1, double b2, double eps, long long step, void *stream);
+/* BF16 copy of FP32 values. */
+int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream);
 
 /* Static message for a status code. */
 const char *lb_strerror(int code);

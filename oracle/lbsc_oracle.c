@@ -214,6 +214,9 @@ typedef struct or_params {
     double rho0;             /* reference density of the homogeneous state */
     uint64_t seed;
     uint32_t replica;
+    double tau_bulk;         /* relaxation time of mode 3 (0: tau)          */
+    double tau_ghost;        /* relaxation time of modes 6, 7, 8 (0: tau)   */
+    int force_mrt;           /* 1: use the moment-space path even for one tau */
 } or_params;
 
 /* Pseudopotential psi(n), Eq. (5) (kind 1), the a exp(-b/n) form preceding
@@ -277,6 +280,48 @@ static void collide_site(const or_params *p, uint32_t site, uint32_t t,
     double N[9] = {0};
     for (int k = 3; k < 9; ++k)
         N[k] = sqrt(mu * rho * basis_norm(k) * (1.0 - gam * gam)) * z[k];
+
+    double tb = p->tau_bulk > 0.0 ? p->tau_bulk : tau;
+    double tg = p->tau_ghost > 0.0 ? p->tau_ghost : tau;
+    if (p->force_mrt || tb != tau || tg != tau) {
+        /* Multiple relaxation times (the NEXT variant of the BGK collision):
+         * in the Hermite basis, m*_k = m_k + l_k (m_eq_k - m_k)
+         * + (1 - l_k/2) S_k + N_k with l_k = 1/tau_k per mode (mode 3: bulk,
+         * modes 4, 5: shear, modes 6, 7, 8: ghosts), S_k the moments of the
+         * Guo source, N_k = sqrt(mu rho b_k (1 - (1 - l_k)^2)) z_k. */
+        double feq[9], sg[9];
+        for (int i = 0; i < 9; ++i) {
+            double cu = CX[i] * ux + CY[i] * uy;
+            feq[i] = WQ[i] * rho *
+                     (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - usq / (2.0 * CS2));
+            double sx = (CX[i] - ux) / CS2 + cu * CX[i] / (CS2 * CS2);
+            double sy = (CY[i] - uy) / CS2 + cu * CY[i] / (CS2 * CS2);
+            sg[i] = WQ[i] * (sx * Fx + sy * Fy);
+        }
+        double mstar[9];
+        for (int k = 0; k < 9; ++k) {
+            double m = 0.0, meq = 0.0, sm = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                m += E_KI[k][i] * g[i];
+                meq += E_KI[k][i] * feq[i];
+                sm += E_KI[k][i] * sg[i];
+            }
+            double tk = (k == 3) ? tb : (k >= 6 ? tg : tau);
+            double lk = 1.0 / tk;
+            double nk = 0.0;
+            if (k >= 3) {
+                double gk = 1.0 - lk;
+                nk = sqrt(mu * rho * B_K[k] * (1.0 - gk * gk)) * z[k];
+            }
+            mstar[k] = m + lk * (meq - m) + (1.0 - 0.5 * lk) * sm + nk;
+        }
+        for (int i = 0; i < 9; ++i) {
+            double v = 0.0;
+            for (int k = 0; k < 9; ++k) v += E_KI[k][i] * mstar[k] / B_K[k];
+            out[i] = WQ[i] * v;
+        }
+        return;
+    }
 
     for (int i = 0; i < 9; ++i) {
         double cu = CX[i] * ux + CY[i] * uy;

@@ -22,6 +22,9 @@ class OrParams(C.Structure):
         ("rho0", C.c_double),
         ("seed", C.c_uint64),
         ("replica", C.c_uint32),
+        ("tau_bulk", C.c_double),
+        ("tau_ghost", C.c_double),
+        ("force_mrt", C.c_int),
     ]
 
 
@@ -112,18 +115,19 @@ def stencil(order):
 
 
 def make_params(nx, ny, G, tau, kT, psi_kind=0, psi_p1=0.0, psi_p2=0.0, stencil=4,
-                rho0=0.0, seed=0, replica=0):
+                rho0=0.0, seed=0, replica=0, tau_bulk=0.0, tau_ghost=0.0, force_mrt=0):
     return OrParams(nx, ny, G, tau, kT, psi_kind, psi_p1, psi_p2, stencil, rho0,
-                    seed, replica)
+                    seed, replica, tau_bulk, tau_ghost, force_mrt)
 
 
 class OracleLattice:
     """One periodic nx x ny lattice held by the FP64 oracle."""
 
     def __init__(self, nx, ny, G, tau, kT, psi_kind=0, stencil=4, psi_p1=0.0,
-                 psi_p2=0.0, replica=0):
+                 psi_p2=0.0, replica=0, tau_bulk=0.0, tau_ghost=0.0, force_mrt=0):
         self.p = make_params(nx, ny, G, tau, kT, psi_kind, psi_p1, psi_p2, stencil,
-                             replica=replica)
+                             replica=replica, tau_bulk=tau_bulk, tau_ghost=tau_ghost,
+                             force_mrt=force_mrt)
         self.nx, self.ny = nx, ny
         self._h = lib().or_create(C.byref(self.p))
         if not self._h:

@@ -25,6 +25,7 @@ LB_ERR_STATE = -8
 LB_PSI_EXP, LB_PSI_CRITICAL, LB_PSI_AEXP = 0, 1, 2
 LB_FP32, LB_FP64 = 0, 1
 LB_PTR_POPULATIONS, LB_PTR_DENSITY_SAMPLE, LB_PTR_SK_ACCUM = 0, 1, 2
+LB_KERNEL_AUTO, LB_KERNEL_PLAIN, LB_KERNEL_TMA = 0, 1, 2
 
 # Every function the header declares, for export checks.
 EXPORTED = [
@@ -35,6 +36,14 @@ EXPORTED = [
     "lb_sk_reset", "lb_sk_sample_now", "lb_structure_factor",
     "lb_structure_factor_counts", "lb_conserved", "lb_save", "lb_load",
     "lb_device_ptr", "lb_stream", "lb_strerror", "lb_conserved_static",
+    "lb_set_kernel", "lb_get_kernel",
+    "lb_ens_create", "lb_ens_destroy", "lb_ens_init", "lb_ens_sk_config",
+    "lb_ens_set_strip_height", "lb_ens_autotune", "lb_ens_step", "lb_ens_sync",
+    "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
+    "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments",
+    "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
+    "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
+    "lb_nn_to_bf16",
 ]
 
 
@@ -51,7 +60,13 @@ class lb_params(C.Structure):
         ("psi_kind", C.c_int), ("psi_p1", C.c_double), ("psi_p2", C.c_double),
         ("stencil", C.c_int), ("precision", C.c_int),
         ("stream", C.c_void_p), ("device", C.c_int),
+        ("tau_bulk", C.c_double), ("tau_ghost", C.c_double),
     ]
+
+
+class lb_replica(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("G", C.c_double), ("tau", C.c_double),
+                ("kT", C.c_double), ("rho0", C.c_double)]
 
 
 _lib = None
@@ -98,6 +113,7 @@ def bind(L):
         "lb_sk_sample_now": (C.c_int, [P]),
         "lb_structure_factor": (C.c_int, [P, _D, C.c_int, C.POINTER(C.c_longlong)]),
         "lb_structure_factor_counts": (C.c_int, [P, _LL, C.c_int]),
+        "lb_sk_moments": (C.c_int, [P, _D]),
         "lb_conserved": (C.c_int, [P, _D]),
         "lb_save": (C.c_int, [P, C.c_char_p]),
         "lb_load": (C.c_int, [P, C.c_char_p]),
@@ -105,6 +121,37 @@ def bind(L):
         "lb_stream": (C.c_void_p, [P]),
         "lb_strerror": (C.c_char_p, [C.c_int]),
         "lb_conserved_static": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]),
+        "lb_set_kernel": (C.c_int, [P, C.c_int]),
+        "lb_get_kernel": (C.c_int, [P]),
+        "lb_ens_create": (C.c_int, [C.POINTER(P), C.POINTER(lb_replica), C.c_int, C.c_int,
+                                    C.c_double, C.c_double, C.c_int, C.c_uint64, P]),
+        "lb_ens_destroy": (None, [P]),
+        "lb_ens_init": (C.c_int, [P, C.c_double]),
+        "lb_ens_sk_config": (C.c_int, [P, C.c_int, C.c_longlong]),
+        "lb_ens_set_strip_height": (C.c_int, [P, C.c_int]),
+        "lb_ens_autotune": (C.c_int, [P, C.c_int, C.c_char_p, C.POINTER(C.c_int)]),
+        "lb_ens_step": (C.c_int, [P, C.c_int]),
+        "lb_ens_sync": (C.c_int, [P]),
+        "lb_ens_get_step": (C.c_longlong, [P]),
+        "lb_ens_num_tiles": (C.c_int, [P]),
+        "lb_ens_populations": (C.c_int, [P, C.c_int, _D]),
+        "lb_ens_density": (C.c_int, [P, C.c_int, _D]),
+        "lb_ens_conserved": (C.c_int, [P, C.c_int, _D]),
+        "lb_ens_structure_factor": (C.c_int, [P, C.c_int, _D, C.c_int, C.POINTER(C.c_longlong)]),
+        # surrogate building blocks: device pointers, sizes, stream
+        "lb_nn_conv3x3": (C.c_int, [P, P, P, P] + [C.c_int] * 7 + [P]),
+        "lb_nn_conv3x3_wgrad": (C.c_int, [P, P, P, P] + [C.c_int] * 5 + [P]),
+        "lb_nn_relu_mask": (C.c_int, [P, P, P, C.c_size_t, P]),
+        "lb_nn_pool2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
+        "lb_nn_up2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
+        "lb_nn_add": (C.c_int, [P, P, P, C.c_size_t, P]),
+        "lb_nn_coarse_grain": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                         P, C.c_int, P]),
+        "lb_nn_mse": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, C.c_size_t, P, P, P]),
+        "lb_nn_residual": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_size_t, P]),
+        "lb_nn_adam": (C.c_int, [P, P, P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_longlong, P]),
+        "lb_nn_to_bf16": (C.c_int, [P, P, C.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -154,6 +201,14 @@ def lb_set_replica(h, replica):
 
 def lb_set_strip_height(h, rows):
     _check(load().lb_set_strip_height(h, rows), "lb_set_strip_height")
+
+
+def lb_set_kernel(h, mode):
+    _check(load().lb_set_kernel(h, int(mode)), "lb_set_kernel")
+
+
+def lb_get_kernel(h):
+    return load().lb_get_kernel(h)
 
 
 def lb_step(h, n=1):
@@ -218,6 +273,12 @@ def lb_structure_factor(h, out, nbins=0):
     return out, n.value
 
 
+def lb_sk_moments(h):
+    out = np.zeros(2)
+    _check(load().lb_sk_moments(h, out), "lb_sk_moments")
+    return out
+
+
 def lb_structure_factor_counts(h, nbins):
     out = np.zeros(nbins, np.int64)
     _check(load().lb_structure_factor_counts(h, out, int(nbins)), "lb_structure_factor_counts")
@@ -251,3 +312,77 @@ def lb_conserved_static(d_df, precision, nx, ny, rho0, d_out3, stream=None):
     caller-owned device array of 3 doubles (see include/lbsc.h)."""
     _check(load().lb_conserved_static(d_df, precision, nx, ny, rho0, d_out3, stream),
            "lb_conserved_static")
+
+
+# ---- batched ensembles -------------------------------------------------------
+def lb_ens_create(reps, psi_kind=LB_PSI_EXP, psi_p1=0.0, psi_p2=0.0, stencil=4, seed=0,
+                  stream=None):
+    """reps: sequence of (nx, ny, G, tau, kT, rho0)."""
+    arr = (lb_replica * len(reps))(*[lb_replica(*r) for r in reps])
+    h = C.c_void_p()
+    _check(load().lb_ens_create(C.byref(h), arr, len(reps), psi_kind, psi_p1, psi_p2, stencil,
+                                seed, stream), "lb_ens_create")
+    return h
+
+
+def lb_ens_destroy(h):
+    load().lb_ens_destroy(h)
+
+
+def lb_ens_init(h, init_amp=0.0):
+    _check(load().lb_ens_init(h, init_amp), "lb_ens_init")
+
+
+def lb_ens_sk_config(h, every, start):
+    _check(load().lb_ens_sk_config(h, int(every), int(start)), "lb_ens_sk_config")
+
+
+def lb_ens_set_strip_height(h, rows):
+    _check(load().lb_ens_set_strip_height(h, int(rows)), "lb_ens_set_strip_height")
+
+
+def lb_ens_autotune(h, trial_steps=20, cache_path=None):
+    c = C.c_int()
+    _check(load().lb_ens_autotune(h, int(trial_steps),
+                                  os.fsencode(cache_path) if cache_path else None, C.byref(c)),
+           "lb_ens_autotune")
+    return c.value
+
+
+def lb_ens_step(h, n=1):
+    _check(load().lb_ens_step(h, int(n)), "lb_ens_step")
+
+
+def lb_ens_sync(h):
+    _check(load().lb_ens_sync(h), "lb_ens_sync")
+
+
+def lb_ens_get_step(h):
+    return load().lb_ens_get_step(h)
+
+
+def lb_ens_num_tiles(h):
+    return load().lb_ens_num_tiles(h)
+
+
+def lb_ens_populations(h, r, out):
+    _check(load().lb_ens_populations(h, int(r), out), "lb_ens_populations")
+    return out
+
+
+def lb_ens_density(h, r, out):
+    _check(load().lb_ens_density(h, int(r), out), "lb_ens_density")
+    return out
+
+
+def lb_ens_conserved(h, r):
+    out = np.zeros(3)
+    _check(load().lb_ens_conserved(h, int(r), out), "lb_ens_conserved")
+    return out
+
+
+def lb_ens_structure_factor(h, r, out, nbins=0):
+    n = C.c_longlong()
+    _check(load().lb_ens_structure_factor(h, int(r), out, int(nbins), C.byref(n)),
+           "lb_ens_structure_factor")
+    return out, n.value

@@ -46,6 +46,8 @@ struct lb_ctx {
     uint32_t replica = 0;
     long long t = 0;
     int strip_h = 32;
+    int kernel_mode = 0;            // LB_KERNEL_*
+    TmaMaps maps;                   // tensor maps of df[0], df[1] (FP32 only)
     StepArgs base;
 };
 
@@ -77,6 +79,8 @@ int validate(const lb_params *p) {
     // 32-bit element indices in the kernels: 9 nx ny < 2^32
     if (9.0 * (double)p->nx * (double)p->ny >= 4294967296.0) return LB_ERR_ARG;
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return LB_ERR_ARG;
+    if (p->tau_bulk != 0.0 && (!(p->tau_bulk > 0.5) || !isfinite(p->tau_bulk))) return LB_ERR_ARG;
+    if (p->tau_ghost != 0.0 && (!(p->tau_ghost > 0.5) || !isfinite(p->tau_ghost))) return LB_ERR_ARG;
     if (!(p->kT >= 0.0) || !isfinite(p->kT)) return LB_ERR_ARG;
     if (!isfinite(p->G)) return LB_ERR_ARG;
     if (p->stencil != 4 && p->stencil != 6 && p->stencil != 8) return LB_ERR_ARG;
@@ -119,10 +123,14 @@ void fill_base(lb_ctx *h) {
     a.psi0 = psi_of(p, h->rho0);
     a.psi_c = p.psi_kind == LB_PSI_EXP ? exp(-h->rho0) : a.psi0;
     a.psi_b = p.psi_kind == LB_PSI_EXP ? 0.0 : p.psi_p2;
+    const double tb = p.tau_bulk > 0.0 ? p.tau_bulk : p.tau;
+    const double tg = p.tau_ghost > 0.0 ? p.tau_ghost : p.tau;
     a.gamma = 1.0 - 1.0 / p.tau;
-    a.src_scale = 1.0 - 0.5 / p.tau;
+    a.gamma_b = 1.0 - 1.0 / tb;
+    a.gamma_g = 1.0 - 1.0 / tg;
     const double mu = p.kT / kCs2;
-    for (int k = 0; k < 6; ++k) a.noise_amp[k] = sqrt(mu * kB[k] * (1.0 - a.gamma * a.gamma));
+    const double gk[6] = {a.gamma_b, a.gamma, a.gamma, a.gamma_g, a.gamma_g, a.gamma_g};
+    for (int k = 0; k < 6; ++k) a.noise_amp[k] = sqrt(mu * kB[k] * (1.0 - gk[k] * gk[k]));
     philox_round_keys(h->seed, a.round_keys);
     a.replica = h->replica;
     a.noise = p.kT > 0.0 ? 1 : 0;
@@ -264,6 +272,8 @@ int lb_create_ex(lb_ctx **out, const lb_params *p) {
         return cuda_status(e);
     }
     h->strip_h = default_strip(p->nx, p->ny);
+    if (tma_eligible(p->precision, p->nx, p->ny))
+        tma_encode_maps(&h->maps, h->df[0], h->df[1], p->nx, p->ny);
     fill_base(h);
     *out = h;
     return LB_OK;
@@ -324,11 +334,27 @@ int lb_set_strip_height(lb_ctx *h, int rows) {
     return LB_OK;
 }
 
+int lb_set_kernel(lb_ctx *h, int mode) {
+    if (!h || mode < LB_KERNEL_AUTO || mode > LB_KERNEL_TMA) return LB_ERR_ARG;
+    if (mode == LB_KERNEL_TMA && !h->maps.ok) return LB_ERR_UNSUPPORTED;
+    h->kernel_mode = mode;
+    return LB_OK;
+}
+
+int lb_get_kernel(const lb_ctx *h) {
+    if (!h) return LB_ERR_ARG;
+    // AUTO takes the plain-load kernel: on GB300 it measures faster than the
+    // staged one for this step (the step is issue-bound, and the staged
+    // kernel's per-row mbarrier hand-off costs more than the loads it saves).
+    return (h->kernel_mode == LB_KERNEL_TMA && h->maps.ok) ? LB_KERNEL_TMA : LB_KERNEL_PLAIN;
+}
+
 int lb_step(lb_ctx *h, int n) {
     if (!h || n < 0) return LB_ERR_ARG;
     if (!h->inited) return LB_ERR_STATE;
     int rc = select_device(h);
     if (rc) return rc;
+    const bool tma = lb_get_kernel(h) == LB_KERNEL_TMA;
     for (int s = 0; s < n; ++s) {
         const long long tn = h->t + 1;
         const bool sample = h->sk_every > 0 && h->acc && tn >= h->sk_start &&
@@ -338,7 +364,10 @@ int lb_step(lb_ctx *h, int n) {
         a.dst = h->df[h->cur ^ 1];
         a.drho_out = sample ? h->drho : nullptr;
         a.step = (uint32_t)h->t;
-        LB_CHECK(launch_step(h->p.precision, h->p.stencil, a, h->stream));
+        if (tma)
+            LB_CHECK(launch_step_tma(h->p.stencil, a, h->maps, h->cur, h->stream));
+        else
+            LB_CHECK(launch_step(h->p.precision, h->p.stencil, a, h->stream));
         h->cur ^= 1;
         h->t = tn;
         if (sample) {
@@ -358,7 +387,7 @@ int lb_sync(lb_ctx *h) {
     LB_CHECK(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         LB_CHECK(cudaMemset(h->d_flag, 0, sizeof(int)));
-        return LB_ERR_NONFINITE;
+        return (flag & LB_STEP_TIMEOUT) ? LB_ERR_TIMEOUT : LB_ERR_NONFINITE;
     }
     return LB_OK;
 }
@@ -535,6 +564,17 @@ int lb_structure_factor(lb_ctx *h, double *host_out, int nbins, long long *nsamp
     return lb_sync(h);
 }
 
+int lb_sk_moments(lb_ctx *h, double out[2]) {
+    if (!h || !out) return LB_ERR_ARG;
+    int rc = select_device(h);
+    if (rc) return rc;
+    if (!h->acc) return LB_ERR_STATE;
+    const double inv = h->sk_count > 0 ? 1.0 / (double)h->sk_count : 0.0;
+    LB_CHECK(launch_sk_moments(h->acc, inv, h->p.nx, h->p.ny, h->ldx, h->d_out, h->stream));
+    LB_CHECK(cudaMemcpyAsync(out, h->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return lb_sync(h);
+}
+
 int lb_structure_factor_counts(lb_ctx *h, long long *host_counts, int nbins) {
     if (!h || !host_counts || nbins <= 0 || nbins > 4096) return LB_ERR_ARG;
     const int nx = h->p.nx, ny = h->p.ny;
@@ -573,11 +613,11 @@ int lb_conserved(lb_ctx *h, double out[3]) {
 
 // ---- checkpoint -----------------------------------------------------------
 namespace {
-const char kMagic[8] = {'L', 'B', 'S', 'C', '0', '0', '0', '1'};
+const char kMagic[8] = {'L', 'B', 'S', 'C', '0', '0', '0', '2'};
 struct CkptHeader {
     char magic[8];
     int32_t nx, ny, precision, stencil, psi_kind, sk_every, has_acc, pad;
-    double G, tau, kT, p1, p2, rho0;
+    double G, tau, kT, p1, p2, rho0, tau_bulk, tau_ghost;
     uint64_t seed;
     uint32_t replica, pad2;
     int64_t t, sk_start, sk_count;
@@ -603,6 +643,8 @@ int lb_save(lb_ctx *h, const char *path) {
     hd.p1 = h->p.psi_p1;
     hd.p2 = h->p.psi_p2;
     hd.rho0 = h->rho0;
+    hd.tau_bulk = h->p.tau_bulk;
+    hd.tau_ghost = h->p.tau_ghost;
     hd.seed = h->seed;
     hd.replica = h->replica;
     hd.t = h->t;
@@ -653,6 +695,8 @@ int lb_load(lb_ctx *h, const char *path) {
     np.kT = hd.kT;
     np.psi_p1 = hd.p1;
     np.psi_p2 = hd.p2;
+    np.tau_bulk = hd.tau_bulk;
+    np.tau_ghost = hd.tau_ghost;
     if (validate(&np) != LB_OK) {
         fclose(f);
         return LB_ERR_IO;

@@ -1,0 +1,182 @@
+// Per-site arithmetic of the fused D2Q9 step shared by the step kernels:
+// kernel parameters, pull streaming from global memory, and the
+// moment-space collision with Guo forcing and Philox noise (Eq. (12)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbsc_device.cuh"
+#include "lbsc_internal.cuh"
+
+namespace lbsc {
+
+template <typename T> struct KParams {
+    const T *__restrict__ src;
+    T *__restrict__ dst;
+    T *__restrict__ drho_out;
+    int *__restrict__ flag;
+    int nx, ny, strip_h, psi_kind, noise;
+    uint32_t step, replica;
+    T rho0, force_pref, psi_c, psi_b, psi0;
+    T gamma_b, gamma, gamma_g;        // 1 - 1/tau of the bulk, shear and ghost modes
+    T c3a, c3b, c4a, c4b, c5a, c5b;   // folded relaxation/source constants
+    T amp[6];
+    uint32_t rk[20];
+};
+
+__device__ __forceinline__ int wrap_once(int a, int n) {
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// Pull streaming of one site: g_i(x) = f*_i(x - c_i).  32-bit element
+// indices (the context requires 9 nx ny < 2^32).
+template <typename T>
+__device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane_, int nx, int xc,
+                                     int xm, int xp, int yc, int ym, int yp, T g[9]) {
+    const uint32_t plane = (uint32_t)plane_;
+    const uint32_t rc = (uint32_t)yc * nx, rm = (uint32_t)ym * nx, rp = (uint32_t)yp * nx;
+    g[0] = __ldg(src + (0u * plane + rc + xc));
+    g[1] = __ldg(src + (1u * plane + rc + xm));
+    g[2] = __ldg(src + (2u * plane + rm + xc));
+    g[3] = __ldg(src + (3u * plane + rc + xp));
+    g[4] = __ldg(src + (4u * plane + rp + xc));
+    g[5] = __ldg(src + (5u * plane + rm + xm));
+    g[6] = __ldg(src + (6u * plane + rm + xp));
+    g[7] = __ldg(src + (7u * plane + rp + xp));
+    g[8] = __ldg(src + (8u * plane + rp + xm));
+}
+
+// 1/rho and sqrt(rho) from one reciprocal square root (FP32); FP64 keeps the
+// correctly rounded operations.
+__device__ __forceinline__ void inv_and_sqrt(float rho, float &inv, float &sr) {
+    const float r = rsqrtf(rho);
+    inv = r * r;
+    sr = rho * r;
+}
+__device__ __forceinline__ void inv_and_sqrt(double rho, double &inv, double &sr) {
+    inv = 1.0 / rho;
+    sr = sqrt(rho);
+}
+
+template <typename T>
+__device__ __forceinline__ T sum9(const T g[9]) {
+    return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+}
+
+// Collision of one site in the Hermite moment basis, Eq. (12):
+// moments of the pulled deviations g -> Guo velocity u = (j + F/2)/rho ->
+// relaxation of the stress modes towards rho u u with the Guo source
+// (1 - 1/2tau_k)(u F + F u) (BGK when every rate is 1/tau; bulk mode 3,
+// shear modes 4-5 and ghosts 6-8 may relax at their own rates), ghost modes
+// relaxed towards zero, momentum j + F
+// -> noise sqrt(mu rho b_k (1 - gamma^2)) z_k on modes 3..8 -> inverse
+// transform delta f_i = w_i sum_k e_ki m_k / b_k.  The inverse is factored
+// into symmetric sums and differences with the weights folded in.
+template <typename T>
+__device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<T> &p,
+                                        const uint32_t *__restrict__ rk, uint32_t site, T f[9]) {
+    // forward transform (integer coefficients, shared subexpressions)
+    const T e13 = g[1] - g[3], e24 = g[2] - g[4];
+    const T s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const T d57 = g[5] - g[7], d86 = g[8] - g[6];
+    const T s57 = g[5] + g[7], s68 = g[6] + g[8];
+    const T sa = s13 + s24, sd = s57 + s68;
+    const T drho = g[0] + (sa + sd);
+    const T t1 = d57 + d86, t2 = d57 - d86;
+    const T m1 = e13 + t1;                                   // j_x
+    const T m2 = e24 + t2;                                   // j_y
+    const T m3 = fma(T(4), sd, fma(T(-2), g[0], sa));        // 3c^2 - 2
+    const T m4 = s13 - s24;                                  // cx^2 - cy^2
+    const T m5 = s57 - s68;                                  // cx cy
+    const T m6 = fma(T(2), t1, -e13);                        // (3c^2 - 4) cx
+    const T m7 = fma(T(2), t2, -e24);                        // (3c^2 - 4) cy
+    const T m8 = fma(T(8), sd, fma(T(-4), sa, g[0] + g[0])); // 9c^4 - 15c^2 + 2
+
+    T inv_rho, sr;
+    inv_and_sqrt(p.rho0 + drho, inv_rho, sr);
+    const T jxh = fma(T(0.5), Fx, m1), jyh = fma(T(0.5), Fy, m2);   // rho u
+    const T ux = jxh * inv_rho, uy = jyh * inv_rho;
+    const T qxx = jxh * ux, qyy = jyh * uy, qxy = jxh * uy;          // rho u u
+    const T pxx = ux * Fx, pyy = uy * Fy, pxy = fma(ux, Fy, uy * Fx);
+    const T gs = p.gamma, gg = p.gamma_g;
+    T m3s = fma(p.gamma_b, m3, fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy)));
+    T m4s = fma(gs, m4, fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy)));
+    T m5s = fma(gs, m5, fma(p.c5a, qxy, p.c5b * pxy));
+    T m6s = gg * m6, m7s = gg * m7, m8s = gg * m8;
+    const T jxs = m1 + Fx, jys = m2 + Fy;
+
+    if (p.noise) {
+        const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), rk);
+        const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), rk);
+        T c, sn, rad;
+        box_muller_polar(uniform01<T>(r0.x), uniform01<T>(r0.y), rad, c, sn);
+        rad *= sr;
+        m3s = fma(p.amp[0] * rad, c, m3s);
+        m4s = fma(p.amp[1] * rad, sn, m4s);
+        box_muller_polar(uniform01<T>(r0.z), uniform01<T>(r0.w), rad, c, sn);
+        rad *= sr;
+        m5s = fma(p.amp[2] * rad, c, m5s);
+        m6s = fma(p.amp[3] * rad, sn, m6s);
+        box_muller_polar(uniform01<T>(r1.x), uniform01<T>(r1.y), rad, c, sn);
+        rad *= sr;
+        m7s = fma(p.amp[4] * rad, c, m7s);
+        m8s = fma(p.amp[5] * rad, sn, m8s);
+    }
+
+    // inverse transform
+    f[0] = fma(T(1.0 / 18.0), m8s, fma(T(-2.0 / 9.0), m3s, T(4.0 / 9.0) * drho));
+    const T B = fma(T(1.0 / 36.0), m3s - m8s, T(1.0 / 9.0) * drho);
+    const T P = fma(T(0.25), m4s, B), R = fma(T(-0.25), m4s, B);
+    const T Q = fma(T(-1.0 / 6.0), m6s, T(1.0 / 3.0) * jxs);
+    const T Sq = fma(T(-1.0 / 6.0), m7s, T(1.0 / 3.0) * jys);
+    f[1] = P + Q;
+    f[3] = P - Q;
+    f[2] = R + Sq;
+    f[4] = R - Sq;
+    const T D = fma(T(1.0 / 72.0), m8s, T(1.0 / 36.0) * (drho + m3s));
+    const T U = fma(T(0.25), m5s, D), V = fma(T(-0.25), m5s, D);
+    const T A = T(1.0 / 12.0) * (jxs + m6s), Bd = T(1.0 / 12.0) * (jys + m7s);
+    const T X = A + Bd, Y = A - Bd;
+    f[5] = U + X;
+    f[7] = U - X;
+    f[6] = V - Y;
+    f[8] = V + Y;
+}
+
+template <typename T>
+inline KParams<T> make_params(const StepArgs &a) {
+    KParams<T> k;
+    k.src = (const T *)a.src;
+    k.dst = (T *)a.dst;
+    k.drho_out = (T *)a.drho_out;
+    k.flag = a.flag;
+    k.nx = a.nx;
+    k.ny = a.ny;
+    k.strip_h = a.strip_h;
+    k.psi_kind = (int)a.psi_kind;
+    k.noise = a.noise;
+    k.step = a.step;
+    k.replica = a.replica;
+    k.rho0 = (T)a.rho0;
+    k.force_pref = (T)a.force_pref;
+    k.psi_c = (T)a.psi_c;
+    k.psi_b = (T)a.psi_b;
+    k.psi0 = (T)a.psi0;
+    k.gamma = (T)a.gamma;
+    k.gamma_b = (T)a.gamma_b;
+    k.gamma_g = (T)a.gamma_g;
+    // m3: (1-gb) 3 rho u^2 + hb 6 u.F ; m4: (1-gs) rho (ux^2-uy^2) + hs 2 (uxFx-uyFy)
+    // m5: (1-gs) rho ux uy + hs (ux Fy + uy Fx), h = (1 + gamma)/2 = 1 - 1/(2 tau)
+    k.c3a = (T)(3.0 * (1.0 - a.gamma_b));
+    k.c3b = (T)(3.0 * (1.0 + a.gamma_b));
+    k.c4a = (T)(1.0 - a.gamma);
+    k.c4b = (T)(1.0 + a.gamma);
+    k.c5a = (T)(1.0 - a.gamma);
+    k.c5b = (T)(0.5 * (1.0 + a.gamma));
+    for (int i = 0; i < 6; ++i) k.amp[i] = (T)a.noise_amp[i];
+    for (int i = 0; i < 20; ++i) k.rk[i] = a.round_keys[i];
+    return k;
+}
+
+}  // namespace lbsc

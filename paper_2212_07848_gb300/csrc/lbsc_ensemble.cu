@@ -1,0 +1,762 @@
+// Batched ensembles: many independent periodic lattices of uneven size,
+// coupling G, density rho0 (and optionally tau, kT) advanced together.
+//
+// Statistics of S(k) near the critical point and the spinodal (the scaling
+// of Figs. 2-3 of arXiv:2212.07848) need many independent realisations; one
+// small lattice cannot fill a GB300 and a launch per replica per step is
+// launch-bound.  Here every step of every replica is one launch over a tile
+// list (replica, 128-column strip, row strip) sorted largest replica first;
+// each CTA copies its replica's parameters into shared memory and runs the
+// same per-strip code as the single-lattice kernel, so a replica evolves
+// bit-identically to a single lattice with the same seed and replica index.
+// The step counter and the current-buffer index live on the device and are
+// advanced by the last CTA to finish, so a captured CUDA graph of several
+// steps can be replayed for any step range.  S(k) of all replicas is sampled
+// by batched FFT kernels over (replica, row pair) and (replica, column tile)
+// descriptors.  An autotuner times candidate strip heights on a snapshot of
+// the state and caches the choice.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbsc.h"
+#include "lbsc_fft.cuh"
+#include "lbsc_internal.cuh"
+#include "lbsc_strip.cuh"
+
+namespace lbsc {
+namespace {
+
+// Per-replica state on the device.
+struct EnsRep {
+    float *buf[2];
+    float *drho;
+    float2 *spec;
+    double *acc;
+    const float2 *tw_x, *tw_y;
+    int nx, ny, ldx, psi_kind;
+    int noise;
+    uint32_t replica;
+    float rho0, force_pref, psi_c, psi_b, psi0, gamma;
+    float c3a, c3b, c4a, c4b, c5a, c5b;
+    float amp[6];
+};   // single relaxation time per replica (BGK)
+struct EnsTile {
+    int r, x0, y0, y1;
+};
+struct EnsClock {
+    uint32_t t;
+    int cur;
+    uint32_t done;
+    uint32_t pad;
+};
+struct EnsKeys {
+    uint32_t rk[20];
+};
+
+template <int ORDER>
+__global__ void __launch_bounds__(kStepTX + 32)
+ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles, int ntiles,
+                EnsClock *clk, int *flag, const EnsKeys keys, int sk_every, long long sk_start) {
+    __shared__ KParams<float> sp;
+    __shared__ int s_sample;
+    __shared__ uint32_t s_t;
+    __shared__ int s_cur;
+    const EnsTile tile = tiles[blockIdx.x];
+    if (threadIdx.x == 0) {
+        const uint32_t t = __ldcg(&clk->t);
+        const int cur = __ldcg(&clk->cur);
+        const EnsRep &R = reps[tile.r];
+        const long long tn = (long long)t + 1;
+        const bool sample =
+            R.drho && sk_every > 0 && tn >= sk_start && (tn - sk_start) % sk_every == 0;
+        sp.src = R.buf[cur];
+        sp.dst = R.buf[cur ^ 1];
+        sp.drho_out = sample ? R.drho : nullptr;
+        sp.flag = flag;
+        sp.nx = R.nx;
+        sp.ny = R.ny;
+        sp.strip_h = tile.y1 - tile.y0;
+        sp.psi_kind = R.psi_kind;
+        sp.noise = R.noise;
+        sp.step = t;
+        sp.replica = R.replica;
+        sp.rho0 = R.rho0;
+        sp.force_pref = R.force_pref;
+        sp.psi_c = R.psi_c;
+        sp.psi_b = R.psi_b;
+        sp.psi0 = R.psi0;
+        sp.gamma = R.gamma;
+        sp.gamma_b = R.gamma;
+        sp.gamma_g = R.gamma;
+        sp.c3a = R.c3a;
+        sp.c3b = R.c3b;
+        sp.c4a = R.c4a;
+        sp.c4b = R.c4b;
+        sp.c5a = R.c5a;
+        sp.c5b = R.c5b;
+        for (int k = 0; k < 6; ++k) sp.amp[k] = R.amp[k];
+        s_sample = sample ? 1 : 0;
+        s_t = t;
+        s_cur = cur;
+    }
+    __syncthreads();
+    if (s_sample)
+        step_strip<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+    else
+        step_strip<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        // every CTA read the clock before finishing, so the last one to
+        // finish may advance it
+        if (atomicAdd(&clk->done, 1u) == (uint32_t)ntiles - 1) {
+            clk->done = 0;
+            clk->t = s_t + 1;
+            clk->cur = s_cur ^ 1;
+            __threadfence();
+        }
+    }
+}
+
+__device__ __forceinline__ int ilog2_dev(int n) { return __ffs(n) - 1; }
+
+__global__ void ens_rows_kernel(const EnsRep *__restrict__ reps, const int2 *__restrict__ desc) {
+    const int2 d = desc[blockIdx.x];
+    const EnsRep &R = reps[d.x];
+    sk_rows_block<float>(R.drho, R.spec, R.tw_x, R.nx, ilog2_dev(R.nx), R.ldx, d.y);
+}
+
+__global__ void ens_cols_kernel(const EnsRep *__restrict__ reps, const int2 *__restrict__ desc,
+                                int cpb) {
+    const int2 d = desc[blockIdx.x];
+    const EnsRep &R = reps[d.x];
+    sk_cols_block<float>(R.spec, R.acc, R.tw_y, R.nx, R.ny, ilog2_dev(R.ny), R.ldx, cpb,
+                         1.0 / ((double)R.nx * R.ny), d.y);
+}
+
+__global__ void clock_set_kernel(EnsClock *clk, uint32_t t, int cur) {
+    clk->t = t;
+    clk->cur = cur;
+    clk->done = 0;
+}
+
+constexpr double kCs2 = 1.0 / 3.0;
+constexpr double kB[6] = {4.0, 4.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 16.0};
+constexpr double kW[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                          1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace lbsc
+
+using namespace lbsc;
+
+struct lb_ens {
+    int nrep = 0, stencil = 4, psi_kind = 0, dev = 0;
+    double p1 = 0, p2 = 0;
+    uint64_t seed = 0;
+    std::vector<lb_replica> reps;
+    std::vector<EnsRep> h_reps;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    unsigned char *pool = nullptr;      // populations of every replica (two buffers)
+    unsigned char *sk_pool = nullptr;   // delta rho, spectra, accumulators, twiddles
+    EnsRep *d_reps = nullptr;
+    EnsTile *d_tiles = nullptr;
+    int ntiles = 0;
+    int2 *d_rows = nullptr, *d_cols = nullptr;
+    int nrows = 0, ncols = 0, cpb = 4, max_nx = 0, max_ny = 0;
+    EnsClock *d_clk = nullptr;
+    int *d_flag = nullptr;
+    double *d_io = nullptr, *d_partials = nullptr, *d_out = nullptr;
+    size_t io_elems = 0;
+    int nred = 0;
+    EnsKeys keys;
+    long long t = 0;
+    int cur = 0;
+    bool inited = false;
+    int strip_h = 32;
+    int sk_every = 0;
+    long long sk_start = 0, sk_count = 0;
+    cudaGraphExec_t graph_plain = nullptr;     // kGraphSteps steps, no sampling
+    cudaGraphExec_t graph_window = nullptr;    // sk_every steps, sampling at the last
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LB_OK;
+    if (e == cudaErrorMemoryAllocation) return LB_ERR_NOMEM;
+    return LB_ERR_CUDA;
+}
+#define ENS_CHECK(call)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_status(e_);   \
+    } while (0)
+
+double psi_of(int kind, double p1, double p2, double rho) {
+    switch (kind) {
+    case LB_PSI_EXP: return -expm1(-rho);
+    case LB_PSI_CRITICAL: return sqrt(p1 * p2) * exp(1.0 - p2 / rho);
+    default: return p1 * exp(-p2 / rho);
+    }
+}
+
+void fill_rep_params(lb_ens *e, int r) {
+    const lb_replica &q = e->reps[r];
+    EnsRep &R = e->h_reps[r];
+    const double gam = 1.0 - 1.0 / q.tau, hs = 1.0 - 0.5 / q.tau;
+    R.psi_kind = e->psi_kind;
+    R.noise = q.kT > 0.0 ? 1 : 0;
+    R.replica = (uint32_t)r;
+    R.rho0 = (float)q.rho0;
+    R.force_pref = (float)(-q.G * kCs2);
+    R.psi0 = (float)psi_of(e->psi_kind, e->p1, e->p2, q.rho0);
+    R.psi_c = e->psi_kind == LB_PSI_EXP ? (float)exp(-q.rho0) : R.psi0;
+    R.psi_b = e->psi_kind == LB_PSI_EXP ? 0.0f : (float)e->p2;
+    R.gamma = (float)gam;
+    R.c3a = (float)(3.0 * (1.0 - gam));
+    R.c3b = (float)(6.0 * hs);
+    R.c4a = (float)(1.0 - gam);
+    R.c4b = (float)(2.0 * hs);
+    R.c5a = (float)(1.0 - gam);
+    R.c5b = (float)hs;
+    const double mu = q.kT / kCs2;
+    for (int k = 0; k < 6; ++k) R.amp[k] = (float)sqrt(mu * kB[k] * (1.0 - gam * gam));
+}
+
+void drop_graphs(lb_ens *e) {
+    if (e->graph_plain) cudaGraphExecDestroy(e->graph_plain);
+    if (e->graph_window) cudaGraphExecDestroy(e->graph_window);
+    e->graph_plain = e->graph_window = nullptr;
+}
+
+// Tiles of 128 columns x strip rows, largest replicas first.
+int build_tiles(lb_ens *e) {
+    std::vector<EnsTile> tiles;
+    std::vector<int> order(e->nrep);
+    for (int r = 0; r < e->nrep; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long)e->reps[a].nx * e->reps[a].ny > (long)e->reps[b].nx * e->reps[b].ny;
+    });
+    for (int r : order) {
+        const int nx = e->reps[r].nx, ny = e->reps[r].ny;
+        const int h = std::min(e->strip_h, ny);
+        for (int y0 = 0; y0 < ny; y0 += h)
+            for (int x0 = 0; x0 < nx; x0 += kStepTX) tiles.push_back({r, x0, y0, std::min(y0 + h, ny)});
+    }
+    if (e->d_tiles) cudaFree(e->d_tiles);
+    e->d_tiles = nullptr;
+    ENS_CHECK(cudaMalloc(&e->d_tiles, tiles.size() * sizeof(EnsTile)));
+    ENS_CHECK(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
+                         cudaMemcpyHostToDevice));
+    e->ntiles = (int)tiles.size();
+    drop_graphs(e);
+    return LB_OK;
+}
+
+// One step of every replica; `sample` also runs the S(k) sample of all
+// replicas (the step kernel then writes delta rho: the device decides from
+// its own step counter, which agrees with the host's).
+cudaError_t launch_ens_step(lb_ens *e, bool sample) {
+    const int sk_every = sample ? e->sk_every : 0;
+    if (e->stencil == 4)
+        ens_step_kernel<4><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
+            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
+    else if (e->stencil == 6)
+        ens_step_kernel<6><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
+            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
+    else
+        ens_step_kernel<8><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
+            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || !sample) return err;
+    ens_rows_kernel<<<e->nrows, 512, (size_t)e->max_nx * sizeof(float2), e->stream>>>(e->d_reps,
+                                                                                       e->d_rows);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    ens_cols_kernel<<<e->ncols, 512, (size_t)e->cpb * e->max_ny * sizeof(float2), e->stream>>>(
+        e->d_reps, e->d_cols, e->cpb);
+    return cudaGetLastError();
+}
+
+bool is_sample_step(const lb_ens *e, long long tn) {
+    return e->sk_every > 0 && e->sk_pool && tn >= e->sk_start &&
+           (tn - e->sk_start) % e->sk_every == 0;
+}
+
+// Capture `steps` consecutive steps, the last one sampling if sample_last.
+int capture(lb_ens *e, int steps, bool sample_last, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    ENS_CHECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int s = 0; s < steps && err == cudaSuccess; ++s)
+        err = launch_ens_step(e, sample_last && s == steps - 1);
+    cudaError_t err2 = cudaStreamEndCapture(e->stream, &g);
+    if (err != cudaSuccess || err2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(err != cudaSuccess ? err : err2);
+    }
+    err = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    ENS_CHECK(err);
+    return LB_OK;
+}
+
+void free_ens(lb_ens *e) {
+    drop_graphs(e);
+    cudaFree(e->pool);
+    cudaFree(e->sk_pool);
+    cudaFree(e->d_reps);
+    cudaFree(e->d_tiles);
+    cudaFree(e->d_rows);
+    cudaFree(e->d_cols);
+    cudaFree(e->d_clk);
+    cudaFree(e->d_flag);
+    cudaFree(e->d_io);
+    cudaFree(e->d_partials);
+    cudaFree(e->d_out);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+}
+
+int rep_arg(const lb_ens *e, int r) {
+    if (!e || r < 0 || r >= e->nrep) return LB_ERR_ARG;
+    if (!e->inited) return LB_ERR_STATE;
+    return LB_OK;
+}
+
+int ens_sync(lb_ens *e) {
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    int flag = 0;
+    ENS_CHECK(cudaMemcpy(&flag, e->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        ENS_CHECK(cudaMemset(e->d_flag, 0, sizeof(int)));
+        return (flag & LB_STEP_TIMEOUT) ? LB_ERR_TIMEOUT : LB_ERR_NONFINITE;
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, double psi_p1,
+                  double psi_p2, int stencil, uint64_t seed, void *stream) {
+    if (!out || !reps || nrep < 1 || nrep > 65536) return LB_ERR_ARG;
+    *out = nullptr;
+    if (stencil != 4 && stencil != 6 && stencil != 8) return LB_ERR_ARG;
+    if (psi_kind != LB_PSI_EXP && !(psi_p1 > 0.0 && psi_p2 > 0.0)) return LB_ERR_ARG;
+    if (psi_kind < 0 || psi_kind > 2) return LB_ERR_ARG;
+    for (int r = 0; r < nrep; ++r) {
+        const lb_replica &q = reps[r];
+        if (q.nx < 4 || q.ny < 4 || q.nx % 4 || q.ny % 4) return LB_ERR_ARG;
+        if (9.0 * (double)q.nx * q.ny >= 4294967296.0) return LB_ERR_ARG;
+        if (!(q.tau > 0.5) || !(q.kT >= 0.0) || !isfinite(q.G) || !(q.rho0 > 0.0)) return LB_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return LB_ERR_CUDA;
+    lb_ens *e = new (std::nothrow) lb_ens();
+    if (!e) return LB_ERR_NOMEM;
+    cudaGetDevice(&e->dev);
+    e->nrep = nrep;
+    e->stencil = stencil;
+    e->psi_kind = psi_kind;
+    e->p1 = psi_p1;
+    e->p2 = psi_p2;
+    e->seed = seed;
+    e->reps.assign(reps, reps + nrep);
+    e->h_reps.resize(nrep);
+    philox_round_keys(seed, e->keys.rk);
+    if (stream) {
+        e->stream = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        e->own_stream = true;
+    } else {
+        delete e;
+        return LB_ERR_CUDA;
+    }
+    size_t bytes = 0, max_sites = 0;
+    std::vector<size_t> off(nrep);
+    for (int r = 0; r < nrep; ++r) {
+        const size_t n = (size_t)reps[r].nx * reps[r].ny;
+        off[r] = bytes;
+        bytes += align256(2 * 9 * n * sizeof(float));
+        max_sites = std::max(max_sites, n);
+    }
+    cudaError_t err = cudaMalloc(&e->pool, bytes);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_reps, nrep * sizeof(EnsRep));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_clk, sizeof(EnsClock));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_flag, sizeof(int));
+    e->io_elems = std::max(max_sites, (size_t)8192);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_io, e->io_elems * sizeof(double));
+    e->nred = conserved_blocks(4096, 4096);
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_partials, 3 * (size_t)e->nred * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_out, 4 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMemset(e->d_flag, 0, sizeof(int));
+    if (err != cudaSuccess) {
+        free_ens(e);
+        delete e;
+        return cuda_status(err);
+    }
+    for (int r = 0; r < nrep; ++r) {
+        EnsRep &R = e->h_reps[r];
+        memset(&R, 0, sizeof(R));
+        const size_t n = (size_t)reps[r].nx * reps[r].ny;
+        R.buf[0] = (float *)(e->pool + off[r]);
+        R.buf[1] = R.buf[0] + 9 * n;
+        R.nx = reps[r].nx;
+        R.ny = reps[r].ny;
+        fill_rep_params(e, r);
+        e->max_nx = std::max(e->max_nx, R.nx);
+        e->max_ny = std::max(e->max_ny, R.ny);
+    }
+    int rc = build_tiles(e);
+    if (rc == LB_OK && cudaMemcpy(e->d_reps, e->h_reps.data(), nrep * sizeof(EnsRep),
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = LB_ERR_CUDA;
+    if (rc != LB_OK) {
+        free_ens(e);
+        delete e;
+        return rc;
+    }
+    *out = e;
+    return LB_OK;
+}
+
+void lb_ens_destroy(lb_ens *e) {
+    if (!e) return;
+    cudaSetDevice(e->dev);
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    free_ens(e);
+    delete e;
+}
+
+int lb_ens_init(lb_ens *e, double init_amp) {
+    if (!e || !isfinite(init_amp)) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    for (int r = 0; r < e->nrep; ++r)
+        ENS_CHECK(launch_init(0, e->h_reps[r].buf[0], e->h_reps[r].nx, e->h_reps[r].ny, init_amp,
+                              e->keys.rk, (uint32_t)r, e->stream));
+    e->t = 0;
+    e->cur = 0;
+    clock_set_kernel<<<1, 1, 0, e->stream>>>(e->d_clk, 0, 0);
+    ENS_CHECK(cudaGetLastError());
+    if (e->sk_pool) {
+        for (int r = 0; r < e->nrep; ++r) {
+            const EnsRep &R = e->h_reps[r];
+            ENS_CHECK(cudaMemsetAsync(R.acc, 0, (size_t)R.ny * R.ldx * sizeof(double), e->stream));
+        }
+    }
+    e->sk_count = 0;
+    e->inited = true;
+    return LB_OK;
+}
+
+int lb_ens_sk_config(lb_ens *e, int sample_every, long long start_step) {
+    if (!e || sample_every < 0 || start_step < 0) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    if (sample_every > 0 && !e->sk_pool) {
+        for (int r = 0; r < e->nrep; ++r) {
+            const lb_replica &q = e->reps[r];
+            if (!is_pow2(q.nx) || !is_pow2(q.ny) || q.nx > 8192 || q.ny > 8192)
+                return LB_ERR_UNSUPPORTED;
+        }
+        size_t bytes = 0;
+        std::vector<size_t> o_drho(e->nrep), o_spec(e->nrep), o_acc(e->nrep), o_tx(e->nrep),
+            o_ty(e->nrep);
+        for (int r = 0; r < e->nrep; ++r) {
+            const int nx = e->reps[r].nx, ny = e->reps[r].ny, ldx = ((nx / 2 + 1) + 3) / 4 * 4;
+            e->h_reps[r].ldx = ldx;
+            o_drho[r] = bytes;
+            bytes += align256((size_t)nx * ny * sizeof(float));
+            o_spec[r] = bytes;
+            bytes += align256((size_t)ny * ldx * sizeof(float2));
+            o_acc[r] = bytes;
+            bytes += align256((size_t)ny * ldx * sizeof(double));
+            o_tx[r] = bytes;
+            bytes += align256((size_t)(nx / 2) * sizeof(float2));
+            o_ty[r] = bytes;
+            bytes += align256((size_t)(ny / 2) * sizeof(float2));
+        }
+        ENS_CHECK(cudaMalloc(&e->sk_pool, bytes));
+        ENS_CHECK(cudaMemsetAsync(e->sk_pool, 0, bytes, e->stream));
+        std::vector<int2> rows, cols;
+        const int cpb = cols_per_block(e->max_ny, sizeof(float2));
+        e->cpb = cpb;
+        for (int r = 0; r < e->nrep; ++r) {
+            EnsRep &R = e->h_reps[r];
+            R.drho = (float *)(e->sk_pool + o_drho[r]);
+            R.spec = (float2 *)(e->sk_pool + o_spec[r]);
+            R.acc = (double *)(e->sk_pool + o_acc[r]);
+            R.tw_x = (const float2 *)(e->sk_pool + o_tx[r]);
+            R.tw_y = (const float2 *)(e->sk_pool + o_ty[r]);
+            ENS_CHECK(launch_twiddles(0, (void *)R.tw_x, R.nx, e->stream));
+            ENS_CHECK(launch_twiddles(0, (void *)R.tw_y, R.ny, e->stream));
+            for (int pr = 0; pr < R.ny / 2; ++pr) rows.push_back(make_int2(r, pr));
+            for (int kx = 0; kx < R.nx / 2 + 1; kx += cpb) cols.push_back(make_int2(r, kx));
+        }
+        e->nrows = (int)rows.size();
+        e->ncols = (int)cols.size();
+        ENS_CHECK(cudaMalloc(&e->d_rows, rows.size() * sizeof(int2)));
+        ENS_CHECK(cudaMalloc(&e->d_cols, cols.size() * sizeof(int2)));
+        ENS_CHECK(cudaMemcpy(e->d_rows, rows.data(), rows.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaMemcpy(e->d_cols, cols.data(), cols.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaMemcpy(e->d_reps, e->h_reps.data(), e->nrep * sizeof(EnsRep),
+                             cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaFuncSetAttribute(ens_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)e->max_nx * sizeof(float2))));
+        ENS_CHECK(cudaFuncSetAttribute(ens_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)cpb * e->max_ny * sizeof(float2))));
+        e->sk_count = 0;
+    }
+    e->sk_every = sample_every;
+    e->sk_start = start_step;
+    drop_graphs(e);
+    return LB_OK;
+}
+
+int lb_ens_set_strip_height(lb_ens *e, int rows) {
+    if (!e || rows < 1) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    e->strip_h = rows;
+    return build_tiles(e);
+}
+
+int lb_ens_step(lb_ens *e, int n) {
+    if (!e || n < 0) return LB_ERR_ARG;
+    if (!e->inited) return LB_ERR_STATE;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    constexpr int kGraphSteps = 32;
+    const bool sk = e->sk_every > 0 && e->sk_pool;
+    while (n > 0) {
+        const long long t = e->t;
+        // a window of kGraphSteps steps with no sampling step inside
+        const bool plain_ok = n >= kGraphSteps &&
+                              (!sk || t + kGraphSteps < e->sk_start);
+        // a window t+1 .. t+every whose only sampling step is its last
+        const bool window_ok = sk && e->sk_every >= 2 && n >= e->sk_every && t >= e->sk_start &&
+                               (t - e->sk_start) % e->sk_every == 0;
+        if (plain_ok || window_ok) {
+            cudaGraphExec_t *g = plain_ok ? &e->graph_plain : &e->graph_window;
+            const int len = plain_ok ? kGraphSteps : e->sk_every;
+            if (!*g) {
+                int rc = capture(e, len, !plain_ok, g);
+                if (rc != LB_OK) return rc;
+            }
+            ENS_CHECK(cudaGraphLaunch(*g, e->stream));
+            e->t += len;
+            e->cur = (int)((e->cur + len) & 1);
+            if (!plain_ok) e->sk_count += 1;
+            n -= len;
+            continue;
+        }
+        const bool sample = is_sample_step(e, t + 1);
+        ENS_CHECK(launch_ens_step(e, sample));
+        e->t += 1;
+        e->cur ^= 1;
+        if (sample) e->sk_count += 1;
+        n -= 1;
+    }
+    return LB_OK;
+}
+
+int lb_ens_sync(lb_ens *e) {
+    if (!e) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    return ens_sync(e);
+}
+
+long long lb_ens_get_step(const lb_ens *e) { return e ? e->t : -1; }
+
+int lb_ens_num_tiles(const lb_ens *e) { return e ? e->ntiles : LB_ERR_ARG; }
+
+int lb_ens_populations(lb_ens *e, int r, double *host_out) {
+    int rc = rep_arg(e, r);
+    if (rc || !host_out) return rc ? rc : LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    const EnsRep &R = e->h_reps[r];
+    const size_t n = (size_t)R.nx * R.ny;
+    std::vector<float> tmp;
+    try {
+        tmp.resize(9 * n);
+    } catch (...) {
+        return LB_ERR_NOMEM;
+    }
+    ENS_CHECK(cudaMemcpyAsync(tmp.data(), R.buf[e->cur], 9 * n * sizeof(float),
+                              cudaMemcpyDeviceToHost, e->stream));
+    rc = ens_sync(e);
+    if (rc) return rc;
+    for (int i = 0; i < 9; ++i)
+        for (size_t s = 0; s < n; ++s) host_out[i * n + s] = kW[i] * e->reps[r].rho0 + tmp[i * n + s];
+    return LB_OK;
+}
+
+int lb_ens_density(lb_ens *e, int r, double *host_out) {
+    int rc = rep_arg(e, r);
+    if (rc || !host_out) return rc ? rc : LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    const EnsRep &R = e->h_reps[r];
+    ENS_CHECK(launch_density(0, R.buf[e->cur], e->reps[r].rho0, e->d_io, R.nx, R.ny, e->stream));
+    ENS_CHECK(cudaMemcpyAsync(host_out, e->d_io, (size_t)R.nx * R.ny * sizeof(double),
+                              cudaMemcpyDeviceToHost, e->stream));
+    return ens_sync(e);
+}
+
+int lb_ens_conserved(lb_ens *e, int r, double out[3]) {
+    int rc = rep_arg(e, r);
+    if (rc || !out) return rc ? rc : LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    const EnsRep &R = e->h_reps[r];
+    const int nb = std::min(e->nred, conserved_blocks(R.nx, R.ny));
+    ENS_CHECK(launch_conserved(0, R.buf[e->cur], e->d_partials, nb, e->d_out, R.nx, R.ny,
+                               e->stream));
+    double tmp[3];
+    ENS_CHECK(cudaMemcpyAsync(tmp, e->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+    rc = ens_sync(e);
+    if (rc) return rc;
+    out[0] = (double)R.nx * R.ny * e->reps[r].rho0 + tmp[0];
+    out[1] = tmp[1];
+    out[2] = tmp[2];
+    return LB_OK;
+}
+
+int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
+                            long long *nsamples_out) {
+    int rc = rep_arg(e, r);
+    if (rc || !host_out || nbins < 0 || nbins > 4096) return rc ? rc : LB_ERR_ARG;
+    if (!e->sk_pool) return LB_ERR_STATE;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    const EnsRep &R = e->h_reps[r];
+    const double inv = e->sk_count > 0 ? 1.0 / (double)e->sk_count : 0.0;
+    if (nbins == 0) {
+        ENS_CHECK(launch_sk_readout(R.acc, inv, e->d_io, R.nx, R.ny, R.ldx, e->stream));
+        ENS_CHECK(cudaMemcpyAsync(host_out, e->d_io, (size_t)(R.nx / 2 + 1) * R.ny * sizeof(double),
+                                  cudaMemcpyDeviceToHost, e->stream));
+        rc = ens_sync(e);
+        if (rc) return rc;
+    } else {
+        ENS_CHECK(cudaMemsetAsync(e->d_io, 0, 2 * (size_t)nbins * sizeof(double), e->stream));
+        ENS_CHECK(launch_sk_bins(R.acc, inv, e->d_io, e->d_io + nbins, nbins, R.nx, R.ny, R.ldx,
+                                 e->stream));
+        std::vector<double> tmp(2 * (size_t)nbins);
+        ENS_CHECK(cudaMemcpyAsync(tmp.data(), e->d_io, tmp.size() * sizeof(double),
+                                  cudaMemcpyDeviceToHost, e->stream));
+        rc = ens_sync(e);
+        if (rc) return rc;
+        for (int b = 0; b < nbins; ++b)
+            host_out[b] = tmp[nbins + b] > 0 ? tmp[b] / tmp[nbins + b] : NAN;
+    }
+    if (nsamples_out) *nsamples_out = e->sk_count;
+    return LB_OK;
+}
+
+// Autotuner: time each candidate strip height on a snapshot of the state and
+// keep the fastest; the state, clock and S(k) sums are restored afterwards.
+// The choice is cached in `cache_path` (one "key strip" line per ensemble
+// shape and device) when the path is not NULL.
+int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *chosen) {
+    if (!e || trial_steps < 1) return LB_ERR_ARG;
+    if (!e->inited) return LB_ERR_STATE;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    cudaDeviceProp prop;
+    ENS_CHECK(cudaGetDeviceProperties(&prop, e->dev));
+    std::string key = std::string(prop.name) + "|E" + std::to_string(e->stencil);
+    {
+        std::vector<long> sizes;
+        for (const auto &q : e->reps) sizes.push_back((long)q.nx * 100000 + q.ny);
+        std::sort(sizes.begin(), sizes.end());
+        unsigned long long h = 1469598103934665603ull;
+        for (long v : sizes) h = (h ^ (unsigned long long)v) * 1099511628211ull;
+        char buf[64];
+        snprintf(buf, sizeof(buf), "|n%d|%016llx", e->nrep, h);
+        key += buf;
+        for (auto &c : key)
+            if (c == ' ') c = '_';
+    }
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char k[512];
+            int v = 0;
+            while (fscanf(f, "%511s %d", k, &v) == 2) {
+                if (key == k && v > 0) {
+                    fclose(f);
+                    if (chosen) *chosen = v;
+                    return lb_ens_set_strip_height(e, v);
+                }
+            }
+            fclose(f);
+        }
+    }
+    // snapshot
+    size_t pool_bytes = 0;
+    for (int r = 0; r < e->nrep; ++r)
+        pool_bytes += align256(2 * 9 * (size_t)e->reps[r].nx * e->reps[r].ny * sizeof(float));
+    unsigned char *snap = nullptr;
+    ENS_CHECK(cudaMalloc(&snap, pool_bytes));
+    ENS_CHECK(cudaMemcpyAsync(snap, e->pool, pool_bytes, cudaMemcpyDeviceToDevice, e->stream));
+    const long long t0 = e->t, count0 = e->sk_count;
+    const int cur0 = e->cur, every0 = e->sk_every;
+    const int cand[] = {8, 12, 16, 24, 32, 48};
+    float best_ms = 1e30f;
+    int best = e->strip_h;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    e->sk_every = 0;
+    int rc = LB_OK;
+    for (int c : cand) {
+        if ((rc = lb_ens_set_strip_height(e, c)) != LB_OK) break;
+        for (int w = 0; w < 2 && rc == LB_OK; ++w) rc = cuda_status(launch_ens_step(e, false));
+        cudaEventRecord(a, e->stream);
+        for (int s = 0; s < trial_steps && rc == LB_OK; ++s)
+            rc = cuda_status(launch_ens_step(e, false));
+        cudaEventRecord(b, e->stream);
+        if (rc != LB_OK) break;
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    // restore
+    e->sk_every = every0;
+    ENS_CHECK(cudaMemcpyAsync(e->pool, snap, pool_bytes, cudaMemcpyDeviceToDevice, e->stream));
+    e->t = t0;
+    e->cur = cur0;
+    e->sk_count = count0;
+    clock_set_kernel<<<1, 1, 0, e->stream>>>(e->d_clk, (uint32_t)t0, cur0);
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    cudaFree(snap);
+    if (rc != LB_OK) return rc;
+    rc = lb_ens_set_strip_height(e, best);
+    if (rc != LB_OK) return rc;
+    if (chosen) *chosen = best;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %d\n", key.c_str(), best);
+            fclose(f);
+        }
+    }
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -11,13 +11,26 @@ namespace lbsc {
 // strip of kStepTX columns; each CTA sweeps strip_h rows of its strip.
 constexpr int kStepTX = 128;
 
+// Bits of the device status flag read by lb_sync.
+constexpr int LB_STEP_NONFINITE = 1;
+constexpr int LB_STEP_TIMEOUT = 2;
+
+// Opaque storage for the CUDA tensor maps (CUtensorMap, 128 bytes each) of
+// the two FP32 population buffers: row loads (136 columns x 9 planes) and
+// row stores (128 columns x 9 planes).
+struct TmaMaps {
+    alignas(64) unsigned char load[2][128];
+    alignas(64) unsigned char store[2][128];
+    bool ok = false;
+};
+
 // Parameters of one fused time step (Eq. (12) with the force of Eq. (1)).
 // Floating-point values are converted to the storage precision in the kernel.
 struct StepArgs {
     const void *src;      // deviations delta f* [9][ny][nx] at time t
     void *dst;            // deviations delta f* [9][ny][nx] at time t+1
     void *drho_out;       // delta rho [ny][nx] of the new state, or nullptr
-    int *flag;            // set to 1 when a non-finite value is produced
+    int *flag;            // LB_STEP_* bits (non-finite value, wait timeout)
     int nx, ny;
     int strip_h;          // rows swept by one CTA
     double rho0;          // reference density of the stored deviations
@@ -26,9 +39,10 @@ struct StepArgs {
     double psi_c;         // kind 0: exp(-rho0); kinds 1, 2: psi(rho0)
     double psi_b;         // kinds 1, 2: b (nc or b); unused for kind 0
     double psi0;          // psi(rho0)
-    double gamma;         // 1 - 1/tau
-    double src_scale;     // (1 + gamma) / 2 = 1 - 1/(2 tau)
-    double noise_amp[6];  // sqrt(mu b_k (1 - gamma^2)), k = 3..8 (times sqrt(rho))
+    double gamma;         // 1 - 1/tau of the shear modes 4, 5
+    double gamma_b;       // 1 - 1/tau_bulk of mode 3
+    double gamma_g;       // 1 - 1/tau_ghost of modes 6, 7, 8
+    double noise_amp[6];  // sqrt(mu b_k (1 - gamma_k^2)), k = 3..8 (times sqrt(rho))
     uint32_t round_keys[20];  // Philox4x32-10 key schedule (k0, k1) per round
     uint32_t step;        // counter word 1: number of completed steps
     uint32_t replica;     // counter word 2
@@ -46,6 +60,11 @@ struct SkArgs {
 };
 
 cudaError_t launch_step(int precision, int stencil, const StepArgs &a, cudaStream_t s);
+bool tma_eligible(int precision, int nx, int ny);
+bool tma_encode_maps(TmaMaps *m, void *buf0, void *buf1, int nx, int ny);
+// src_buf: index (0/1) of the buffer holding the current state.
+cudaError_t launch_step_tma(int stencil, const StepArgs &a, const TmaMaps &m, int src_buf,
+                            cudaStream_t s);
 cudaError_t launch_init(int precision, void *df, int nx, int ny, double amp,
                         const uint32_t round_keys[20], uint32_t replica, cudaStream_t s);
 cudaError_t launch_density(int precision, const void *df, double rho0, double *out,
@@ -58,6 +77,8 @@ cudaError_t launch_sk_readout(const double *acc, double inv_count, double *out, 
                               int ny, int ldx, cudaStream_t s);
 cudaError_t launch_sk_bins(const double *acc, double inv_count, double *bins, double *counts,
                            int nbins, int nx, int ny, int ldx, cudaStream_t s);
+cudaError_t launch_sk_moments(const double *acc, double inv_count, int nx, int ny, int ldx,
+                              double *out2, cudaStream_t s);
 cudaError_t launch_conserved(int precision, const void *df, double *partials, int nblocks,
                              double *out3, int nx, int ny, cudaStream_t s);
 int conserved_blocks(int nx, int ny);

@@ -1,0 +1,524 @@
+// Learned surrogate building blocks: BF16 tensor-core 3x3 convolutions on
+// periodic NHWC fields (forward, input gradient, weight gradient) with FP32
+// accumulation, and the elementwise pieces of a small convolutional
+// operator (pooling, upsampling, skip sums, ReLU mask, coarse-graining of the
+// lattice density, MSE loss, Adam).  The surrogate advances the coarse
+// density of a quench by a fixed stride; the plain lattice Boltzmann step
+// stays the reference it is judged against.
+//
+// Convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16 in, FP32
+// accumulate): M = output pixels (a 128-pixel row segment per CTA), N =
+// output channels, K = 9 taps x input channels; the im2col tile is gathered
+// with circular (periodic) padding straight from NHWC into shared memory.
+// The input gradient is the same kernel run on dY with the taps mirrored and
+// the weight matrix transposed; the weight gradient is a GEMM over pixels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lbsc.h"
+
+namespace lbsc {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// ---------------------------------------------------------------------------
+// Forward / input-gradient convolution.
+//   forward: y[p][n] = act( bias[n] + sum_{tap, c} x[p + off(tap)][c] w[tap][n][c] )
+//   dgrad  : dx[p][c] = sum_{tap, n} dy[p + off(tap)][n] w[8 - tap][n][c]
+// CTA: 128 pixels (a row segment) x BN channels; 4 warps, each 32 pixels x BN.
+// ---------------------------------------------------------------------------
+template <int BN, int BK, bool DGRAD>
+__global__ void __launch_bounds__(128)
+conv3x3_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w, const float *__restrict__ bias,
+               bf16 *__restrict__ y, int H, int W, int Cin, int Cout, int relu) {
+    // GEMM view: K = 9 * Kc (Kc = channels of x), N = Nc (channels of y)
+    constexpr int P = BK + 8;                      // smem row pitch (elements)
+    __shared__ __align__(16) bf16 As[128 * P];
+    __shared__ __align__(16) bf16 Bs[BN * P];
+    const int Kc = Cin, Nc = Cout;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int x0 = blockIdx.x * 128;
+    const int yrow = blockIdx.y % H, b = blockIdx.y / H;
+    const int n0 = blockIdx.z * BN;
+    const size_t img = (size_t)b * H * W;
+
+    float acc[2][BN / 8][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const int ys = wrapi(yrow + dy, H);
+        for (int c0 = 0; c0 < Kc; c0 += BK) {
+            // A: 128 pixels x BK channels, 16-byte vectors (8 bf16)
+            constexpr int AV = 128 * BK / 8;
+            for (int v = tid; v < AV; v += 128) {
+                const int px = v / (BK / 8), cv = v % (BK / 8);
+                const int xs = wrapi(x0 + px + dx, W);
+                const uint4 val = *reinterpret_cast<const uint4 *>(
+                    x + (img + (size_t)ys * W + xs) * Kc + c0 + cv * 8);
+                *reinterpret_cast<uint4 *>(&As[px * P + cv * 8]) = val;
+            }
+            // B: BN output channels x BK input channels
+            if (!DGRAD) {
+                constexpr int BV = BN * BK / 8;
+                for (int v = tid; v < BV; v += 128) {
+                    const int nn = v / (BK / 8), cv = v % (BK / 8);
+                    const uint4 val = *reinterpret_cast<const uint4 *>(
+                        w + ((size_t)tap * Nc + n0 + nn) * Kc + c0 + cv * 8);
+                    *reinterpret_cast<uint4 *>(&Bs[nn * P + cv * 8]) = val;
+                }
+            } else {
+                // w is [9][Kc][Nc] of the forward layer (Kc = its Cout, Nc = its Cin):
+                // B[nn][kk] = w[8 - tap][kk][nn]
+                for (int e = tid; e < BN * BK; e += 128) {
+                    const int kk = e / BN, nn = e % BN;
+                    Bs[nn * P + kk] = w[((size_t)(8 - tap) * Kc + c0 + kk) * Nc + n0 + nn];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                uint32_t af[2][4];
+#pragma unroll
+                for (int mi = 0; mi < 2; ++mi) {
+                    const int r = warp * 32 + mi * 16 + g;
+                    const int k = ks * 16 + 2 * t;
+                    af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r * P + k]);
+                    af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k]);
+                    af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r * P + k + 8]);
+                    af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k + 8]);
+                }
+#pragma unroll
+                for (int ni = 0; ni < BN / 8; ++ni) {
+                    const int nn = ni * 8 + g;
+                    const int k = ks * 16 + 2 * t;
+                    uint32_t bfr[2];
+                    bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[nn * P + k]);
+                    bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[nn * P + k + 8]);
+#pragma unroll
+                    for (int mi = 0; mi < 2; ++mi) mma_bf16_16816(acc[mi][ni], af[mi], bfr);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue: bias, ReLU, BF16 store (channel pairs)
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < BN / 8; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int px = warp * 32 + mi * 16 + g + h * 8;
+                const int n = n0 + ni * 8 + 2 * t;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (bias) {
+                    v0 += bias[n];
+                    v1 += bias[n + 1];
+                }
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                *reinterpret_cast<__nv_bfloat162 *>(
+                    y + (img + (size_t)yrow * W + x0 + px) * Nc + n) = __floats2bfloat162_rn(v0, v1);
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n]
+// GEMM: M = n (16-row tiles of Cout), N = c, K = pixels (chunks of 32).
+// CTA: one tap, 64 n x 64 c (or less), `chunk` pixels; 4 warps, warp w
+// takes n rows [16 w, 16 w + 16).
+// ---------------------------------------------------------------------------
+template <int BMN, int BNC>
+__global__ void __launch_bounds__(128)
+wgrad_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ dy, float *__restrict__ dw,
+             int NB, int H, int W, int Cin, int Cout, int chunk) {
+    constexpr int BK = 32, P = BK + 8;
+    __shared__ __align__(16) bf16 As[BMN * P];    // [n][p]
+    __shared__ __align__(16) bf16 Bs[BNC * P];    // [c][p]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int tap = blockIdx.y % 9;
+    const int ntile = blockIdx.y / 9;
+    const int n0 = (ntile % (Cout / BMN)) * BMN;
+    const int c0 = (ntile / (Cout / BMN)) * BNC;
+    const int dyy = tap / 3 - 1, dxx = tap % 3 - 1;
+    const size_t P0 = (size_t)blockIdx.x * chunk;
+    const size_t Ptot = (size_t)NB * H * W;
+    constexpr int MT = BMN / 16 / 4 > 0 ? BMN / 16 / 4 : 1;   // m16 tiles per warp
+    float acc[MT][BNC / 8][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < BNC / 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int warps_m = BMN / 16 < 4 ? BMN / 16 : 4;
+
+    for (int kp0 = 0; kp0 < chunk; kp0 += BK) {
+        for (int e = tid; e < BK * BMN; e += 128) {
+            const int kp = e / BMN, nn = e % BMN;
+            const size_t p = P0 + kp0 + kp;
+            As[nn * P + kp] = p < Ptot ? dy[p * Cout + n0 + nn] : __float2bfloat16(0.f);
+        }
+        for (int e = tid; e < BK * BNC; e += 128) {
+            const int kp = e / BNC, cc = e % BNC;
+            const size_t p = P0 + kp0 + kp;
+            bf16 v = __float2bfloat16(0.f);
+            if (p < Ptot) {
+                const size_t bimg = p / ((size_t)H * W);
+                const int rem = (int)(p % ((size_t)H * W));
+                const int yy = wrapi(rem / W + dyy, H), xx = wrapi(rem % W + dxx, W);
+                v = x[((bimg * H + yy) * W + xx) * Cin + c0 + cc];
+            }
+            Bs[cc * P + kp] = v;
+        }
+        __syncthreads();
+        if (warp < warps_m) {
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+                for (int mi = 0; mi < MT; ++mi) {
+                    const int r = (warp + mi * 4) * 16 + g;
+                    const int k = ks * 16 + 2 * t;
+                    uint32_t af[4];
+                    af[0] = *reinterpret_cast<const uint32_t *>(&As[r * P + k]);
+                    af[1] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k]);
+                    af[2] = *reinterpret_cast<const uint32_t *>(&As[r * P + k + 8]);
+                    af[3] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k + 8]);
+#pragma unroll
+                    for (int ni = 0; ni < BNC / 8; ++ni) {
+                        const int cc = ni * 8 + g;
+                        uint32_t bfr[2];
+                        bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[cc * P + k]);
+                        bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[cc * P + k + 8]);
+                        mma_bf16_16816(acc[mi][ni], af, bfr);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (warp < warps_m) {
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < BNC / 8; ++ni)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int n = n0 + (warp + mi * 4) * 16 + g + h * 8;
+                    const int c = c0 + ni * 8 + 2 * t;
+                    float *d = dw + ((size_t)tap * Cout + n) * Cin + c;
+                    atomicAdd(d, acc[mi][ni][2 * h]);
+                    atomicAdd(d + 1, acc[mi][ni][2 * h + 1]);
+                }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise pieces (NHWC BF16 activations, FP32 parameters and losses).
+// ---------------------------------------------------------------------------
+#define GRID_STRIDE(i, n) \
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+__global__ void bias_grad_kernel(const bf16 *__restrict__ dy, float *__restrict__ db, size_t P, int C) {
+    // one block per channel group of 32; threads stride over pixels
+    const int c = blockIdx.y * 32 + (threadIdx.x & 31);
+    if (c >= C) return;
+    float s = 0.f;
+    for (size_t p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; p < P;
+         p += (size_t)gridDim.x * (blockDim.x / 32))
+        s += __bfloat162float(dy[p * C + c]);
+    atomicAdd(&db[c], s);
+}
+
+__global__ void relu_mask_kernel(const bf16 *__restrict__ dy, const bf16 *__restrict__ y,
+                                 bf16 *__restrict__ dz, size_t n) {
+    GRID_STRIDE(i, n) dz[i] = __bfloat162float(y[i]) > 0.f ? dy[i] : __float2bfloat16(0.f);
+}
+
+__global__ void pool2_fwd_kernel(const bf16 *__restrict__ x, bf16 *__restrict__ y, int NB, int H,
+                                 int W, int C) {
+    const int h = H / 2, w = W / 2;
+    GRID_STRIDE(i, (size_t)NB * h * w * C) {
+        const int c = (int)(i % C);
+        size_t r = i / C;
+        const int X = (int)(r % w), Y = (int)((r / w) % h), b = (int)(r / ((size_t)w * h));
+        const size_t base = (((size_t)b * H + 2 * Y) * W + 2 * X) * C + c;
+        const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + C]) +
+                        __bfloat162float(x[base + (size_t)W * C]) +
+                        __bfloat162float(x[base + (size_t)W * C + C]);
+        y[i] = __float2bfloat16(0.25f * s);
+    }
+}
+
+__global__ void pool2_bwd_kernel(const bf16 *__restrict__ dy, bf16 *__restrict__ dx, int NB, int H,
+                                 int W, int C) {
+    GRID_STRIDE(i, (size_t)NB * H * W * C) {
+        const int c = (int)(i % C);
+        size_t r = i / C;
+        const int x = (int)(r % W), yy = (int)((r / W) % H), b = (int)(r / ((size_t)W * H));
+        dx[i] = __float2bfloat16(
+            0.25f * __bfloat162float(dy[(((size_t)b * (H / 2) + yy / 2) * (W / 2) + x / 2) * C + c]));
+    }
+}
+
+__global__ void up2_fwd_kernel(const bf16 *__restrict__ x, bf16 *__restrict__ y, int NB, int H,
+                               int W, int C) {
+    // x: [NB][H][W][C] -> y: [NB][2H][2W][C]
+    GRID_STRIDE(i, (size_t)NB * 4 * H * W * C) {
+        const int c = (int)(i % C);
+        size_t r = i / C;
+        const int X = (int)(r % (2 * W)), Y = (int)((r / (2 * W)) % (2 * H)),
+                  b = (int)(r / ((size_t)4 * W * H));
+        y[i] = x[(((size_t)b * H + Y / 2) * W + X / 2) * C + c];
+    }
+}
+
+__global__ void up2_bwd_kernel(const bf16 *__restrict__ dy, bf16 *__restrict__ dx, int NB, int H,
+                               int W, int C) {
+    // dy: [NB][2H][2W][C] -> dx: [NB][H][W][C]
+    GRID_STRIDE(i, (size_t)NB * H * W * C) {
+        const int c = (int)(i % C);
+        size_t r = i / C;
+        const int x = (int)(r % W), yy = (int)((r / W) % H), b = (int)(r / ((size_t)W * H));
+        const size_t base = (((size_t)b * 2 * H + 2 * yy) * 2 * W + 2 * x) * C + c;
+        const size_t row = (size_t)2 * W * C;
+        dx[i] = __float2bfloat16(__bfloat162float(dy[base]) + __bfloat162float(dy[base + C]) +
+                                 __bfloat162float(dy[base + row]) +
+                                 __bfloat162float(dy[base + row + C]));
+    }
+}
+
+__global__ void add_kernel(const bf16 *__restrict__ a, const bf16 *__restrict__ b,
+                           bf16 *__restrict__ y, size_t n) {
+    GRID_STRIDE(i, n) y[i] = __float2bfloat16(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+// Coarse-grain the density of a lattice state (FP32 deviations [9][ny][nx])
+// by f x f block averages into channel 0 of an NHWC BF16 field [ny/f][nx/f][C]:
+// (rho - rho0) / scale; channel 1 = gfeat; channels 2.. = 0.
+__global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int f, float scale,
+                              float gfeat, bf16 *__restrict__ out, int C) {
+    const int cx = nx / f, cy = ny / f;
+    const size_t plane = (size_t)nx * ny;
+    GRID_STRIDE(i, (size_t)cx * cy) {
+        const int X = (int)(i % cx), Y = (int)(i / cx);
+        float s = 0.f;
+        for (int yy = 0; yy < f; ++yy)
+            for (int xx = 0; xx < f; ++xx) {
+                const size_t site = (size_t)(Y * f + yy) * nx + X * f + xx;
+                float d = 0.f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) d += df[k * plane + site];
+                s += d;
+            }
+        bf16 *o = out + i * C;
+        o[0] = __float2bfloat16(s / (f * f) / scale);
+        if (C > 1) o[1] = __float2bfloat16(gfeat);
+        for (int c = 2; c < C; ++c) o[c] = __float2bfloat16(0.f);
+    }
+}
+
+// MSE over channel 0 of an [n][C] field against a [n][Ct] target channel 0:
+// loss += sum (y - t)^2 / n (FP32 atomics), dy = 2 (y - t) / n on channel 0.
+__global__ void mse_kernel(const bf16 *__restrict__ y, int C, const bf16 *__restrict__ tgt, int Ct,
+                           const bf16 *__restrict__ base, int Cb, size_t n, float *__restrict__ loss,
+                           bf16 *__restrict__ dy) {
+    float s = 0.f;
+    GRID_STRIDE(i, n) {
+        // prediction = base + y (residual), target = tgt
+        const float pred = __bfloat162float(base[i * Cb]) + __bfloat162float(y[i * C]);
+        const float d = pred - __bfloat162float(tgt[i * Ct]);
+        s += d * d;
+        if (dy) {
+            dy[i * C] = __float2bfloat16(2.f * d / (float)n);
+            for (int c = 1; c < C; ++c) dy[i * C + c] = __float2bfloat16(0.f);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
+}
+
+// next = base + y (channel 0), other channels copied from base (the rollout input)
+__global__ void residual_kernel(const bf16 *__restrict__ base, const bf16 *__restrict__ y, int C,
+                                bf16 *__restrict__ next, int Cn, size_t n) {
+    GRID_STRIDE(i, n) {
+        next[i * Cn] = __float2bfloat16(__bfloat162float(base[i * Cn]) + __bfloat162float(y[i * C]));
+        for (int c = 1; c < Cn; ++c) next[i * Cn + c] = base[i * Cn + c];
+    }
+}
+
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, bf16 *__restrict__ wb, size_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    GRID_STRIDE(i, n) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void f2bf_kernel(const float *__restrict__ a, bf16 *__restrict__ b, size_t n) {
+    GRID_STRIDE(i, n) b[i] = __float2bfloat16(a[i]);
+}
+
+int blocks_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 152 * 32 ? b : 152 * 32);
+}
+
+}  // namespace
+}  // namespace lbsc
+
+using namespace lbsc;
+
+#define NN_RET() return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA
+
+extern "C" {
+
+int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int wd,
+                  int cin, int cout, int relu, int dgrad, void *stream) {
+    if (!x || !w || !y || nb < 1 || h < 1 || wd < 128 || wd % 128 || cin % 16 || cout % 16 ||
+        cin < 16 || cout < 16)
+        return LB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // GEMM K channels = channels of the kernel's input, N = of its output
+    dim3 grid(wd / 128, h * nb, 1);
+    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
+    bf16 *yb = (bf16 *)y;
+    const int bn = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
+    grid.z = cout / bn;
+    const bool k32 = cin % 32 == 0;
+#define LAUNCH(BN, BK, DG) \
+    conv3x3_kernel<BN, BK, DG><<<grid, 128, 0, s>>>(xb, wb, bias, yb, h, wd, cin, cout, relu)
+    if (!dgrad) {
+        if (bn == 64) { if (k32) LAUNCH(64, 32, false); else LAUNCH(64, 16, false); }
+        else if (bn == 32) { if (k32) LAUNCH(32, 32, false); else LAUNCH(32, 16, false); }
+        else { if (k32) LAUNCH(16, 32, false); else LAUNCH(16, 16, false); }
+    } else {
+        if (bias || relu) return LB_ERR_ARG;
+        if (bn == 64) { if (k32) LAUNCH(64, 32, true); else LAUNCH(64, 16, true); }
+        else if (bn == 32) { if (k32) LAUNCH(32, 32, true); else LAUNCH(32, 16, true); }
+        else { if (k32) LAUNCH(16, 32, true); else LAUNCH(16, 16, true); }
+    }
+#undef LAUNCH
+    NN_RET();
+}
+
+int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
+                        int wd, int cin, int cout, void *stream) {
+    if (!x || !dy || !dw || nb < 1 || h < 1 || wd < 1 || cin % 16 || cout % 16) return LB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t P = (size_t)nb * h * wd;
+    const int chunk = 2048;
+    const int bm = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
+    const int bc = cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16);
+    dim3 grid((unsigned)((P + chunk - 1) / chunk), 9 * (cout / bm) * (cin / bc));
+    const bf16 *xb = (const bf16 *)x, *db = (const bf16 *)dy;
+#define WG(BM, BC) wgrad_kernel<BM, BC><<<grid, 128, 0, s>>>(xb, db, dw, nb, h, wd, cin, cout, chunk)
+    if (bm == 64) { if (bc == 64) WG(64, 64); else if (bc == 32) WG(64, 32); else WG(64, 16); }
+    else if (bm == 32) { if (bc == 64) WG(32, 64); else if (bc == 32) WG(32, 32); else WG(32, 16); }
+    else { if (bc == 64) WG(16, 64); else if (bc == 32) WG(16, 32); else WG(16, 16); }
+#undef WG
+    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    if (dbias) {
+        dim3 gb(256, (cout + 31) / 32);
+        bias_grad_kernel<<<gb, 256, 0, s>>>(db, dbias, P, cout);
+    }
+    NN_RET();
+}
+
+int lb_nn_relu_mask(const void *dy, const void *y, void *dz, size_t n, void *stream) {
+    relu_mask_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)dy, (const bf16 *)y, (bf16 *)dz, n);
+    NN_RET();
+}
+
+int lb_nn_pool2(const void *x, void *y, int nb, int h, int w, int c, int backward, void *stream) {
+    if (h % 2 || w % 2) return LB_ERR_ARG;
+    const size_t n = backward ? (size_t)nb * h * w * c : (size_t)nb * (h / 2) * (w / 2) * c;
+    if (!backward)
+        pool2_fwd_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, nb, h, w, c);
+    else
+        pool2_bwd_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, nb, h, w, c);
+    NN_RET();
+}
+
+int lb_nn_up2(const void *x, void *y, int nb, int h, int w, int c, int backward, void *stream) {
+    // (h, w): the coarse size
+    const size_t n = backward ? (size_t)nb * h * w * c : (size_t)nb * 4 * h * w * c;
+    if (!backward)
+        up2_fwd_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, nb, h, w, c);
+    else
+        up2_bwd_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16 *)x, (bf16 *)y, nb, h, w, c);
+    NN_RET();
+}
+
+int lb_nn_add(const void *a, const void *b, void *y, size_t n, void *stream) {
+    add_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>((const bf16 *)a, (const bf16 *)b, (bf16 *)y, n);
+    NN_RET();
+}
+
+int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, double gfeat, void *out,
+                       int c, void *stream) {
+    if (!df || !out || f < 1 || nx % f || ny % f || c < 1) return LB_ERR_ARG;
+    coarse_kernel<<<blocks_for((size_t)(nx / f) * (ny / f)), 256, 0, (cudaStream_t)stream>>>(
+        df, nx, ny, f, (float)scale, (float)gfeat, (bf16 *)out, c);
+    NN_RET();
+}
+
+int lb_nn_mse(const void *y, int c, const void *target, int ct, const void *base, int cb, size_t n,
+              float *loss, void *dy, void *stream) {
+    mse_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)y, c, (const bf16 *)target, ct, (const bf16 *)base, cb, n, loss, (bf16 *)dy);
+    NN_RET();
+}
+
+int lb_nn_residual(const void *base, const void *y, int c, void *next, int cn, size_t n, void *stream) {
+    residual_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)base, (const bf16 *)y, c, (bf16 *)next, cn, n);
+    NN_RET();
+}
+
+int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_t n, double lr,
+               double b1, double b2, double eps, long long step, void *stream) {
+    const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
+    adam_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (bf16 *)w_bf16, n,
+                                                                 (float)lr, (float)b1, (float)b2,
+                                                                 (float)eps, c1, c2);
+    NN_RET();
+}
+
+int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream) {
+    f2bf_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(a, (bf16 *)b, n);
+    NN_RET();
+}
+
+}  // extern "C"

@@ -11,54 +11,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "lbsc_fft.cuh"
 #include "lbsc_internal.cuh"
 
 namespace lbsc {
-
-template <typename T> struct C2;
-template <> struct C2<float> { using t = float2; };
-template <> struct C2<double> { using t = double2; };
-
-template <typename CT>
-__device__ __forceinline__ CT cmul(CT a, CT b) {
-    CT r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-
-static inline int ilog2(int n) {
-    int l = 0;
-    while ((1 << l) < n) ++l;
-    return l;
-}
-
-// In-place radix-2 DIT over `nfft` independent transforms of length n stored
-// contiguously in shared memory (input already in bit-reversed order).
-template <typename CT>
-__device__ void fft_smem(CT *s, int n, int log2n, int nfft, const CT *__restrict__ tw) {
-    const int half = n >> 1;
-    const int total = nfft * half;
-    for (int l = 0; l < log2n; ++l) {
-        const int m = 1 << l;                 // half-size of the butterflies
-        const int stride = half >> l;         // twiddle index stride: n / (2m)
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int f = b / half;
-            const int t = b - f * half;
-            const int j = t & (m - 1);
-            const int base = f * n + ((t >> l) << (l + 1)) + j;
-            const CT w = tw[j * stride];
-            const CT u = s[base];
-            const CT v = cmul(s[base + m], w);
-            CT a, c;
-            a.x = u.x + v.x; a.y = u.y + v.y;
-            c.x = u.x - v.x; c.y = u.y - v.y;
-            s[base] = a;
-            s[base + m] = c;
-        }
-        __syncthreads();
-    }
-}
 
 // Twiddles e^{-2 pi i m / n}, m < n/2, evaluated in FP64.
 template <typename T>
@@ -82,80 +38,18 @@ cudaError_t launch_twiddles(int precision, void *tw, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Row pass: block b transforms rows 2b and 2b+1 packed as z = a + i b and
-// separates X_a(k) = (Z(k) + conj Z(n-k)) / 2, X_b(k) = (Z(k) - conj Z(n-k)) / 2i.
 template <typename T>
 __global__ void sk_rows_kernel(const T *__restrict__ drho, typename C2<T>::t *__restrict__ spec,
                                const typename C2<T>::t *__restrict__ tw, int nx, int log2nx,
                                int ldx) {
-    using CT = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CT *s = reinterpret_cast<CT *>(smem_raw);
-    const int ya = 2 * blockIdx.x, yb = ya + 1;
-    const T *ra = drho + (size_t)ya * nx;
-    const T *rb = drho + (size_t)yb * nx;
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        CT v;
-        v.x = ra[j];
-        v.y = rb[j];
-        s[__brev((unsigned)j) >> (32 - log2nx)] = v;
-    }
-    __syncthreads();
-    fft_smem<CT>(s, nx, log2nx, 1, tw);
-    CT *oa = spec + (size_t)ya * ldx;
-    CT *ob = spec + (size_t)yb * ldx;
-    for (int k = threadIdx.x; k <= nx / 2; k += blockDim.x) {
-        const CT z = s[k];
-        const CT zc = s[(nx - k) & (nx - 1)];
-        CT xa, xb;
-        xa.x = T(0.5) * (z.x + zc.x);
-        xa.y = T(0.5) * (z.y - zc.y);
-        // (z - conj(zc)) / (2i) = -(i/2) (z - conj(zc))
-        xb.x = T(0.5) * (z.y + zc.y);
-        xb.y = T(-0.5) * (z.x - zc.x);
-        oa[k] = xa;
-        ob[k] = xb;
-    }
+    sk_rows_block<T>(drho, spec, tw, nx, log2nx, ldx, blockIdx.x);
 }
 
-// Column pass: block b transforms columns kx0 .. kx0+cpb-1 (length ny) and
-// accumulates |X|^2 / N.
 template <typename T>
 __global__ void sk_cols_kernel(const typename C2<T>::t *__restrict__ spec, double *__restrict__ acc,
                                const typename C2<T>::t *__restrict__ tw, int nx, int ny,
                                int log2ny, int ldx, int cpb, double inv_n) {
-    using CT = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CT *s = reinterpret_cast<CT *>(smem_raw);
-    const int hx = nx / 2 + 1;
-    const int kx0 = blockIdx.x * cpb;
-    const int total = cpb * ny;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e % cpb, y = e / cpb;
-        CT v;
-        if (kx0 + c < hx) {
-            v = spec[(size_t)y * ldx + kx0 + c];
-        } else {
-            v.x = T(0);
-            v.y = T(0);
-        }
-        s[c * ny + (__brev((unsigned)y) >> (32 - log2ny))] = v;
-    }
-    __syncthreads();
-    fft_smem<CT>(s, ny, log2ny, cpb, tw);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e % cpb, ky = e / cpb;
-        if (kx0 + c >= hx) continue;
-        const CT v = s[c * ny + ky];
-        const double re = (double)v.x, im = (double)v.y;
-        acc[(size_t)ky * ldx + kx0 + c] += (re * re + im * im) * inv_n;
-    }
-}
-
-static int cols_per_block(int ny, size_t csize) {
-    int cpb = 4;
-    while (cpb > 1 && (size_t)cpb * ny * csize > 128 * 1024) cpb >>= 1;
-    return cpb;
+    sk_cols_block<T>(spec, acc, tw, nx, ny, log2ny, ldx, cpb, inv_n, blockIdx.x * cpb);
 }
 
 template <typename T>
@@ -238,6 +132,52 @@ cudaError_t launch_sk_bins(const double *acc, double inv_count, double *bins, do
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     sk_bins_kernel<<<blocks, 256, 0, s>>>(acc, inv_count, bins, counts, nbins, nx, ny, ldx);
+    return cudaGetLastError();
+}
+
+}  // namespace lbsc
+
+namespace lbsc {
+
+// First moments of the mean S(k) over the full plane (k = 0 excluded):
+// out = (sum_k S(k), sum_k |k| S(k)), |k| = 2 pi sqrt((kx/nx)^2 + (ky/ny)^2)
+// with folded indices; a half-plane column 0 < kx < nx/2 counts twice.  One
+// block, fixed summation order.
+__global__ void __launch_bounds__(256)
+sk_moments_kernel(const double *__restrict__ acc, double inv_count, int nx, int ny, int ldx,
+                  double *__restrict__ out) {
+    const int hx = nx / 2 + 1;
+    double s0 = 0.0, s1 = 0.0;
+    for (int e = threadIdx.x; e < hx * ny; e += blockDim.x) {
+        const int ky = e / hx, kx = e % hx;
+        if (kx == 0 && ky == 0) continue;
+        const int my = ky <= ny / 2 ? ky : ky - ny;
+        const double w = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
+        const double S = acc[(size_t)ky * ldx + kx] * inv_count;
+        const double qx = (double)kx / nx, qy = (double)my / ny;
+        s0 += w * S;
+        s1 += w * S * 6.283185307179586 * sqrt(qx * qx + qy * qy);
+    }
+    __shared__ double sh0[256], sh1[256];
+    sh0[threadIdx.x] = s0;
+    sh1[threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh0[threadIdx.x] += sh0[threadIdx.x + o];
+            sh1[threadIdx.x] += sh1[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh0[0];
+        out[1] = sh1[0];
+    }
+}
+
+cudaError_t launch_sk_moments(const double *acc, double inv_count, int nx, int ny, int ldx,
+                              double *out2, cudaStream_t s) {
+    sk_moments_kernel<<<1, 256, 0, s>>>(acc, inv_count, nx, ny, ldx, out2);
     return cudaGetLastError();
 }
 

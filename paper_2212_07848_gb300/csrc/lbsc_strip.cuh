@@ -1,0 +1,137 @@
+// The fused D2Q9 step for one strip of a lattice (shared by the
+// single-lattice kernel and the batched ensemble kernel).  See lbsc_step.cu
+// for the design.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbsc_collide.cuh"
+#include "lbsc_device.cuh"
+#include "lbsc_internal.cuh"
+
+namespace lbsc {
+
+// One CTA's work: the strip of columns [x0, x0 + kStepTX) and rows [y0, y1)
+// of the lattice described by p (the CTA has kStepTX + 32 threads).  Shared
+// by the single-lattice kernel and the batched ensemble kernel.
+// rk: the Philox round keys (kept apart from p so that callers can serve
+// them from the constant bank).
+template <typename T, int ORDER, bool SAMPLE>
+__device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *__restrict__ rk,
+                                           int x0, int y0, int y1) {
+    using S = Stencil<ORDER>;
+    constexpr int H = S::H;
+    constexpr int RING = (H == 1) ? 4 : 8;   // >= 2H + 2 rows, power of two
+    constexpr int W = kStepTX + 2 * H;
+    __shared__ T s_dpsi[RING][W];
+
+    const int nx = p.nx, ny = p.ny;
+    const size_t plane = (size_t)nx * ny;
+    const int tx = threadIdx.x;
+    const int xe = min(x0 + kStepTX, nx);
+    const int ncol = xe - x0;
+
+    // Threads 0..kStepTX-1 own the strip's columns; the extra warp owns the
+    // 2H halo columns (left, then right) and only computes their
+    // pseudopotential, so every warp does the same pull-and-psi work per row.
+    const bool interior = tx < kStepTX;
+    const int hl = tx - kStepTX;
+    const bool active = interior ? (tx < ncol) : (hl < 2 * H);
+    int x, slot_col;
+    if (interior) {
+        x = active ? x0 + tx : x0;
+        slot_col = tx + H;
+    } else if (hl < H) {
+        x = wrap_once(x0 - H + hl, nx);
+        slot_col = hl;
+    } else {
+        x = wrap_once(xe + (min(hl, 2 * H - 1) - H), nx);
+        slot_col = ncol + H + (min(hl, 2 * H - 1) - H);
+    }
+    const bool collides = interior && active;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+
+    const T rho0 = p.rho0;
+
+    T q[H + 1][9];   // pulled populations of rows yy-H .. yy
+#pragma unroll
+    for (int r = 0; r <= H; ++r)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[r][i] = T(0);
+
+    const int it_end = (y1 - y0) + 2 * H;
+    // Register prefetch: the loads of row it+1 are issued before row it is
+    // collided, so they are in flight during the collision arithmetic.
+    T gn[9];
+    {
+        const int yc = wrap_once(y0 - H, ny);
+        const int ym = yc == 0 ? ny - 1 : yc - 1;
+        const int yp = yc == ny - 1 ? 0 : yc + 1;
+        if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+    }
+#pragma unroll 2
+    for (int it = 0; it < it_end; ++it) {
+        const int slot = it & (RING - 1);
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = gn[i];
+        if (it + 1 < it_end && active) {
+            const int yc = wrap_once(y0 - H + it + 1, ny);
+            const int ym = yc == 0 ? ny - 1 : yc - 1;
+            const int yp = yc == ny - 1 ? 0 : yc + 1;
+            pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+        }
+        const int yy = y0 - H + it;
+        if (active)
+            s_dpsi[slot][slot_col] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
+#pragma unroll
+        for (int r = 0; r < H; ++r)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) q[r][i] = q[r + 1][i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[H][i] = g[i];
+        __syncthreads();
+        if (it < 2 * H || !collides) continue;
+
+        // ---- collide row yr = yy - H ------------------------------------
+        const int yr = yy - H;
+        const int cslot = (it - H) & (RING - 1);
+
+        // Shan-Chen force, Eq. (1), as antisymmetric pairs so that a uniform
+        // psi gives exactly zero: sum_a w_a psi(x+e_a) e_a over the full set
+        // equals sum over half pairs of w_a [dpsi(x+e_a) - dpsi(x-e_a)] e_a.
+        T sx = T(0), sy = T(0);
+#pragma unroll
+        for (int a = 0; a < S::N; ++a) {
+            const HalfVec hv = S::v(a);
+            const T dpl = s_dpsi[(it - H + hv.ey) & (RING - 1)][tx + H + hv.ex];
+            const T dmi = s_dpsi[(it - H - hv.ey) & (RING - 1)][tx + H - hv.ex];
+            const T d = T(hv.w) * (dpl - dmi);
+            if (hv.ex != 0) sx += T(hv.ex) * d;
+            if (hv.ey != 0) sy += T(hv.ey) * d;
+        }
+        const T psic = p.psi0 + s_dpsi[cslot][tx + H];
+        const T Fx = p.force_pref * psic * sx;
+        const T Fy = p.force_pref * psic * sy;
+
+        T f[9];
+        collide(q[0], Fx, Fy, p, rk, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
+
+        const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
+        p.dst[o] = f[0];
+        p.dst[o + pl] = f[1];
+        p.dst[o + 2u * pl] = f[2];
+        p.dst[o + 3u * pl] = f[3];
+        p.dst[o + 4u * pl] = f[4];
+        p.dst[o + 5u * pl] = f[5];
+        p.dst[o + 6u * pl] = f[6];
+        p.dst[o + 7u * pl] = f[7];
+        p.dst[o + 8u * pl] = f[8];
+        if (SAMPLE) p.drho_out[o] = sum9(q[0]);
+        if (!isfinite(f[1] + f[5])) atomicOr(p.flag, LB_STEP_NONFINITE);
+    }
+}
+
+}  // namespace lbsc

@@ -18,13 +18,16 @@ class Lattice:
     G (< 0 attractive), tau (> 1/2), kT (>= 0), psi_kind (0: 1-exp(-rho);
     1: sqrt(Tc nc) exp(1-nc/rho); 2: a exp(-b/rho)), psi_p1/psi_p2, stencil
     (4, 6, 8), precision ("fp32" or "fp64"), stream (an int cudaStream_t,
-    e.g. torch.cuda.current_stream().cuda_stream), device.
+    e.g. torch.cuda.current_stream().cuda_stream), device, tau_bulk and
+    tau_ghost (0: equal to tau, the BGK collision).
     """
 
     def __init__(self, nx, ny, G, tau=1.0, kT=0.0, psi_kind=0, stencil=4,
-                 precision="fp32", psi_p1=0.0, psi_p2=0.0, stream=None, device=-1):
+                 precision="fp32", psi_p1=0.0, psi_p2=0.0, stream=None, device=-1,
+                 tau_bulk=0.0, tau_ghost=0.0):
         p = abi.lb_params_init()
         p.nx, p.ny, p.G, p.tau, p.kT = nx, ny, G, tau, kT
+        p.tau_bulk, p.tau_ghost = tau_bulk, tau_ghost
         p.psi_kind, p.psi_p1, p.psi_p2, p.stencil = psi_kind, psi_p1, psi_p2, stencil
         p.precision = abi.LB_FP32 if precision in ("fp32", abi.LB_FP32) else abi.LB_FP64
         p.stream = stream
@@ -111,6 +114,15 @@ class Lattice:
         out = np.empty(nbins)
         return abi.lb_structure_factor(self._h, out, nbins)
 
+    def sk_moments(self):
+        """(sum_k S, sum_k |k| S) of the mean S(k), k = 0 excluded."""
+        return abi.lb_sk_moments(self._h)
+
+    def domain_size(self):
+        """L = 2 pi sum S / sum |k| S (this library's definition)."""
+        m = self.sk_moments()
+        return 2.0 * 3.141592653589793 * m[0] / m[1]
+
     def structure_factor_counts(self, nbins):
         return abi.lb_structure_factor_counts(self._h, nbins)
 
@@ -125,6 +137,14 @@ class Lattice:
 
     def set_strip_height(self, rows):
         abi.lb_set_strip_height(self._h, rows)
+
+    def set_kernel(self, mode):
+        """abi.LB_KERNEL_AUTO / LB_KERNEL_PLAIN / LB_KERNEL_TMA."""
+        abi.lb_set_kernel(self._h, mode)
+
+    @property
+    def kernel(self):
+        return abi.lb_get_kernel(self._h)
 
     def device_ptr(self, which=abi.LB_PTR_POPULATIONS):
         return abi.lb_device_ptr(self._h, which)

@@ -1,0 +1,99 @@
+"""Batched ensemble: every replica evolves exactly as a single lattice with
+the same parameters, seed and replica index (the same per-site code), for
+steps taken singly or replayed from captured graphs, with S(k) sampling;
+small replicas also match the oracle; the autotuner leaves the state intact."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from pairs import LN2, max_rel
+
+pytestmark = pytest.mark.gpu
+
+REPS = [(64, 64, -3.6, 1.0, 1e-5, LN2), (128, 32, -4.2, 0.8, 1e-5, 0.7),
+        (32, 32, -4.8, 1.3, 1e-5, 0.65), (256, 128, -3.9, 1.0, 1e-6, 0.75),
+        (64, 64, -4.0, 1.0, 0.0, LN2), (16, 64, -3.6, 1.1, 1e-5, 0.72)]
+
+
+def _single(r, rep, seed, amp, sk=None):
+    from paper_2212_07848_gb300.lattice import Lattice
+    nx, ny, G, tau, kT, rho0 = rep
+    g = Lattice(nx, ny, G, tau, kT)
+    g.set_replica(r)
+    g.init(rho0, seed, amp)
+    if sk:
+        g.sk_config(*sk)
+    return g
+
+
+@pytest.mark.parametrize("strip", [8, 32])
+def test_replicas_match_single_lattices(strip):
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    e = Ensemble(REPS, seed=77)
+    e.set_strip_height(strip)
+    e.init(0.01)
+    e.sk_config(5, 10)
+    e.step(3)          # single launches
+    e.step(64)         # graph windows of 5 steps with a sample at the end
+    e.step(4)
+    e.sync()
+    assert e.t == 71
+    for r, rep in enumerate(REPS):
+        g = _single(r, rep, 77, 0.01, (5, 10))
+        g.step(71)
+        assert np.array_equal(e.populations(r), g.populations()), r
+        Se, ne = e.structure_factor(r)
+        Sg, ng = g.structure_factor()
+        assert ne == ng == 13
+        assert np.array_equal(Se, Sg), r
+
+
+def test_plain_graph_windows_match():
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    a = Ensemble(REPS, seed=5)
+    b = Ensemble(REPS, seed=5)
+    a.init(0.02)
+    b.init(0.02)
+    a.step(100)                      # three 32-step graph replays + 4 single steps
+    for _ in range(100):
+        b.step(1)                    # single launches only
+    for r in range(len(REPS)):
+        assert np.array_equal(a.populations(r), b.populations(r))
+
+
+def test_small_replica_matches_oracle():
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    e = Ensemble(REPS, seed=9)
+    e.init(0.01)
+    e.step(60)
+    for r in (0, 2, 5):
+        nx, ny, G, tau, kT, rho0 = REPS[r]
+        o = O.OracleLattice(nx, ny, G, tau, kT, replica=r)
+        o.init(rho0, 9, 0.01)
+        o.step(60)
+        assert max_rel(e.populations(r), o.populations()) < 1e-4
+        c = e.conserved(r)
+        assert abs(c[0] - o.conserved()[0]) / c[0] < 1e-6
+
+
+def test_autotune_keeps_state(tmp_path):
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    a = Ensemble(REPS, seed=3)
+    b = Ensemble(REPS, seed=3)
+    a.init(0.01)
+    b.init(0.01)
+    a.step(7)
+    b.step(7)
+    cache = str(tmp_path / "tune.txt")
+    s = a.autotune(5, cache)
+    assert s in (8, 12, 16, 24, 32, 48)
+    assert a.t == 7
+    a.step(10)
+    b.step(10)
+    for r in range(len(REPS)):
+        assert np.array_equal(a.populations(r), b.populations(r))
+    # a second ensemble of the same shape reads the choice from the cache
+    c = Ensemble(REPS, seed=3)
+    c.init(0.0)
+    assert c.autotune(5, cache) == s
+    assert open(cache).read().count("\n") == 1

@@ -1,0 +1,126 @@
+"""Surrogate kernels against the FP32 CPU reference: tensor-core 3x3
+convolution (forward, input gradient, weight gradient), pooling and
+upsampling forward/backward, ReLU mask, Adam.  Inputs are BF16; the
+reference sums their exact values in FP64, so the tolerance covers the FP32
+accumulation order and the BF16 rounding of the output only."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_ref as R
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _lib():
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    P = C.c_void_p
+    L.lb_nn_conv3x3.argtypes = [P, P, P, P] + [C.c_int] * 7 + [P]
+    L.lb_nn_conv3x3_wgrad.argtypes = [P, P, P, P] + [C.c_int] * 5 + [P]
+    L.lb_nn_pool2.argtypes = [P, P] + [C.c_int] * 5 + [P]
+    L.lb_nn_up2.argtypes = [P, P] + [C.c_int] * 5 + [P]
+    L.lb_nn_relu_mask.argtypes = [P, P, P, C.c_size_t, P]
+    L.lb_nn_adam.argtypes = [P, P, P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double,
+                             C.c_double, C.c_longlong, P]
+    return L
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _bf(shape, scale=1.0, seed=0):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    return (scale * torch.randn(shape, generator=g)).to(torch.bfloat16).cuda()
+
+
+def _np(t):
+    return t.float().cpu().numpy()
+
+
+def _close(got, ref, tol):
+    scale = np.sqrt(np.mean(ref ** 2)) + 1e-30
+    err = np.abs(got - ref).max() / scale
+    assert err < tol, err
+
+
+CONV = [(2, 4, 128, 16, 32), (1, 3, 256, 64, 128), (2, 2, 128, 128, 64), (1, 2, 128, 32, 16)]
+
+
+@pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
+def test_conv_forward(nb, h, w, cin, cout):
+    L = _lib()
+    x = _bf((nb, h, w, cin), seed=1)
+    wt = _bf((9, cout, cin), 0.1, seed=2)
+    b = torch.randn(cout, device="cuda")
+    y = torch.empty((nb, h, w, cout), dtype=torch.bfloat16, device="cuda")
+    for relu in (0, 1):
+        assert L.lb_nn_conv3x3(_p(x), _p(wt), _p(b), _p(y), nb, h, w, cin, cout, relu, 0, None) == 0
+        torch.cuda.synchronize()
+        ref = R.conv3x3(_np(x), _np(wt), b.cpu().numpy(), bool(relu))
+        _close(_np(y), ref, 1.5e-2)
+
+
+@pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
+def test_conv_input_gradient(nb, h, w, cin, cout):
+    L = _lib()
+    dy = _bf((nb, h, w, cout), seed=3)
+    wt = _bf((9, cout, cin), 0.1, seed=4)
+    dx = torch.empty((nb, h, w, cin), dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_conv3x3(_p(dy), _p(wt), None, _p(dx), nb, h, w, cout, cin, 0, 1, None) == 0
+    torch.cuda.synchronize()
+    _close(_np(dx), R.conv3x3_dgrad(_np(dy), _np(wt)), 1.5e-2)
+
+
+@pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
+def test_conv_weight_gradient(nb, h, w, cin, cout):
+    L = _lib()
+    x = _bf((nb, h, w, cin), seed=5)
+    dy = _bf((nb, h, w, cout), seed=6)
+    dw = torch.zeros((9, cout, cin), device="cuda")
+    db = torch.zeros(cout, device="cuda")
+    for _ in range(2):                       # accumulates
+        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), _p(db), nb, h, w, cin, cout, None) == 0
+    torch.cuda.synchronize()
+    _close(dw.cpu().numpy(), 2 * R.conv3x3_wgrad(_np(x), _np(dy)), 1e-3)
+    _close(db.cpu().numpy(), 2 * _np(dy).sum(axis=(0, 1, 2)), 1e-3)
+
+
+def test_pool_up_relu_adam():
+    L = _lib()
+    x = _bf((2, 8, 16, 16), seed=7)
+    y = torch.empty((2, 4, 8, 16), dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_pool2(_p(x), _p(y), 2, 8, 16, 16, 0, None) == 0
+    dx = torch.empty_like(x)
+    assert L.lb_nn_pool2(_p(y), _p(dx), 2, 8, 16, 16, 1, None) == 0
+    u = torch.empty_like(x)
+    assert L.lb_nn_up2(_p(y), _p(u), 2, 4, 8, 16, 0, None) == 0
+    du = torch.empty_like(y)
+    assert L.lb_nn_up2(_p(x), _p(du), 2, 4, 8, 16, 1, None) == 0
+    torch.cuda.synchronize()
+    _close(_np(y), R.pool2(_np(x)), 1e-2)
+    _close(_np(dx), 0.25 * R.up2(_np(y)), 1e-2)
+    _close(_np(u), R.up2(_np(y)), 1e-2)
+    _close(_np(du), 4 * R.pool2(_np(x)), 1e-2)
+    a = _bf((1000,), seed=8)
+    m = torch.empty_like(a)
+    assert L.lb_nn_relu_mask(_p(a), _p(a), _p(m), 1000, None) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(m), np.where(_np(a) > 0, _np(a), 0.0))
+    n = 513
+    w = torch.randn(n, device="cuda")
+    g = torch.randn(n, device="cuda")
+    mo = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    wb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    w0 = w.cpu().numpy().copy()
+    assert L.lb_nn_adam(_p(w), _p(g), _p(mo), _p(v), _p(wb), n, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 0
+    torch.cuda.synchronize()
+    gg = g.cpu().numpy()
+    mm, vv = 0.1 * gg, 0.001 * gg * gg
+    ref = w0 - 1e-3 * (mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8)
+    assert np.abs(w.cpu().numpy() - ref).max() < 1e-6
+    assert np.abs(_np(wb) - ref).max() < 1e-2

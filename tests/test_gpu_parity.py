@@ -154,3 +154,13 @@ def test_torch_stream_and_zero_copy_view():
     v = g.torch_populations()
     assert v.shape == (9, 64, 64) and v.dtype == torch.float32
     assert np.array_equal(v.cpu().numpy(), g.download_state())
+
+
+@pytest.mark.parametrize("precision,steps,tol", [("fp64", 200, 1e-12), ("fp32", 100, 1e-4)])
+@pytest.mark.parametrize("st,tau,tb,tg", [(4, 0.8, 1.4, 1.1), (6, 1.2, 0.7, 1.9)])
+def test_mrt_matches_oracle(precision, steps, tol, st, tau, tb, tg):
+    g, o = make_pair(68, 36, -3.6, tau, 1e-4, stencil=st, precision=precision, seed=13,
+                     amp=0.01, tau_bulk=tb, tau_ghost=tg)
+    g.step(steps)
+    o.step(steps)
+    _compare(g, o, tol)
