@@ -198,6 +198,63 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
             "sizes": "uniform {64,128,256,512}^2, G~U[-4.8,-3.6], rho0=ln2(1+U[-0.1,0.1])"}
 
 
+def surrogate_leg(ntraj=16, size=2048, steps=4000, stride=200, iters=1200, batch=8, seed=11):
+    """Learned surrogate against the solver it stands in for: quench
+    trajectories at size^2 (G ~ U[-5.2, -4.4], rho0 = ln2, kT = 1e-6)
+    coarse-grained 4x every `stride` steps; the network is trained on all but
+    two, which score it (one-stride MSE against persistence from frame 1 on,
+    and the domain size L(t) of a 10-stride rollout against the solver's).
+    The speedup is the solver's time for `stride` steps at size^2 over the
+    surrogate's time for one stride at (size/4)^2."""
+    import torch
+
+    from paper_2212_07848_gb300 import surrogate as S
+    from paper_2212_07848_gb300.lattice import Lattice
+    frames, Gs, gen_s = S.generate(ntraj, size, steps, stride, seed0=seed * 1000)
+    m = size // 4
+    net = S.SurrogateNet(m, batch, seed=seed)
+    train_ids, test_ids = list(range(ntraj - 2)), [ntraj - 2, ntraj - 1]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=seed, t_min=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    mse, persist = S.one_step_mse(net, frames, Gs, test_ids, t_min=1)
+    k, f0, nroll = test_ids[0], 2, 10
+    out = S.rollout(net, frames[k, f0].clone(), float(Gs[k]), nroll).cpu().numpy()
+    ref = frames[k, f0 + 1:f0 + 1 + nroll].cpu().numpy()
+    L_sur = [S.radial_sk(f)[1] for f in out]
+    L_ref = [S.radial_sk(f)[1] for f in ref]
+    L_err = float(np.max(np.abs(np.array(L_sur) - np.array(L_ref)) / np.array(L_ref)))
+    x0 = frames[k, f0].clone()
+    S.rollout(net, x0, float(Gs[k]), 3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    S.rollout(net, x0, float(Gs[k]), 20)
+    b.record()
+    b.synchronize()
+    sur_ms = a.elapsed_time(b) / 20
+    lat = Lattice(size, size, float(Gs[k]), 1.0, 1e-6)
+    lat.init(RHO0, 5, 0.0)
+    lat.step(stride)
+    lat.sync()
+    st = torch.cuda.ExternalStream(lat.stream())
+    a.record(st)
+    lat.step(5 * stride)
+    b.record(st)
+    b.synchronize()
+    lb_ms = a.elapsed_time(b) / 5
+    lat.close()
+    return {"lattice": f"{size}^2 -> {m}^2 (4x coarse)", "stride": stride,
+            "trajectories": ntraj, "train_iters": iters, "batch": batch,
+            "generate_s": gen_s, "train_s": train_s,
+            "heldout_mse": mse, "persistence_mse": persist, "mse_ratio": mse / persist,
+            "rollout_strides": nroll, "rollout_L_max_rel_err": L_err,
+            "surrogate_ms_per_stride": sur_ms, "solver_ms_per_stride": lb_ms,
+            "speedup": lb_ms / sur_ms}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -321,6 +378,9 @@ def run_gpu(args, rank, world, local_rank):
     ens = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         ens = ensemble_leg(lat.stream())
+    sur = None
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        sur = surrogate_leg()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -348,6 +408,8 @@ def run_gpu(args, rank, world, local_rank):
             line["cpu_baseline"] = cb
         if ens is not None:
             line["ensemble"] = ens
+        if sur is not None:
+            line["surrogate"] = sur
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
@@ -362,6 +424,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble vs per-replica leg")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the learned-surrogate leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

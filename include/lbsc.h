@@ -307,7 +307,7 @@ int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
  *              tap = 3 (dy+1) + (dx+1)), bias [cout] or NULL, act = ReLU if relu;
  *   dgrad = 1: the input gradient dx [..][cout] of a forward layer with
  *              weights w [9][cin][cout] from dy [..][cin] (bias NULL, relu 0).
- * Requires w % 128 == 0 and channel counts multiples of 16. */
+ * Requires h * w % 128 == 0 and channel counts multiples of 16. */
 int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int w_,
                   int cin, int cout, int relu, int dgrad, void *stream);
 /* Weight and bias gradients, accumulated (+=) into FP32 dw [9][cout][cin] and
@@ -322,21 +322,28 @@ int lb_nn_pool2(const void *x, void *y, int nb, int h, int w_, int c, int backwa
 int lb_nn_up2(const void *x, void *y, int nb, int h, int w_, int c, int backward, void *stream);
 /* y = a + b elementwise (n values). */
 int lb_nn_add(const void *a, const void *b, void *y, size_t n, void *stream);
-/* Channel 0 of out [ny/f][nx/f][c] = (block mean of rho - rho0) / scale over f x f
- * blocks of FP32 deviations df [9][ny][nx]; channel 1 = gfeat; others 0. */
-int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, double gfeat,
-                       void *out, int c, void *stream);
-/* Residual MSE on channel 0 of n pixels: *loss += mean((base + y - target)^2);
- * dy (may be NULL) = 2 (base + y - target) / n on channel 0, 0 elsewhere. */
-int lb_nn_mse(const void *y, int c, const void *target, int ct, const void *base, int cb, size_t n,
-              float *loss, void *dy, void *stream);
-/* next channel 0 = base + y, other channels copied from base. */
-int lb_nn_residual(const void *base, const void *y, int c, void *next, int cn, size_t n,
-                   void *stream);
+/* Coarse-grained density of a lattice state: FP32 out [ny/f][nx/f] = (mean of
+ * rho - rho0 over each f x f block) / scale, from FP32 deviations df [9][ny][nx]
+ * (the populations buffer of an LB_FP32 lattice).  LB_ERR_ARG unless f divides
+ * nx and ny and scale != 0. */
+int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, float *out,
+                       void *stream);
+/* Residual MSE over n pixels: prediction = base + y[.][0] (FP32 base, BF16 y
+ * [n][c]); *loss += mean((prediction - target)^2) (accumulates: zero it first);
+ * dy (may be NULL) [n][c] = d loss / d y: 2 (prediction - target) / n on
+ * channel 0, 0 elsewhere. */
+int lb_nn_mse(const void *y, int c, const float *target, const float *base, size_t n, float *loss,
+              void *dy, void *stream);
+/* Rollout update: FP32 state [n] += y[.][0]; channel 0 of the network input x
+ * [n][cx] = BF16(state), other channels of x untouched. */
+int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, void *stream);
 /* Adam step (bias-corrected, `step` >= 1) on FP32 w with gradient g and moments
  * m, v; w_bf16 (may be NULL) receives the BF16 copy. */
 int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_t n, double lr,
                double b1, double b2, double eps, long long step, void *stream);
+/* Network input from an FP32 field src [n]: out [n][c] with channel 0 =
+ * BF16(src), channel 1 = gfeat (the coupling feature), others 0. */
+int lb_nn_expand(const float *src, double gfeat, void *out, int c, size_t n, void *stream);
 /* BF16 copy of FP32 values. */
 int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream);
 

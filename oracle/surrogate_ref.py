@@ -1,4 +1,4 @@
-"""FP32 CPU reference of the surrogate's layers (numpy), for checking the
+"""CPU reference of the surrogate network (numpy, FP64 sums), for checking the
 BF16 tensor-core kernels and their gradients.
 
 TEST INFRASTRUCTURE ONLY.  Layout: NHWC [nb][h][w][c], periodic boundaries,
@@ -46,3 +46,64 @@ def pool2(x):
 
 def up2(x):
     return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def pool2_backward(dy):
+    return 0.25 * up2(dy)
+
+
+def up2_backward(dy):
+    return 4.0 * pool2(dy)
+
+
+def net_forward(x, w, b):
+    """The surrogate network on x [nb][n][n][16]: returns (y, activations)
+    with w[i] [9][cout][cin], b[i] [cout] for the five layers
+    16->32 (n), 32->64 (n/2), 64->128 (n/4), 128->64 (n/2), 64->16 (n);
+    pooling after layers 1 and 2, upsampling before layers 4 and 5, and the
+    skip a4 + a2 before the last upsampling."""
+    a1 = conv3x3(x, w[0], b[0], True)
+    p1 = pool2(a1)
+    a2 = conv3x3(p1, w[1], b[1], True)
+    p2 = pool2(a2)
+    a3 = conv3x3(p2, w[2], b[2], True)
+    u3 = up2(a3)
+    a4 = conv3x3(u3, w[3], b[3], True)
+    s4 = a4 + a2
+    u4 = up2(s4)
+    y = conv3x3(u4, w[4], b[4], False)
+    return y, dict(a1=a1, p1=p1, a2=a2, p2=p2, a3=a3, u3=u3, a4=a4, u4=u4)
+
+
+def net_loss(y, base, target):
+    """Residual MSE: mean over pixels of (base + y[..., 0] - target)^2."""
+    d = base + y[..., 0] - target
+    return float(np.mean(d * d)), d
+
+
+def net_backward(x, w, acts, d):
+    """Parameter gradients of net_loss by reverse-mode differentiation of
+    net_forward (chain rule layer by layer).  Returns (dw list, db list)."""
+    dy = np.zeros(d.shape + (w[4].shape[1],))
+    dy[..., 0] = 2.0 * d / d.size
+    dw, db = [None] * 5, [None] * 5
+    ins = [x, acts["p1"], acts["p2"], acts["u3"], acts["u4"]]
+
+    def layer(i, dz):
+        dw[i] = conv3x3_wgrad(ins[i], dz)
+        db[i] = dz.sum(axis=(0, 1, 2))
+
+    layer(4, dy)
+    ds4 = up2_backward(conv3x3_dgrad(dy, w[4]))
+    dz4 = ds4 * (acts["a4"] > 0)
+    layer(3, dz4)
+    da3 = up2_backward(conv3x3_dgrad(dz4, w[3]))
+    dz3 = da3 * (acts["a3"] > 0)
+    layer(2, dz3)
+    da2 = pool2_backward(conv3x3_dgrad(dz3, w[2])) + ds4
+    dz2 = da2 * (acts["a2"] > 0)
+    layer(1, dz2)
+    da1 = pool2_backward(conv3x3_dgrad(dz2, w[1]))
+    dz1 = da1 * (acts["a1"] > 0)
+    layer(0, dz1)
+    return dw, db

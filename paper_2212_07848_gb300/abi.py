@@ -43,7 +43,7 @@ EXPORTED = [
     "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
-    "lb_nn_to_bf16",
+    "lb_nn_to_bf16", "lb_nn_expand",
 ]
 
 
@@ -145,13 +145,13 @@ def bind(L):
         "lb_nn_pool2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
         "lb_nn_up2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
         "lb_nn_add": (C.c_int, [P, P, P, C.c_size_t, P]),
-        "lb_nn_coarse_grain": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                                         P, C.c_int, P]),
-        "lb_nn_mse": (C.c_int, [P, C.c_int, P, C.c_int, P, C.c_int, C.c_size_t, P, P, P]),
+        "lb_nn_coarse_grain": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]),
+        "lb_nn_mse": (C.c_int, [P, C.c_int, P, P, C.c_size_t, P, P, P]),
         "lb_nn_residual": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_size_t, P]),
         "lb_nn_adam": (C.c_int, [P, P, P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_longlong, P]),
         "lb_nn_to_bf16": (C.c_int, [P, P, C.c_size_t, P]),
+        "lb_nn_expand": (C.c_int, [P, C.c_double, P, C.c_int, C.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -38,7 +38,8 @@ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >
 // Forward / input-gradient convolution.
 //   forward: y[p][n] = act( bias[n] + sum_{tap, c} x[p + off(tap)][c] w[tap][n][c] )
 //   dgrad  : dx[p][c] = sum_{tap, n} dy[p + off(tap)][n] w[8 - tap][n][c]
-// CTA: 128 pixels (a row segment) x BN channels; 4 warps, each 32 pixels x BN.
+// CTA: 128 consecutive pixels of one image (row-major, may span rows) x BN
+// channels; 4 warps, each 32 pixels x BN.
 // ---------------------------------------------------------------------------
 template <int BN, int BK, bool DGRAD>
 __global__ void __launch_bounds__(128)
@@ -51,8 +52,8 @@ conv3x3_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w, const flo
     const int Kc = Cin, Nc = Cout;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int x0 = blockIdx.x * 128;
-    const int yrow = blockIdx.y % H, b = blockIdx.y / H;
+    const int pix0 = blockIdx.x * 128;            // first pixel of the tile in its image
+    const int b = blockIdx.y;
     const int n0 = blockIdx.z * BN;
     const size_t img = (size_t)b * H * W;
 
@@ -66,13 +67,13 @@ conv3x3_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w, const flo
 
     for (int tap = 0; tap < 9; ++tap) {
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const int ys = wrapi(yrow + dy, H);
         for (int c0 = 0; c0 < Kc; c0 += BK) {
             // A: 128 pixels x BK channels, 16-byte vectors (8 bf16)
             constexpr int AV = 128 * BK / 8;
             for (int v = tid; v < AV; v += 128) {
                 const int px = v / (BK / 8), cv = v % (BK / 8);
-                const int xs = wrapi(x0 + px + dx, W);
+                const int pix = pix0 + px;
+                const int ys = wrapi(pix / W + dy, H), xs = wrapi(pix % W + dx, W);
                 const uint4 val = *reinterpret_cast<const uint4 *>(
                     x + (img + (size_t)ys * W + xs) * Kc + c0 + cv * 8);
                 *reinterpret_cast<uint4 *>(&As[px * P + cv * 8]) = val;
@@ -139,8 +140,8 @@ conv3x3_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w, const flo
                     v0 = fmaxf(v0, 0.f);
                     v1 = fmaxf(v1, 0.f);
                 }
-                *reinterpret_cast<__nv_bfloat162 *>(
-                    y + (img + (size_t)yrow * W + x0 + px) * Nc + n) = __floats2bfloat162_rn(v0, v1);
+                *reinterpret_cast<__nv_bfloat162 *>(y + (img + pix0 + px) * Nc + n) =
+                    __floats2bfloat162_rn(v0, v1);
             }
 }
 
@@ -317,10 +318,9 @@ __global__ void add_kernel(const bf16 *__restrict__ a, const bf16 *__restrict__ 
 }
 
 // Coarse-grain the density of a lattice state (FP32 deviations [9][ny][nx])
-// by f x f block averages into channel 0 of an NHWC BF16 field [ny/f][nx/f][C]:
-// (rho - rho0) / scale; channel 1 = gfeat; channels 2.. = 0.
+// by f x f block averages: out [ny/f][nx/f] = (block mean of rho - rho0) / scale.
 __global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int f, float scale,
-                              float gfeat, bf16 *__restrict__ out, int C) {
+                              float *__restrict__ out) {
     const int cx = nx / f, cy = ny / f;
     const size_t plane = (size_t)nx * ny;
     GRID_STRIDE(i, (size_t)cx * cy) {
@@ -334,23 +334,18 @@ __global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int 
                 for (int k = 0; k < 9; ++k) d += df[k * plane + site];
                 s += d;
             }
-        bf16 *o = out + i * C;
-        o[0] = __float2bfloat16(s / (f * f) / scale);
-        if (C > 1) o[1] = __float2bfloat16(gfeat);
-        for (int c = 2; c < C; ++c) o[c] = __float2bfloat16(0.f);
+        out[i] = s / (f * f) / scale;
     }
 }
 
-// MSE over channel 0 of an [n][C] field against a [n][Ct] target channel 0:
-// loss += sum (y - t)^2 / n (FP32 atomics), dy = 2 (y - t) / n on channel 0.
-__global__ void mse_kernel(const bf16 *__restrict__ y, int C, const bf16 *__restrict__ tgt, int Ct,
-                           const bf16 *__restrict__ base, int Cb, size_t n, float *__restrict__ loss,
+// Residual MSE: prediction = base + y[.][0] (FP32 base, BF16 increment),
+// loss += mean((prediction - target)^2), dy = d loss / d y (channel 0; 0 elsewhere).
+__global__ void mse_kernel(const bf16 *__restrict__ y, int C, const float *__restrict__ tgt,
+                           const float *__restrict__ base, size_t n, float *__restrict__ loss,
                            bf16 *__restrict__ dy) {
     float s = 0.f;
     GRID_STRIDE(i, n) {
-        // prediction = base + y (residual), target = tgt
-        const float pred = __bfloat162float(base[i * Cb]) + __bfloat162float(y[i * C]);
-        const float d = pred - __bfloat162float(tgt[i * Ct]);
+        const float d = base[i] + __bfloat162float(y[i * C]) - tgt[i];
         s += d * d;
         if (dy) {
             dy[i * C] = __float2bfloat16(2.f * d / (float)n);
@@ -361,12 +356,14 @@ __global__ void mse_kernel(const bf16 *__restrict__ y, int C, const bf16 *__rest
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
 }
 
-// next = base + y (channel 0), other channels copied from base (the rollout input)
-__global__ void residual_kernel(const bf16 *__restrict__ base, const bf16 *__restrict__ y, int C,
-                                bf16 *__restrict__ next, int Cn, size_t n) {
+// Rollout update: state (FP32) += y[.][0]; channel 0 of the next network input
+// x [n][Cx] = BF16(state), its other channels untouched.
+__global__ void residual_kernel(float *__restrict__ state, const bf16 *__restrict__ y, int C,
+                                bf16 *__restrict__ x, int Cx, size_t n) {
     GRID_STRIDE(i, n) {
-        next[i * Cn] = __float2bfloat16(__bfloat162float(base[i * Cn]) + __bfloat162float(y[i * C]));
-        for (int c = 1; c < Cn; ++c) next[i * Cn + c] = base[i * Cn + c];
+        const float v = state[i] + __bfloat162float(y[i * C]);
+        state[i] = v;
+        x[i * Cx] = __float2bfloat16(v);
     }
 }
 
@@ -385,13 +382,25 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
     }
 }
 
+// Network input from an FP32 field: out[i][0] = BF16(src[i]), out[i][1] = gfeat,
+// out[i][2..C) = 0.
+__global__ void expand_kernel(const float *__restrict__ src, float gfeat, bf16 *__restrict__ out,
+                              int C, size_t n) {
+    GRID_STRIDE(i, n) {
+        bf16 *o = out + i * C;
+        o[0] = __float2bfloat16(src[i]);
+        if (C > 1) o[1] = __float2bfloat16(gfeat);
+        for (int c = 2; c < C; ++c) o[c] = __float2bfloat16(0.f);
+    }
+}
+
 __global__ void f2bf_kernel(const float *__restrict__ a, bf16 *__restrict__ b, size_t n) {
     GRID_STRIDE(i, n) b[i] = __float2bfloat16(a[i]);
 }
 
 int blocks_for(size_t n) {
     size_t b = (n + 255) / 256;
-    return (int)(b < 152 * 32 ? b : 152 * 32);
+    return (int)(b < 1 ? 1 : b < 152 * 32 ? b : 152 * 32);
 }
 
 }  // namespace
@@ -405,12 +414,12 @@ extern "C" {
 
 int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int wd,
                   int cin, int cout, int relu, int dgrad, void *stream) {
-    if (!x || !w || !y || nb < 1 || h < 1 || wd < 128 || wd % 128 || cin % 16 || cout % 16 ||
-        cin < 16 || cout < 16)
+    if (!x || !w || !y || nb < 1 || h < 2 || wd < 2 || ((size_t)h * wd) % 128 || cin % 16 ||
+        cout % 16 || cin < 16 || cout < 16)
         return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     // GEMM K channels = channels of the kernel's input, N = of its output
-    dim3 grid(wd / 128, h * nb, 1);
+    dim3 grid((unsigned)((size_t)h * wd / 128), nb, 1);
     const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
     bf16 *yb = (bf16 *)y;
     const int bn = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
@@ -486,24 +495,26 @@ int lb_nn_add(const void *a, const void *b, void *y, size_t n, void *stream) {
     NN_RET();
 }
 
-int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, double gfeat, void *out,
-                       int c, void *stream) {
-    if (!df || !out || f < 1 || nx % f || ny % f || c < 1) return LB_ERR_ARG;
+int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, float *out,
+                       void *stream) {
+    if (!df || !out || f < 1 || nx % f || ny % f || !(scale != 0.0)) return LB_ERR_ARG;
     coarse_kernel<<<blocks_for((size_t)(nx / f) * (ny / f)), 256, 0, (cudaStream_t)stream>>>(
-        df, nx, ny, f, (float)scale, (float)gfeat, (bf16 *)out, c);
+        df, nx, ny, f, (float)scale, out);
     NN_RET();
 }
 
-int lb_nn_mse(const void *y, int c, const void *target, int ct, const void *base, int cb, size_t n,
-              float *loss, void *dy, void *stream) {
+int lb_nn_mse(const void *y, int c, const float *target, const float *base, size_t n, float *loss,
+              void *dy, void *stream) {
+    if (!y || !target || !base || !loss || c < 1) return LB_ERR_ARG;
     mse_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
-        (const bf16 *)y, c, (const bf16 *)target, ct, (const bf16 *)base, cb, n, loss, (bf16 *)dy);
+        (const bf16 *)y, c, target, base, n, loss, (bf16 *)dy);
     NN_RET();
 }
 
-int lb_nn_residual(const void *base, const void *y, int c, void *next, int cn, size_t n, void *stream) {
-    residual_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
-        (const bf16 *)base, (const bf16 *)y, c, (bf16 *)next, cn, n);
+int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, void *stream) {
+    if (!state || !y || !x || c < 1 || cx < 1) return LB_ERR_ARG;
+    residual_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(state, (const bf16 *)y, c,
+                                                                      (bf16 *)x, cx, n);
     NN_RET();
 }
 
@@ -513,6 +524,13 @@ int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_
     adam_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (bf16 *)w_bf16, n,
                                                                  (float)lr, (float)b1, (float)b2,
                                                                  (float)eps, c1, c2);
+    NN_RET();
+}
+
+int lb_nn_expand(const float *src, double gfeat, void *out, int c, size_t n, void *stream) {
+    if (!src || !out || c < 1) return LB_ERR_ARG;
+    expand_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(src, (float)gfeat, (bf16 *)out,
+                                                                   c, n);
     NN_RET();
 }
 

@@ -1,0 +1,284 @@
+"""Learned surrogate: a small convolutional operator that advances the 4x
+coarse-grained density of an unstable-branch quench by a fixed stride of
+lattice steps, trained on trajectories of the solver (which stays its
+reference and its fallback).  The paper has no such part; it serves the
+long quench runs behind the paper's unstable-branch experiment.
+
+Network (NHWC BF16 activations, FP32 master weights, periodic boundaries):
+    a1 = relu(conv(x, 16 -> 32))            at N x N
+    a2 = relu(conv(pool(a1), 32 -> 64))     at N/2
+    a3 = relu(conv(pool(a2), 64 -> 128))    at N/4
+    a4 = relu(conv(up(a3), 128 -> 64))      at N/2
+    y  = conv(up(a4 + a2), 64 -> 16)        at N; prediction = x[..., 0] + y[..., 0]
+Input channel 0 is the coarse density deviation rho - rho0, channel 1 the
+coupling feature (G + 4.8) / 0.4, the rest zero.  Every operation is a
+kernel of liblbsc.so (tensor-core convolutions, elementwise pieces, Adam);
+torch only provides device memory.
+"""
+import ctypes as C
+import math
+import time
+
+import numpy as np
+
+from . import abi
+
+CIN = 16
+LAYERS = [(16, 32), (32, 64), (64, 128), (128, 64), (64, 16)]   # (cin, cout)
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise abi.LbError(rc, what)
+
+
+def gfeat(G):
+    return (G + 4.8) / 0.4
+
+
+class SurrogateNet:
+    def __init__(self, n, batch, seed=0, stream=None):
+        import torch
+        self.torch = torch
+        self.n, self.batch = n, batch
+        self.L = abi.load()
+        self.s = stream
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        self.w, self.b, self.wb, self.dw, self.db = [], [], [], [], []
+        self.mw, self.vw, self.mb, self.vb = [], [], [], []
+        for ci, co in LAYERS:
+            std = math.sqrt(2.0 / (9 * ci))
+            w = (std * torch.randn((9, co, ci), generator=g)).cuda()
+            if co == 16:                       # output layer starts near zero
+                w *= 0.01
+            self.w.append(w)
+            self.b.append(torch.zeros(co, device="cuda"))
+            self.wb.append(w.to(torch.bfloat16))
+            for lst, like in ((self.dw, w), (self.mw, w), (self.vw, w)):
+                lst.append(torch.zeros_like(like))
+            for lst in (self.db, self.mb, self.vb):
+                lst.append(torch.zeros(co, device="cuda"))
+        self.step_count = 0
+        self._alloc(batch)
+
+    def _alloc(self, nb):
+        t, n, bf = self.torch, self.n, self.torch.bfloat16
+        z = lambda h, c: t.empty((nb, h, h, c), dtype=bf, device="cuda")
+        self.nb = nb
+        self.a1, self.p1, self.a2, self.p2 = z(n, 32), z(n // 2, 32), z(n // 2, 64), z(n // 4, 64)
+        self.a3, self.u3, self.a4, self.s4 = z(n // 4, 128), z(n // 2, 128), z(n // 2, 64), z(n // 2, 64)
+        self.u4, self.y = z(n, 64), z(n, 16)
+        # gradients
+        self.dy, self.du4, self.ds4, self.dz4 = z(n, 16), z(n, 64), z(n // 2, 64), z(n // 2, 64)
+        self.du3, self.da3, self.dz3, self.dp2 = z(n // 2, 128), z(n // 4, 128), z(n // 4, 128), z(n // 4, 64)
+        self.da2, self.dz2, self.dp1 = z(n // 2, 64), z(n // 2, 64), z(n // 2, 32)
+        self.da1, self.dz1, self.tmp2 = z(n, 32), z(n, 32), z(n // 2, 64)
+
+    def _conv(self, x, i, out, relu, h):
+        ci, co = LAYERS[i]
+        _check(self.L.lb_nn_conv3x3(_p(x), _p(self.wb[i]), _p(self.b[i]), _p(out), self.nb, h, h,
+                                    ci, co, relu, 0, self.s), "conv")
+
+    def forward(self, x):
+        """x: [nb][n][n][16] BF16; returns y [nb][n][n][16] (channel 0 = increment)."""
+        n, L, nb = self.n, self.L, self.nb
+        self._conv(x, 0, self.a1, 1, n)
+        _check(L.lb_nn_pool2(_p(self.a1), _p(self.p1), nb, n, n, 32, 0, self.s), "pool")
+        self._conv(self.p1, 1, self.a2, 1, n // 2)
+        _check(L.lb_nn_pool2(_p(self.a2), _p(self.p2), nb, n // 2, n // 2, 64, 0, self.s), "pool")
+        self._conv(self.p2, 2, self.a3, 1, n // 4)
+        _check(L.lb_nn_up2(_p(self.a3), _p(self.u3), nb, n // 4, n // 4, 128, 0, self.s), "up")
+        self._conv(self.u3, 3, self.a4, 1, n // 2)
+        _check(L.lb_nn_add(_p(self.a4), _p(self.a2), _p(self.s4), self.s4.numel(), self.s), "add")
+        _check(L.lb_nn_up2(_p(self.s4), _p(self.u4), nb, n // 2, n // 2, 64, 0, self.s), "up")
+        self._conv(self.u4, 4, self.y, 0, n)
+        return self.y
+
+    def backward(self, x):
+        """Accumulate parameter gradients from self.dy (dL/dy)."""
+        n, L, nb, s = self.n, self.L, self.nb, self.s
+        wg = lambda inp, dz, i, h: _check(L.lb_nn_conv3x3_wgrad(
+            _p(inp), _p(dz), _p(self.dw[i]), _p(self.db[i]), nb, h, h, LAYERS[i][0], LAYERS[i][1], s), "wgrad")
+        dg = lambda dz, i, out, h: _check(L.lb_nn_conv3x3(
+            _p(dz), _p(self.wb[i]), None, _p(out), nb, h, h, LAYERS[i][1], LAYERS[i][0], 0, 1, s), "dgrad")
+        wg(self.u4, self.dy, 4, n)
+        dg(self.dy, 4, self.du4, n)
+        _check(L.lb_nn_up2(_p(self.du4), _p(self.ds4), nb, n // 2, n // 2, 64, 1, s), "upb")
+        _check(L.lb_nn_relu_mask(_p(self.ds4), _p(self.a4), _p(self.dz4), self.dz4.numel(), s), "relu")
+        wg(self.u3, self.dz4, 3, n // 2)
+        dg(self.dz4, 3, self.du3, n // 2)
+        _check(L.lb_nn_up2(_p(self.du3), _p(self.da3), nb, n // 4, n // 4, 128, 1, s), "upb")
+        _check(L.lb_nn_relu_mask(_p(self.da3), _p(self.a3), _p(self.dz3), self.dz3.numel(), s), "relu")
+        wg(self.p2, self.dz3, 2, n // 4)
+        dg(self.dz3, 2, self.dp2, n // 4)
+        _check(L.lb_nn_pool2(_p(self.dp2), _p(self.tmp2), nb, n // 2, n // 2, 64, 1, s), "poolb")
+        _check(L.lb_nn_add(_p(self.tmp2), _p(self.ds4), _p(self.da2), self.da2.numel(), s), "add")
+        _check(L.lb_nn_relu_mask(_p(self.da2), _p(self.a2), _p(self.dz2), self.dz2.numel(), s), "relu")
+        wg(self.p1, self.dz2, 1, n // 2)
+        dg(self.dz2, 1, self.dp1, n // 2)
+        _check(L.lb_nn_pool2(_p(self.dp1), _p(self.da1), nb, n, n, 32, 1, s), "poolb")
+        _check(L.lb_nn_relu_mask(_p(self.da1), _p(self.a1), _p(self.dz1), self.dz1.numel(), s), "relu")
+        wg(x, self.dz1, 0, n)
+
+    def zero_grad(self):
+        for t in self.dw + self.db:
+            t.zero_()
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        for i in range(len(LAYERS)):
+            _check(self.L.lb_nn_adam(_p(self.w[i]), _p(self.dw[i]), _p(self.mw[i]), _p(self.vw[i]),
+                                     _p(self.wb[i]), self.w[i].numel(), lr, b1, b2, eps,
+                                     self.step_count, self.s), "adam")
+            _check(self.L.lb_nn_adam(_p(self.b[i]), _p(self.db[i]), _p(self.mb[i]), _p(self.vb[i]),
+                                     None, self.b[i].numel(), lr, b1, b2, eps, self.step_count,
+                                     self.s), "adam")
+
+    def loss_and_grad(self, x, target, base, grad=True):
+        """MSE of the residual prediction base + y[..., 0] against the FP32
+        target; fills self.dy when `grad`.  Returns the loss as a device tensor."""
+        loss = self.torch.zeros(1, device="cuda")
+        npx = self.nb * self.n * self.n
+        _check(self.L.lb_nn_mse(_p(self.y), 16, _p(target), _p(base), npx, _p(loss),
+                                _p(self.dy) if grad else None, self.s), "mse")
+        return loss
+
+
+def generate(n_traj, size, steps, stride, G_range=(-5.2, -4.4), coarse=4, kT=1e-6, seed0=1000,
+             rho0=math.log(2.0), stencil=4):
+    """Quench trajectories of the lattice solver from a homogeneous density
+    rho0 with thermal noise, coarse-grained every `stride` steps.  Returns
+    (frames FP32 [n_traj][steps // stride + 1][size/coarse][size/coarse] of
+    rho - rho0, the couplings G, seconds spent)."""
+    import torch
+
+    from .lattice import Lattice
+    L = abi.load()
+    rng = np.random.default_rng(seed0)
+    Gs = rng.uniform(G_range[0], G_range[1], n_traj)
+    nf = steps // stride + 1
+    m = size // coarse
+    frames = torch.empty((n_traj, nf, m, m), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_traj):
+        lat = Lattice(size, size, float(Gs[k]), 1.0, kT, stencil=stencil)
+        lat.init(rho0, seed0 + k, 0.0)
+        for f in range(nf):
+            if f:
+                lat.step(stride)
+            _check(L.lb_nn_coarse_grain(C.c_void_p(lat.device_ptr(abi.LB_PTR_POPULATIONS)), size,
+                                        size, coarse, 1.0, _p(frames[k, f]),
+                                        C.c_void_p(lat.stream())), "coarse")
+        lat.sync()
+        lat.close()
+    torch.cuda.synchronize()
+    return frames, Gs, time.perf_counter() - t0
+
+
+def expand(L, field, G, out, stream=None):
+    """16-channel BF16 network input [..][m][m][16] from an FP32 field [..][m][m]."""
+    _check(L.lb_nn_expand(_p(field), gfeat(G), _p(out), CIN, field.numel(), stream), "expand")
+
+
+def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=0):
+    """Adam on random (trajectory, time) pairs of consecutive frames.  Returns
+    the losses logged every `log_every` iterations."""
+    import torch
+    L = net.L
+    if net.nb != net.batch:
+        net._alloc(net.batch)
+    nb, m = net.nb, net.n
+    x = torch.empty((nb, m, m, CIN), dtype=torch.bfloat16, device="cuda")
+    base = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(seed)
+    nf = frames.shape[1]
+    losses = []
+    for it in range(iters):
+        for j in range(nb):
+            k = int(rng.choice(train_ids))
+            f = int(rng.integers(t_min, nf - 1))
+            base[j].copy_(frames[k, f])
+            tgt[j].copy_(frames[k, f + 1])
+            expand(L, frames[k, f], Gs[k], x[j], net.s)
+        net.zero_grad()
+        net.forward(x)
+        loss = net.loss_and_grad(x, tgt, base)
+        net.backward(x)
+        net.adam(lr)
+        if log_every and it % log_every == 0:
+            losses.append(float(loss.item()))
+    return losses
+
+
+def one_step_mse(net, frames, Gs, ids, t_min=0):
+    """Mean one-stride MSE of the surrogate and of persistence (no change) over
+    all consecutive frame pairs of the trajectories `ids`, `net.nb` pairs per
+    forward pass (unused slots of the last pass repeat its last pair)."""
+    import torch
+    L, nb, m = net.L, net.nb, net.n
+    x = torch.empty((nb, m, m, CIN), dtype=torch.bfloat16, device="cuda")
+    base = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    tgt = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    pairs = [(k, f) for k in ids for f in range(t_min, frames.shape[1] - 1)]
+    s_net, s_id = 0.0, 0.0
+    for i in range(0, len(pairs), nb):
+        chunk = pairs[i:i + nb]
+        chunk = chunk + [chunk[-1]] * (nb - len(chunk))
+        for j, (k, f) in enumerate(chunk):
+            base[j].copy_(frames[k, f])
+            tgt[j].copy_(frames[k, f + 1])
+            expand(L, frames[k, f], Gs[k], x[j], net.s)
+        net.forward(x)
+        loss = net.loss_and_grad(x, tgt, base, grad=False)
+        used = len(pairs[i:i + nb])
+        d2 = ((tgt - base) ** 2).mean(dim=(1, 2))
+        y0 = net.y[..., 0].float()
+        e2 = ((base + y0 - tgt) ** 2).mean(dim=(1, 2))
+        s_net += float(e2[:used].sum())
+        s_id += float(d2[:used].sum())
+        del loss
+    return s_net / len(pairs), s_id / len(pairs)
+
+
+def rollout(net, frame0, G, strides):
+    """Apply the surrogate `strides` times from an FP32 field [m][m]; the state
+    stays FP32 (only the network input is BF16).  Returns the FP32 fields after
+    each stride as one tensor [strides][m][m]."""
+    import torch
+    L, m = net.L, net.n
+    if net.nb != 1:
+        net._alloc(1)
+    x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
+    state = frame0.clone()
+    expand(L, state, G, x, net.s)
+    out = torch.empty((strides, m, m), dtype=torch.float32, device="cuda")
+    for s in range(strides):
+        net.forward(x)
+        _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, net.s), "residual")
+        out[s].copy_(state)
+    return out
+
+
+def radial_sk(field):
+    """Radial S(k) (mean |FFT|^2 / N per integer shell) and L = 2 pi sum S / sum |k| S
+    of a periodic 2D field (host analysis of evaluation frames)."""
+    f = np.asarray(field, np.float64)
+    f = f - f.mean()
+    n = f.shape[0]
+    S = np.abs(np.fft.fft2(f)) ** 2 / f.size
+    k = np.fft.fftfreq(n) * n
+    kk = np.hypot(*np.meshgrid(k, k))
+    b = np.rint(kk).astype(int)
+    S[0, 0] = 0.0
+    sums = np.bincount(b.ravel(), S.ravel(), minlength=n)
+    cnt = np.bincount(b.ravel(), minlength=n)
+    Sb = np.where(cnt > 0, sums / np.maximum(cnt, 1), 0.0)
+    kabs = 2 * np.pi * kk / n
+    Ld = 2 * np.pi * S.sum() / (kabs * S).sum()
+    return Sb, Ld

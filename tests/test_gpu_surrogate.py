@@ -1,0 +1,102 @@
+"""The learned surrogate end to end on the GPU: the whole network's forward
+pass, loss and parameter gradients (all liblbsc kernels) against the FP64
+CPU reference; then training on solver quench trajectories, where the
+trained operator must beat persistence on held-out trajectories, roll out
+stably, and take less time per stride than the solver's steps it replaces."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from oracle import surrogate_ref as R
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(got, ref):
+    return float(np.sqrt(np.mean((got - ref) ** 2)) / (np.sqrt(np.mean(ref ** 2)) + 1e-30))
+
+
+def test_network_gradients_match_reference():
+    from paper_2212_07848_gb300.surrogate import LAYERS, SurrogateNet
+    n, nb = 64, 2
+    net = SurrogateNet(n, nb, seed=3)
+    g = torch.Generator(device="cpu").manual_seed(4)
+    for i in range(len(LAYERS)):                   # a non-trivial output layer and biases
+        net.w[i].copy_(torch.randn(net.w[i].shape, generator=g).cuda()
+                       * math.sqrt(2.0 / (9 * LAYERS[i][0])))
+        net.wb[i].copy_(net.w[i].to(torch.bfloat16))
+        net.b[i].copy_(0.1 * torch.randn(net.b[i].shape, generator=g).cuda())
+    x = torch.randn((nb, n, n, 16), generator=g).to(torch.bfloat16).cuda()
+    base = torch.randn((nb, n, n), generator=g).cuda()
+    tgt = torch.randn((nb, n, n), generator=g).cuda()
+    net.zero_grad()
+    net.forward(x)
+    loss = net.loss_and_grad(x, tgt, base)
+    net.backward(x)
+    torch.cuda.synchronize()
+
+    w = [t.float().cpu().numpy().astype(np.float64) for t in net.wb]
+    b = [t.cpu().numpy().astype(np.float64) for t in net.b]
+    xr = x.float().cpu().numpy().astype(np.float64)
+    y, acts = R.net_forward(xr, w, b)
+    ref_loss, d = R.net_loss(y, base.cpu().numpy(), tgt.cpu().numpy())
+    dw, db = R.net_backward(xr, w, acts, d)
+    assert _rel(net.y.float().cpu().numpy(), y) < 2e-2
+    assert abs(float(loss.item()) - ref_loss) < 1e-2 * ref_loss
+    for i in range(len(LAYERS)):
+        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < 5e-2, i
+        assert _rel(net.db[i].cpu().numpy(), db[i]) < 5e-2, i
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2212_07848_gb300 import surrogate as S
+    frames, Gs, gen_s = S.generate(12, 256, 3000, 200, seed0=2000)
+    net = S.SurrogateNet(64, 8, seed=0)
+    # the first stride (uniform noise -> separated domains) carries no
+    # information at the coarse scale: train and score from frame 1 on
+    before = S.one_step_mse(net, frames, Gs, [10, 11], t_min=1)
+    losses = S.train(net, frames, Gs, list(range(10)), 1000, lr=1e-3, seed=1, log_every=50,
+                     t_min=1)
+    return S, net, frames, Gs, losses, before
+
+
+def test_training_beats_persistence(trained):
+    S, net, frames, Gs, losses, before = trained
+    assert np.all(np.isfinite(losses))
+    assert before[0] > 0.9 * before[1]             # starts out as (nearly) persistence
+    mse, persist = S.one_step_mse(net, frames, Gs, [10, 11], t_min=1)
+    print(f"held-out one-stride MSE {mse:.3e} vs persistence {persist:.3e}")
+    assert mse < 0.7 * persist
+
+
+def test_rollout_stable_and_faster_than_solver(trained):
+    S, net, frames, Gs, _, _ = trained
+    from paper_2212_07848_gb300.lattice import Lattice
+    k, f0, strides = 10, 3, 8
+    out = S.rollout(net, frames[k, f0].clone(), float(Gs[k]), strides)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert np.all(np.isfinite(o)) and np.abs(o).max() < 3.0
+    # time per stride of the surrogate against the 200 solver steps it stands for
+    x0 = frames[k, f0].clone()
+    S.rollout(net, x0, float(Gs[k]), 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.rollout(net, x0, float(Gs[k]), 20)
+    torch.cuda.synchronize()
+    t_net = (time.perf_counter() - t0) / 20
+    lat = Lattice(256, 256, float(Gs[k]), 1.0, 1e-6)
+    lat.init(math.log(2.0), 5, 0.0)
+    lat.step(200)
+    lat.sync()
+    t0 = time.perf_counter()
+    lat.step(2000)
+    lat.sync()
+    t_lb = (time.perf_counter() - t0) / 10
+    lat.close()
+    print(f"surrogate {t_net * 1e3:.3f} ms/stride, solver {t_lb * 1e3:.3f} ms per 200 steps")
+    assert t_net < t_lb

@@ -1,0 +1,80 @@
+"""Pins of the CPU reference of the surrogate network: the convolution
+against an explicit loop over pixels and taps, its input and weight
+gradients as the adjoints of the forward map, pooling and upsampling as
+mutual adjoints, and the whole-network backward pass against central finite
+differences of the loss."""
+import numpy as np
+
+from oracle import surrogate_ref as R
+
+
+def _rand(shape, seed, scale=1.0):
+    return scale * np.random.default_rng(seed).standard_normal(shape)
+
+
+def test_conv_matches_explicit_loop():
+    x = _rand((1, 4, 6, 3), 1)
+    w = _rand((9, 2, 3), 2)
+    b = _rand(2, 3)
+    y = R.conv3x3(x, w, b)
+    h, wd = 4, 6
+    for yy in range(h):
+        for xx in range(wd):
+            for n in range(2):
+                s = b[n]
+                for t in range(9):
+                    dy, dx = t // 3 - 1, t % 3 - 1          # tap = 3 (dy + 1) + (dx + 1)
+                    s += np.dot(x[0, (yy + dy) % h, (xx + dx) % wd], w[t, n])
+                assert abs(y[0, yy, xx, n] - s) < 1e-12
+
+
+def test_gradients_are_adjoints():
+    x = _rand((2, 4, 4, 3), 4)
+    w = _rand((9, 5, 3), 5)
+    dy = _rand((2, 4, 4, 5), 6)
+    lhs = np.sum(R.conv3x3(x, w) * dy)
+    assert abs(lhs - np.sum(x * R.conv3x3_dgrad(dy, w))) < 1e-10 * abs(lhs)
+    assert abs(lhs - np.sum(w * R.conv3x3_wgrad(x, dy))) < 1e-10 * abs(lhs)
+    a = _rand((1, 4, 6, 2), 7)
+    c = _rand((1, 2, 3, 2), 8)
+    assert abs(np.sum(R.pool2(a) * c) - np.sum(a * R.pool2_backward(c))) < 1e-12
+    assert abs(np.sum(R.up2(c) * a) - np.sum(c * R.up2_backward(a))) < 1e-12
+
+
+def _net(seed, n=8):
+    chans = [(16, 32), (32, 64), (64, 128), (128, 64), (64, 16)]
+    w = [_rand((9, co, ci), seed + i, np.sqrt(2.0 / (9 * ci))) for i, (ci, co) in enumerate(chans)]
+    b = [_rand(co, seed + 10 + i, 0.1) for i, (ci, co) in enumerate(chans)]
+    x = _rand((1, n, n, 16), seed + 20)
+    base = _rand((1, n, n), seed + 21)
+    tgt = _rand((1, n, n), seed + 22)
+    return x, w, b, base, tgt
+
+
+def test_network_backward_matches_finite_differences():
+    x, w, b, base, tgt = _net(30)
+    y, acts = R.net_forward(x, w, b)
+    _, d = R.net_loss(y, base, tgt)
+    dw, db = R.net_backward(x, w, acts, d)
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    for i in range(5):
+        for _ in range(4):
+            idx = tuple(int(rng.integers(s)) for s in w[i].shape)
+            old = w[i][idx]
+            w[i][idx] = old + h
+            lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+            w[i][idx] = old - h
+            lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+            w[i][idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - dw[i][idx]) <= 1e-4 * abs(fd) + 1e-9, (i, idx, fd, dw[i][idx])
+        j = int(rng.integers(b[i].size))
+        old = b[i][j]
+        b[i][j] = old + h
+        lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        b[i][j] = old - h
+        lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        b[i][j] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - db[i][j]) <= 1e-4 * abs(fd) + 1e-9, (i, j, fd, db[i][j])
