@@ -136,10 +136,12 @@ int lb_set_replica(lb_ctx *h, uint32_t replica);
  * not change results. */
 int lb_set_strip_height(lb_ctx *h, int rows);
 
-/* Choose the step kernel (LB_KERNEL_*).  Both kernels perform the same
+/* Choose the step kernel (LB_KERNEL_*).  All kernels perform the same
  * arithmetic per site and give the same results; they differ only in how rows
- * reach the SM.  LB_ERR_UNSUPPORTED if LB_KERNEL_TMA is requested for a
- * lattice it cannot serve.  lb_get_kernel returns the kernel lb_step uses. */
+ * reach the SM and how the pseudopotential halo is exchanged.
+ * LB_ERR_UNSUPPORTED if the requested kernel cannot serve the lattice
+ * (LB_KERNEL_TMA: FP32 and nx % 128 == 0).
+ * lb_get_kernel returns the kernel lb_step uses. */
 int lb_set_kernel(lb_ctx *h, int mode);
 int lb_get_kernel(const lb_ctx *h);
 

@@ -39,10 +39,12 @@
  *     rho the local pre-collision density;
  *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11,
  *     "Parallel random numbers: as easy as 1, 2, 3"), key = 64-bit seed,
- *     counter = (site, step, replica, block), uniforms (r + 1/2) 2^-32, and
- *     Box-Muller pairs (r0,r1) -> modes 3,4; (r2,r3) -> modes 5,6 from block 0
- *     and (r0,r1) of block 1 -> modes 7,8.  Block 2 of step 0 drives the
- *     optional initial density kick.
+ *     counter = (site, step, replica, block), uniforms (r + 1/2) 2^-32.  One
+ *     call (block 0) per site and step: Box-Muller on a ring of 1024 angles,
+ *     radius word r0 with angle index bits 0-9 of r3 -> modes 3,4; r1 with
+ *     bits 10-19 -> modes 5,6; r2 with bits 20-29 -> modes 7,8.  Block 2 of
+ *     step 0 drives the optional initial density kick (a plain Box-Muller
+ *     pair (r0, r1)).
  */
 #include <math.h>
 #include <stdint.h>
@@ -201,6 +203,25 @@ static void box_muller(uint32_t ra, uint32_t rb, double *z0, double *z1) {
     *z1 = rad * sin(th);
 }
 
+/* Box-Muller with the angle taken from 1024 equally spaced values: radius
+ * from the uniform of word ra, angle th = 2 pi (a + 1/2) / 1024 for a 10-bit
+ * index a.  All moments of (cos th, sin th) below order 1024 equal those of a
+ * uniform angle, so (z0, z1) has the moments of two independent standard
+ * normals up to that order. */
+static void box_muller_ring(uint32_t ra, uint32_t a, double *z0, double *z1) {
+    double rad = sqrt(-2.0 * log(uniform01(ra)));
+    double th = 2.0 * M_PI * ((double)(a & 1023u) + 0.5) / 1024.0;
+    *z0 = rad * cos(th);
+    *z1 = rad * sin(th);
+}
+
+/* The six thermal normals of a site: one Philox draw (block 0). */
+static void site_normals(const uint32_t r[4], double z[6]) {
+    box_muller_ring(r[0], r[3], &z[0], &z[1]);
+    box_muller_ring(r[1], r[3] >> 10, &z[2], &z[3]);
+    box_muller_ring(r[2], r[3] >> 20, &z[4], &z[5]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Model parameters (mirrors the product's create arguments).               */
 /* ------------------------------------------------------------------------ */
@@ -267,12 +288,9 @@ static void collide_site(const or_params *p, uint32_t site, uint32_t t,
     /* Thermal noise: N_k = sqrt(mu rho b_k (1-gamma^2)) z_k on k = 3..8. */
     double z[9] = {0};
     if (p->kT > 0.0) {
-        uint32_t r[4], q[4];
+        uint32_t r[4];
         draw(p, site, t, 0, r);
-        draw(p, site, t, 1, q);
-        box_muller(r[0], r[1], &z[3], &z[4]);
-        box_muller(r[2], r[3], &z[5], &z[6]);
-        box_muller(q[0], q[1], &z[7], &z[8]);
+        site_normals(r, &z[3]);
     }
     double gam = 1.0 - 1.0 / tau;
     double mu = p->kT / CS2;
@@ -657,12 +675,13 @@ int or_stencil(int order, int *ex, int *ey, double *w) {
     return stencil_vectors(order, ex, ey, w);
 }
 void or_normals(const or_params *p, uint32_t site, uint32_t t, double z[6]) {
-    uint32_t r[4], q[4];
+    uint32_t r[4];
     draw(p, site, t, 0, r);
-    draw(p, site, t, 1, q);
-    box_muller(r[0], r[1], &z[0], &z[1]);
-    box_muller(r[2], r[3], &z[2], &z[3]);
-    box_muller(q[0], q[1], &z[4], &z[5]);
+    site_normals(r, z);
+}
+/* One ring Box-Muller pair from a radius word and an angle index. */
+void or_box_muller_ring(uint32_t ra, uint32_t a, double z[2]) {
+    box_muller_ring(ra, a, &z[0], &z[1]);
 }
 
 /* Threads the site loops run on (1 without OpenMP). */

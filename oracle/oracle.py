@@ -73,6 +73,7 @@ def lib():
         L.or_stencil.argtypes = [C.c_int, _I, _I, _D]
         L.or_stencil.restype = C.c_int
         L.or_normals.argtypes = [C.POINTER(OrParams), C.c_uint32, C.c_uint32, _D]
+        L.or_box_muller_ring.argtypes = [C.c_uint32, C.c_uint32, _D]
         L.or_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -211,6 +212,14 @@ def step_sites(params, t, f_full, xs, ys):
 
 
 def normals(params, site, t):
+    """The six thermal normals of a site and step (modes 3..8)."""
     z = np.zeros(6)
     lib().or_normals(C.byref(params), site, t, z)
+    return z
+
+
+def box_muller_ring(radius_word, angle_index):
+    """One Box-Muller pair with the angle taken from a ring of 1024 values."""
+    z = np.zeros(2)
+    lib().or_box_muller_ring(radius_word, angle_index, z)
     return z

@@ -346,7 +346,8 @@ int lb_get_kernel(const lb_ctx *h) {
     // AUTO takes the plain-load kernel: on GB300 it measures faster than the
     // staged one for this step (the step is issue-bound, and the staged
     // kernel's per-row mbarrier hand-off costs more than the loads it saves).
-    return (h->kernel_mode == LB_KERNEL_TMA && h->maps.ok) ? LB_KERNEL_TMA : LB_KERNEL_PLAIN;
+    if (h->kernel_mode == LB_KERNEL_TMA && h->maps.ok) return LB_KERNEL_TMA;
+    return LB_KERNEL_PLAIN;
 }
 
 int lb_step(lb_ctx *h, int n) {
@@ -354,7 +355,7 @@ int lb_step(lb_ctx *h, int n) {
     if (!h->inited) return LB_ERR_STATE;
     int rc = select_device(h);
     if (rc) return rc;
-    const bool tma = lb_get_kernel(h) == LB_KERNEL_TMA;
+    const int kern = lb_get_kernel(h);
     for (int s = 0; s < n; ++s) {
         const long long tn = h->t + 1;
         const bool sample = h->sk_every > 0 && h->acc && tn >= h->sk_start &&
@@ -364,7 +365,7 @@ int lb_step(lb_ctx *h, int n) {
         a.dst = h->df[h->cur ^ 1];
         a.drho_out = sample ? h->drho : nullptr;
         a.step = (uint32_t)h->t;
-        if (tma)
+        if (kern == LB_KERNEL_TMA)
             LB_CHECK(launch_step_tma(h->p.stencil, a, h->maps, h->cur, h->stream));
         else
             LB_CHECK(launch_step(h->p.precision, h->p.stencil, a, h->stream));

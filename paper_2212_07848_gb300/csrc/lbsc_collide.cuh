@@ -47,17 +47,12 @@ __device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane_, i
     g[8] = __ldg(src + (8u * plane + rp + xm));
 }
 
-// 1/rho and sqrt(rho) from one reciprocal square root (FP32); FP64 keeps the
-// correctly rounded operations.
-__device__ __forceinline__ void inv_and_sqrt(float rho, float &inv, float &sr) {
+// 1/rho: FP32 from the reciprocal square root squared; FP64 correctly rounded.
+__device__ __forceinline__ float inv_rho_of(float rho) {
     const float r = rsqrtf(rho);
-    inv = r * r;
-    sr = rho * r;
+    return r * r;
 }
-__device__ __forceinline__ void inv_and_sqrt(double rho, double &inv, double &sr) {
-    inv = 1.0 / rho;
-    sr = sqrt(rho);
-}
+__device__ __forceinline__ double inv_rho_of(double rho) { return 1.0 / rho; }
 
 template <typename T>
 __device__ __forceinline__ T sum9(const T g[9]) {
@@ -70,7 +65,8 @@ __device__ __forceinline__ T sum9(const T g[9]) {
 // (1 - 1/2tau_k)(u F + F u) (BGK when every rate is 1/tau; bulk mode 3,
 // shear modes 4-5 and ghosts 6-8 may relax at their own rates), ghost modes
 // relaxed towards zero, momentum j + F
-// -> noise sqrt(mu rho b_k (1 - gamma^2)) z_k on modes 3..8 -> inverse
+// -> noise sqrt(mu rho b_k (1 - gamma^2)) z_k on modes 3..8 (one Philox
+// call, Box-Muller on a ring of 1024 angles) -> inverse
 // transform delta f_i = w_i sum_k e_ki m_k / b_k.  The inverse is factored
 // into symmetric sums and differences with the weights folded in.
 template <typename T>
@@ -93,8 +89,8 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T m7 = fma(T(2), t2, -e24);                        // (3c^2 - 4) cy
     const T m8 = fma(T(8), sd, fma(T(-4), sa, g[0] + g[0])); // 9c^4 - 15c^2 + 2
 
-    T inv_rho, sr;
-    inv_and_sqrt(p.rho0 + drho, inv_rho, sr);
+    const T rho = p.rho0 + drho;
+    const T inv_rho = inv_rho_of(rho);
     const T jxh = fma(T(0.5), Fx, m1), jyh = fma(T(0.5), Fy, m2);   // rho u
     const T ux = jxh * inv_rho, uy = jyh * inv_rho;
     const T qxx = jxh * ux, qyy = jyh * uy, qxy = jxh * uy;          // rho u u
@@ -107,19 +103,17 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T jxs = m1 + Fx, jys = m2 + Fy;
 
     if (p.noise) {
-        const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), rk);
-        const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), rk);
+        // one Philox call per site and step: radius words r.x, r.y, r.z and
+        // three 10-bit angle indices of r.w (bits 0-9, 10-19, 20-29)
+        const uint4 r = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), rk);
         T c, sn, rad;
-        box_muller_polar(uniform01<T>(r0.x), uniform01<T>(r0.y), rad, c, sn);
-        rad *= sr;
+        box_ring_polar(uniform01<T>(r.x), r.w & 1023u, rho, rad, c, sn);
         m3s = fma(p.amp[0] * rad, c, m3s);
         m4s = fma(p.amp[1] * rad, sn, m4s);
-        box_muller_polar(uniform01<T>(r0.z), uniform01<T>(r0.w), rad, c, sn);
-        rad *= sr;
+        box_ring_polar(uniform01<T>(r.y), (r.w >> 10) & 1023u, rho, rad, c, sn);
         m5s = fma(p.amp[2] * rad, c, m5s);
         m6s = fma(p.amp[3] * rad, sn, m6s);
-        box_muller_polar(uniform01<T>(r1.x), uniform01<T>(r1.y), rad, c, sn);
-        rad *= sr;
+        box_ring_polar(uniform01<T>(r.z), (r.w >> 20) & 1023u, rho, rad, c, sn);
         m7s = fma(p.amp[4] * rad, c, m7s);
         m8s = fma(p.amp[5] * rad, sn, m8s);
     }

@@ -57,18 +57,27 @@ __device__ __forceinline__ void box_muller(double u1, double u2, double &z0, dou
     z1 = r * s;
 }
 
-// The same pair in polar form, (z0, z1) = rad (c, s), so that callers can fold
-// a common scale into rad before the two products.
-__device__ __forceinline__ void box_muller_polar(float u1, float u2, float &rad, float &c,
-                                                 float &s) {
-    const float x = -1.3862943611198906f * __log2f(u1);
-    rad = -x * rsqrtf(fmaxf(x, 1e-30f));   // sign of cos(a - pi) = -cos a folded in
-    __sincosf(fmaf(6.2831853071795865f, u2, -3.1415926535897932f), &s, &c);
+// Box-Muller on a ring of 1024 angles, the noise draw of the step kernels:
+// a radius word gives u1 = (r + 1/2) 2^-32 and a 10-bit index a gives the
+// angle th = 2 pi (a + 1/2) / 1024, so that one Philox4x32 call (three radius
+// words and three 10-bit fields of the fourth word) yields the six normals of
+// a site.  Because the 1024 angles are equally spaced, every moment of
+// (cos th, sin th) below order 1024 equals its continuous average, so the pair
+// rad (cos th, sin th) has the exact moments of two independent standard
+// normals up to that order.  Returned in polar form with the local density
+// folded into the radius: rad = sqrt(-2 rho ln u1), (z0, z1) = rad (c, s).
+// FP32 uses the same hardware forms as box_muller (angle shifted by -pi, the
+// sign folded into rad).
+__device__ __forceinline__ void box_ring_polar(float u1, uint32_t a, float rho, float &rad,
+                                               float &c, float &s) {
+    const float x = (-1.3862943611198906f * rho) * __log2f(u1);   // -2 rho ln u1 >= 0
+    rad = -x * rsqrtf(fmaxf(x, 1e-30f));
+    __sincosf(fmaf((float)a, 6.1359231515425647e-3f, -3.1385246920140220f), &s, &c);
 }
-__device__ __forceinline__ void box_muller_polar(double u1, double u2, double &rad, double &c,
-                                                 double &s) {
-    rad = sqrt(-2.0 * log(u1));
-    sincospi(2.0 * u2, &s, &c);
+__device__ __forceinline__ void box_ring_polar(double u1, uint32_t a, double rho, double &rad,
+                                               double &c, double &s) {
+    rad = sqrt(-2.0 * rho * log(u1));
+    sincospi(((double)a + 0.5) * (1.0 / 512.0), &s, &c);
 }
 
 // e^x - 1.  FP32: the Taylor series through x^7 for |x| <= 1/4 (truncation

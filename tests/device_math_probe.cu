@@ -1,5 +1,6 @@
-// Test-only probe: evaluates the library's FP32 device math (expm1 and the
-// Box-Muller pair from two 32-bit words) on host-given inputs.
+// Test-only probe: evaluates the library's FP32 device math (expm1, the
+// Box-Muller pair from two 32-bit words, and the ring Box-Muller of the step
+// kernels from a radius word and an angle index) on host-given inputs.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,6 +18,17 @@ __global__ void bm_probe(const uint32_t *r, float *z, int n) {
         lbsc::box_muller(lbsc::uniform01<float>(r[2 * i]), lbsc::uniform01<float>(r[2 * i + 1]), a, b);
         z[2 * i] = a;
         z[2 * i + 1] = b;
+    }
+}
+
+// r[2i] = radius word, r[2i+1] = angle index; rho = 1: z = rad (c, s)
+__global__ void ring_probe(const uint32_t *r, float *z, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float rad, c, s;
+        lbsc::box_ring_polar(lbsc::uniform01<float>(r[2 * i]), r[2 * i + 1] & 1023u, 1.0f, rad, c, s);
+        z[2 * i] = rad * c;
+        z[2 * i + 1] = rad * s;
     }
 }
 
@@ -41,5 +53,10 @@ extern "C" int probe_expm1(const float *x, float *y, int n) {
 
 extern "C" int probe_box_muller(const uint32_t *r, float *z, int npairs) {
     return run<uint32_t>(bm_probe, r, 2 * npairs * sizeof(uint32_t), z, 2 * npairs * sizeof(float),
+                         npairs);
+}
+
+extern "C" int probe_box_ring(const uint32_t *r, float *z, int npairs) {
+    return run<uint32_t>(ring_probe, r, 2 * npairs * sizeof(uint32_t), z, 2 * npairs * sizeof(float),
                          npairs);
 }

@@ -124,6 +124,26 @@ def test_box_muller_normals():
     assert np.abs(cc - np.eye(6)).max() < 0.06
 
 
+def test_box_muller_ring_moments_exact():
+    """Over the 1024 angle indices of one radius word R the pair reproduces the
+    isotropic moments exactly: mean z0 = mean z1 = mean z0 z1 = 0,
+    mean z0^2 = mean z1^2 = R^2 / 2, mean z0^4 = 3 R^4 / 8,
+    mean z0^2 z1^2 = R^4 / 8, and R^2 = -2 ln u with u = (r + 1/2) 2^-32."""
+    for word in (0, 12345, 2 ** 31, 2 ** 32 - 1):
+        R2 = -2.0 * np.log((word + 0.5) / 2.0 ** 32)
+        z = np.array([O.box_muller_ring(word, a) for a in range(1024)])
+        z0, z1 = z[:, 0], z[:, 1]
+        assert np.allclose(np.hypot(z0, z1), np.sqrt(R2), rtol=1e-14)
+        tol = 1e-13 * max(R2, 1.0) ** 2
+        for m in (z0.mean(), z1.mean(), (z0 * z1).mean(), (z0 ** 3).mean(), (z0 * z1 ** 2).mean()):
+            assert abs(m) < tol
+        assert abs((z0 ** 2).mean() - R2 / 2) < tol and abs((z1 ** 2).mean() - R2 / 2) < tol
+        assert abs((z0 ** 4).mean() - 3 * R2 ** 2 / 8) < tol
+        assert abs((z0 ** 2 * z1 ** 2).mean() - R2 ** 2 / 8) < tol
+    # the angle index takes 10 bits: index a and a + 1024 give the same pair
+    assert np.array_equal(O.box_muller_ring(777, 5), O.box_muller_ring(777, 5 + 1024))
+
+
 # --------------------------------------------------------------------------
 # Streaming, collision, forcing
 # --------------------------------------------------------------------------
