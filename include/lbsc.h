@@ -313,9 +313,16 @@ int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
 int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int w_,
                   int cin, int cout, int relu, int dgrad, void *stream);
 /* Weight and bias gradients, accumulated (+=) into FP32 dw [9][cout][cin] and
- * dbias [cout] (may be NULL): dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n]. */
+ * dbias [cout] (may be NULL): dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n].
+ * The sum is split over chunks of 128-pixel tiles whose partial sums go to the
+ * caller's device workspace (16-byte aligned, at least
+ * lb_nn_wgrad_workspace(...) bytes) and are then added in a fixed order, so
+ * dw is deterministic.  Requires h * w % 128 == 0 and channel counts
+ * multiples of 16 (LB_ERR_ARG otherwise, or for a missing/short workspace). */
+size_t lb_nn_wgrad_workspace(int nb, int h, int w_, int cin, int cout);
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
-                        int w_, int cin, int cout, void *stream);
+                        int w_, int cin, int cout, void *workspace, size_t workspace_bytes,
+                        void *stream);
 /* dz = dy where y > 0, else 0 (ReLU backward through the layer output y). */
 int lb_nn_relu_mask(const void *dy, const void *y, void *dz, size_t n, void *stream);
 /* 2x2 average pooling of [nb][h][w][c] (backward: spread dy/4). */

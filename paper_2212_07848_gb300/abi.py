@@ -43,7 +43,7 @@ EXPORTED = [
     "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
-    "lb_nn_to_bf16", "lb_nn_expand",
+    "lb_nn_to_bf16", "lb_nn_expand", "lb_nn_wgrad_workspace",
 ]
 
 
@@ -140,7 +140,8 @@ def bind(L):
         "lb_ens_structure_factor": (C.c_int, [P, C.c_int, _D, C.c_int, C.POINTER(C.c_longlong)]),
         # surrogate building blocks: device pointers, sizes, stream
         "lb_nn_conv3x3": (C.c_int, [P, P, P, P] + [C.c_int] * 7 + [P]),
-        "lb_nn_conv3x3_wgrad": (C.c_int, [P, P, P, P] + [C.c_int] * 5 + [P]),
+        "lb_nn_conv3x3_wgrad": (C.c_int, [P, P, P, P] + [C.c_int] * 5 + [P, C.c_size_t, P]),
+        "lb_nn_wgrad_workspace": (C.c_size_t, [C.c_int] * 5),
         "lb_nn_relu_mask": (C.c_int, [P, P, P, C.c_size_t, P]),
         "lb_nn_pool2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
         "lb_nn_up2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),

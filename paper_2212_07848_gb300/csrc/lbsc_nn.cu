@@ -146,95 +146,151 @@ conv3x3_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w, const flo
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient: dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n]
-// GEMM: M = n (16-row tiles of Cout), N = c, K = pixels (chunks of 32).
-// CTA: one tap, 64 n x 64 c (or less), `chunk` pixels; 4 warps, warp w
-// takes n rows [16 w, 16 w + 16).
+// Weight gradient: dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n].
+// GEMM per tap with M = n, N = c and K = pixels, split over chunks of
+// 128-pixel tiles: each CTA writes its chunk's partial sums of all nine taps
+// to a workspace with plain stores, and a second kernel adds the chunks into
+// dw in a fixed order (no atomics, so the result is deterministic).
+// A CTA covers BM output channels x BC input channels with one warp per
+// 16 x 16 block.  Per tile it stages dY [128][BM] and, one tap row (dy) at a
+// time, the three shifted input tiles x[p + off][BC] in shared memory with
+// 16-byte cp.async copies; both operands are K-major there (pixels are rows),
+// so the fragments come from ldmatrix with the .trans qualifier.
 // ---------------------------------------------------------------------------
-template <int BMN, int BNC>
-__global__ void __launch_bounds__(128)
-wgrad_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ dy, float *__restrict__ dw,
-             int NB, int H, int W, int Cin, int Cout, int chunk) {
-    constexpr int BK = 32, P = BK + 8;
-    __shared__ __align__(16) bf16 As[BMN * P];    // [n][p]
-    __shared__ __align__(16) bf16 Bs[BNC * P];    // [c][p]
+constexpr int kWgTile = 128;            // pixels per tile (one GEMM K block)
+constexpr int kWgTargetCtas = 152 * 8;  // CTAs a launch aims for
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const void *smem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(sa));
+}
+
+template <int BM, int BC>
+__global__ void __launch_bounds__(32 * (BM / 16) * (BC / 16))
+wgrad_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ dy, float *__restrict__ part,
+             int H, int W, int Cin, int Cout, int ntiles, int tiles_per_chunk) {
+    constexpr int NT = 32 * (BM / 16) * (BC / 16);
+    constexpr int PD = BM + 8, PX = BC + 8;        // row pitches (16-byte padded)
+    __shared__ __align__(16) bf16 sDy[kWgTile * PD];
+    __shared__ __align__(16) bf16 sX[3][kWgTile * PX];
+    __shared__ int sYX[kWgTile][2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int tap = blockIdx.y % 9;
-    const int ntile = blockIdx.y / 9;
-    const int n0 = (ntile % (Cout / BMN)) * BMN;
-    const int c0 = (ntile / (Cout / BMN)) * BNC;
-    const int dyy = tap / 3 - 1, dxx = tap % 3 - 1;
-    const size_t P0 = (size_t)blockIdx.x * chunk;
-    const size_t Ptot = (size_t)NB * H * W;
-    constexpr int MT = BMN / 16 / 4 > 0 ? BMN / 16 / 4 : 1;   // m16 tiles per warp
-    float acc[MT][BNC / 8][4];
+    const int nw = (warp % (BM / 16)) * 16, cw = (warp / (BM / 16)) * 16;
+    const int n0 = blockIdx.x * BM, c0 = blockIdx.y * BC;
+    const int chunk = blockIdx.z;
+    const int tile_begin = chunk * tiles_per_chunk;
+    const int tile_end = min(tile_begin + tiles_per_chunk, ntiles);
+    const int tiles_per_img = H * W / kWgTile;
+
+    float acc[9][2][4];
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
+    for (int i = 0; i < 9; ++i)
 #pragma unroll
-        for (int j = 0; j < BNC / 8; ++j)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const int warps_m = BMN / 16 < 4 ? BMN / 16 : 4;
 
-    for (int kp0 = 0; kp0 < chunk; kp0 += BK) {
-        for (int e = tid; e < BK * BMN; e += 128) {
-            const int kp = e / BMN, nn = e % BMN;
-            const size_t p = P0 + kp0 + kp;
-            As[nn * P + kp] = p < Ptot ? dy[p * Cout + n0 + nn] : __float2bfloat16(0.f);
+    // ldmatrix row addresses: lane -> (pixel offset, channel offset) of its 8x8 matrix
+    const int mat = lane >> 3, r8 = lane & 7;
+    const int a_pix = r8 + ((mat & 2) ? 8 : 0), a_col = nw + ((mat & 1) ? 8 : 0);
+    const int b_pix = r8 + ((mat & 1) ? 8 : 0), b_col = cw + ((mat & 2) ? 8 : 0);
+
+    for (int tile = tile_begin; tile < tile_end; ++tile) {
+        const int b = tile / tiles_per_img;
+        const int pix0 = (tile - b * tiles_per_img) * kWgTile;
+        const size_t img = (size_t)b * H * W;
+        for (int px = tid; px < kWgTile; px += NT) {
+            sYX[px][0] = (pix0 + px) / W;
+            sYX[px][1] = (pix0 + px) % W;
         }
-        for (int e = tid; e < BK * BNC; e += 128) {
-            const int kp = e / BNC, cc = e % BNC;
-            const size_t p = P0 + kp0 + kp;
-            bf16 v = __float2bfloat16(0.f);
-            if (p < Ptot) {
-                const size_t bimg = p / ((size_t)H * W);
-                const int rem = (int)(p % ((size_t)H * W));
-                const int yy = wrapi(rem / W + dyy, H), xx = wrapi(rem % W + dxx, W);
-                v = x[((bimg * H + yy) * W + xx) * Cin + c0 + cc];
-            }
-            Bs[cc * P + kp] = v;
+        constexpr int DV = kWgTile * BM / 8;
+        for (int v = tid; v < DV; v += NT) {
+            const int px = v / (BM / 8), cv = v % (BM / 8);
+            cp_async16(&sDy[px * PD + cv * 8], dy + (img + pix0 + px) * Cout + n0 + cv * 8);
         }
-        __syncthreads();
-        if (warp < warps_m) {
+        __syncthreads();   // sYX visible
+        for (int ty = 0; ty < 3; ++ty) {
+            const int ddy = ty - 1;
+            constexpr int XV = kWgTile * BC / 8;
 #pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks) {
-#pragma unroll
-                for (int mi = 0; mi < MT; ++mi) {
-                    const int r = (warp + mi * 4) * 16 + g;
-                    const int k = ks * 16 + 2 * t;
-                    uint32_t af[4];
-                    af[0] = *reinterpret_cast<const uint32_t *>(&As[r * P + k]);
-                    af[1] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k]);
-                    af[2] = *reinterpret_cast<const uint32_t *>(&As[r * P + k + 8]);
-                    af[3] = *reinterpret_cast<const uint32_t *>(&As[(r + 8) * P + k + 8]);
-#pragma unroll
-                    for (int ni = 0; ni < BNC / 8; ++ni) {
-                        const int cc = ni * 8 + g;
-                        uint32_t bfr[2];
-                        bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[cc * P + k]);
-                        bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[cc * P + k + 8]);
-                        mma_bf16_16816(acc[mi][ni], af, bfr);
-                    }
+            for (int tx = 0; tx < 3; ++tx) {
+                const int ddx = tx - 1;
+                for (int v = tid; v < XV; v += NT) {
+                    const int px = v / (BC / 8), cv = v % (BC / 8);
+                    const int ys = wrapi(sYX[px][0] + ddy, H), xs = wrapi(sYX[px][1] + ddx, W);
+                    cp_async16(&sX[tx][px * PX + cv * 8],
+                               x + (img + (size_t)ys * W + xs) * Cin + c0 + cv * 8);
                 }
             }
-        }
-        __syncthreads();
-    }
-    if (warp < warps_m) {
+            cp_async_wait_all();
+            __syncthreads();
+#pragma unroll 2
+            for (int k0 = 0; k0 < kWgTile; k0 += 16) {
+                uint32_t af[4];
+                ldsm_x4_trans(af, &sDy[(k0 + a_pix) * PD + a_col]);
 #pragma unroll
-        for (int mi = 0; mi < MT; ++mi)
-#pragma unroll
-            for (int ni = 0; ni < BNC / 8; ++ni)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int n = n0 + (warp + mi * 4) * 16 + g + h * 8;
-                    const int c = c0 + ni * 8 + 2 * t;
-                    float *d = dw + ((size_t)tap * Cout + n) * Cin + c;
-                    atomicAdd(d, acc[mi][ni][2 * h]);
-                    atomicAdd(d + 1, acc[mi][ni][2 * h + 1]);
+                for (int tx = 0; tx < 3; ++tx) {
+                    uint32_t bf[4];
+                    ldsm_x4_trans(bf, &sX[tx][(k0 + b_pix) * PX + b_col]);
+                    mma_bf16_16816(acc[ty * 3 + tx][0], af, &bf[0]);
+                    mma_bf16_16816(acc[ty * 3 + tx][1], af, &bf[2]);
                 }
+            }
+            __syncthreads();   // before the next tap row (or tile) overwrites sX / sDy
+        }
     }
+    // partial sums of this chunk: part[chunk][tap][n][c]
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int n = n0 + nw + g + h * 8;
+                const int c = c0 + cw + ni * 8 + 2 * t;
+                float2 v = make_float2(acc[tap][ni][2 * h], acc[tap][ni][2 * h + 1]);
+                *reinterpret_cast<float2 *>(
+                    part + (((size_t)chunk * 9 + tap) * Cout + n) * Cin + c) = v;
+            }
+}
+
+// dw[i] += sum over chunks of part[chunk][i], chunks added in order.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, float *__restrict__ dw, size_t n,
+                                    int nchunk) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int ch = 0; ch < nchunk; ++ch) s += part[(size_t)ch * n + i];
+        dw[i] += s;
+    }
+}
+
+// Chunking of a weight-gradient launch (shared by the workspace query).
+struct WgPlan {
+    int bm, bc, ntiles, tiles_per_chunk, nchunk;
+};
+WgPlan wgrad_plan(int nb, int h, int w, int cin, int cout) {
+    WgPlan p;
+    p.bm = cout % 32 == 0 ? 32 : 16;
+    p.bc = cin % 32 == 0 ? 32 : 16;
+    p.ntiles = (int)((size_t)nb * h * w / kWgTile);
+    const int blocks = (cout / p.bm) * (cin / p.bc);
+    int want = (kWgTargetCtas + blocks - 1) / blocks;
+    if (want > p.ntiles) want = p.ntiles;
+    if (want < 1) want = 1;
+    p.tiles_per_chunk = (p.ntiles + want - 1) / want;
+    p.nchunk = (p.ntiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    return p;
 }
 
 // ---------------------------------------------------------------------------
@@ -441,25 +497,41 @@ int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int 
     NN_RET();
 }
 
+size_t lb_nn_wgrad_workspace(int nb, int h, int wd, int cin, int cout) {
+    if (nb < 1 || h < 1 || wd < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 ||
+        ((size_t)h * wd) % kWgTile)
+        return 0;
+    const WgPlan p = wgrad_plan(nb, h, wd, cin, cout);
+    return (size_t)p.nchunk * 9 * cout * cin * sizeof(float);
+}
+
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
-                        int wd, int cin, int cout, void *stream) {
-    if (!x || !dy || !dw || nb < 1 || h < 1 || wd < 1 || cin % 16 || cout % 16) return LB_ERR_ARG;
+                        int wd, int cin, int cout, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    if (!x || !dy || !dw || !workspace || nb < 1 || h < 1 || wd < 1 || cin < 16 || cout < 16 ||
+        cin % 16 || cout % 16 || ((size_t)h * wd) % kWgTile)
+        return LB_ERR_ARG;
+    if (workspace_bytes < lb_nn_wgrad_workspace(nb, h, wd, cin, cout)) return LB_ERR_ARG;
+    if (((uintptr_t)workspace) % 16) return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t P = (size_t)nb * h * wd;
-    const int chunk = 2048;
-    const int bm = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
-    const int bc = cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16);
-    dim3 grid((unsigned)((P + chunk - 1) / chunk), 9 * (cout / bm) * (cin / bc));
+    const WgPlan p = wgrad_plan(nb, h, wd, cin, cout);
     const bf16 *xb = (const bf16 *)x, *db = (const bf16 *)dy;
-#define WG(BM, BC) wgrad_kernel<BM, BC><<<grid, 128, 0, s>>>(xb, db, dw, nb, h, wd, cin, cout, chunk)
-    if (bm == 64) { if (bc == 64) WG(64, 64); else if (bc == 32) WG(64, 32); else WG(64, 16); }
-    else if (bm == 32) { if (bc == 64) WG(32, 64); else if (bc == 32) WG(32, 32); else WG(32, 16); }
-    else { if (bc == 64) WG(16, 64); else if (bc == 32) WG(16, 32); else WG(16, 16); }
+    float *part = (float *)workspace;
+    dim3 grid(cout / p.bm, cin / p.bc, p.nchunk);
+#define WG(BM, BC)                                                                              \
+    wgrad_kernel<BM, BC><<<grid, 32 * (BM / 16) * (BC / 16), 0, s>>>(xb, db, part, h, wd, cin, \
+                                                                     cout, p.ntiles,           \
+                                                                     p.tiles_per_chunk)
+    if (p.bm == 32) { if (p.bc == 32) WG(32, 32); else WG(32, 16); }
+    else { if (p.bc == 32) WG(16, 32); else WG(16, 16); }
 #undef WG
+    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    const size_t n = (size_t)9 * cout * cin;
+    wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, n, p.nchunk);
     if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
     if (dbias) {
         dim3 gb(256, (cout + 31) / 32);
-        bias_grad_kernel<<<gb, 256, 0, s>>>(db, dbias, P, cout);
+        bias_grad_kernel<<<gb, 256, 0, s>>>(db, dbias, (size_t)nb * h * wd, cout);
     }
     NN_RET();
 }

@@ -56,18 +56,37 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c) {
     }
 }
 
+// Mass and momentum deviations of one site added to FP64 running sums.  An
+// FP32 state combines its nine deviations in FP32 (the rounding of that
+// 9-term sum, ~2^-24 of the deviations, is at the storage precision itself)
+// and only the three site totals go through FP64, whose throughput on this
+// GPU is a small fraction of FP32's; an FP64 state is summed in FP64.
+__device__ __forceinline__ void add_site_moments(const float *__restrict__ df, size_t plane,
+                                                 size_t s, double &m, double &jx, double &jy) {
+    float g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = df[i * plane + s];
+    m += (double)(((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+    jx += (double)((g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]));
+    jy += (double)((g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]));
+}
+__device__ __forceinline__ void add_site_moments(const double *__restrict__ df, size_t plane,
+                                                 size_t s, double &m, double &jx, double &jy) {
+    double g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = df[i * plane + s];
+    m += ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+    jx += (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
+    jy += (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 conserved_partials_kernel(const T *__restrict__ df, size_t plane, double *__restrict__ partials) {
     double m = 0.0, jx = 0.0, jy = 0.0;
     for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < plane;
          s += (size_t)gridDim.x * blockDim.x) {
-        double g[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = (double)df[i * plane + s];
-        m += ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-        jx += (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
-        jy += (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+        add_site_moments(df, plane, s, m, jx, jy);
     }
     block_sum3(m, jx, jy);
     if (threadIdx.x == 0) {
@@ -134,12 +153,7 @@ conserved_chunk_kernel(const T *__restrict__ df, size_t plane, double *__restric
     size_t end = begin + kStaticSitesPerBlock;
     if (end > plane) end = plane;
     for (size_t s = begin + threadIdx.x; s < end; s += kRedThreads) {
-        double g[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = (double)df[i * plane + s];
-        m += ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-        jx += (g[1] - g[3]) + (g[5] - g[7]) + (g[8] - g[6]);
-        jy += (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+        add_site_moments(df, plane, s, m, jx, jy);
     }
     block_sum3(m, jx, jy);
     if (threadIdx.x == 0) {

@@ -77,6 +77,11 @@ class SurrogateNet:
         self.du3, self.da3, self.dz3, self.dp2 = z(n // 2, 128), z(n // 4, 128), z(n // 4, 128), z(n // 4, 64)
         self.da2, self.dz2, self.dp1 = z(n // 2, 64), z(n // 2, 64), z(n // 2, 32)
         self.da1, self.dz1, self.tmp2 = z(n, 32), z(n, 32), z(n // 2, 64)
+        sizes = [n, n // 2, n // 4, n // 2, n]
+        ws = max(self.L.lb_nn_wgrad_workspace(nb, h, h, ci, co)
+                 for h, (ci, co) in zip(sizes, LAYERS))
+        self.ws_bytes = ws
+        self.ws = t.empty(ws // 4, dtype=t.float32, device="cuda")
 
     def _conv(self, x, i, out, relu, h):
         ci, co = LAYERS[i]
@@ -102,7 +107,8 @@ class SurrogateNet:
         """Accumulate parameter gradients from self.dy (dL/dy)."""
         n, L, nb, s = self.n, self.L, self.nb, self.s
         wg = lambda inp, dz, i, h: _check(L.lb_nn_conv3x3_wgrad(
-            _p(inp), _p(dz), _p(self.dw[i]), _p(self.db[i]), nb, h, h, LAYERS[i][0], LAYERS[i][1], s), "wgrad")
+            _p(inp), _p(dz), _p(self.dw[i]), _p(self.db[i]), nb, h, h, LAYERS[i][0], LAYERS[i][1],
+            _p(self.ws), self.ws_bytes, s), "wgrad")
         dg = lambda dz, i, out, h: _check(L.lb_nn_conv3x3(
             _p(dz), _p(self.wb[i]), None, _p(out), nb, h, h, LAYERS[i][1], LAYERS[i][0], 0, 1, s), "dgrad")
         wg(self.u4, self.dy, 4, n)

@@ -19,7 +19,9 @@ def _lib():
     L = abi.load()
     P = C.c_void_p
     L.lb_nn_conv3x3.argtypes = [P, P, P, P] + [C.c_int] * 7 + [P]
-    L.lb_nn_conv3x3_wgrad.argtypes = [P, P, P, P] + [C.c_int] * 5 + [P]
+    L.lb_nn_conv3x3_wgrad.argtypes = [P, P, P, P] + [C.c_int] * 5 + [P, C.c_size_t, P]
+    L.lb_nn_wgrad_workspace.argtypes = [C.c_int] * 5
+    L.lb_nn_wgrad_workspace.restype = C.c_size_t
     L.lb_nn_pool2.argtypes = [P, P] + [C.c_int] * 5 + [P]
     L.lb_nn_up2.argtypes = [P, P] + [C.c_int] * 5 + [P]
     L.lb_nn_relu_mask.argtypes = [P, P, P, C.c_size_t, P]
@@ -91,11 +93,25 @@ def test_conv_weight_gradient(nb, h, w, cin, cout):
     dy = _bf((nb, h, w, cout), seed=6)
     dw = torch.zeros((9, cout, cin), device="cuda")
     db = torch.zeros(cout, device="cuda")
+    nbytes = L.lb_nn_wgrad_workspace(nb, h, w, cin, cout)
+    assert nbytes > 0
+    ws = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), _p(db), nb, h, w, cin, cout, _p(ws),
+                                 nbytes - 4, None) == -1          # short workspace
     for _ in range(2):                       # accumulates
-        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), _p(db), nb, h, w, cin, cout, None) == 0
+        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), _p(db), nb, h, w, cin, cout, _p(ws),
+                                     nbytes, None) == 0
     torch.cuda.synchronize()
+    first = dw.clone()
     _close(dw.cpu().numpy(), 2 * R.conv3x3_wgrad(_np(x), _np(dy)), 1e-3)
     _close(db.cpu().numpy(), 2 * _np(dy).sum(axis=(0, 1, 2)), 1e-3)
+    # deterministic: the same inputs give the same bits
+    dw.zero_()
+    for _ in range(2):
+        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), None, nb, h, w, cin, cout, _p(ws),
+                                     nbytes, None) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(dw, first)
 
 
 def test_pool_up_relu_adam():
