@@ -344,15 +344,18 @@ int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, flo
 int lb_nn_mse(const void *y, int c, const float *target, const float *base, size_t n, float *loss,
               void *dy, void *stream);
 /* Rollout update: FP32 state [n] += y[.][0]; channel 0 of the network input x
- * [n][cx] = BF16(state), other channels of x untouched. */
+ * [n][cx] = BF16(state), channel 2 (when cx > 2) = the increment y[.][0] just
+ * applied, other channels of x untouched. */
 int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, void *stream);
 /* Adam step (bias-corrected, `step` >= 1) on FP32 w with gradient g and moments
  * m, v; w_bf16 (may be NULL) receives the BF16 copy. */
 int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_t n, double lr,
                double b1, double b2, double eps, long long step, void *stream);
 /* Network input from an FP32 field src [n]: out [n][c] with channel 0 =
- * BF16(src), channel 1 = gfeat (the coupling feature), others 0. */
-int lb_nn_expand(const float *src, double gfeat, void *out, int c, size_t n, void *stream);
+ * BF16(src), channel 1 = gfeat (the coupling feature), channel 2 =
+ * BF16(src - prev) (the field's last increment; 0 when prev is NULL), others 0. */
+int lb_nn_expand(const float *src, const float *prev, double gfeat, void *out, int c, size_t n,
+                 void *stream);
 /* BF16 copy of FP32 values. */
 int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream);
 

@@ -152,7 +152,7 @@ def bind(L):
         "lb_nn_adam": (C.c_int, [P, P, P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_longlong, P]),
         "lb_nn_to_bf16": (C.c_int, [P, P, C.c_size_t, P]),
-        "lb_nn_expand": (C.c_int, [P, C.c_double, P, C.c_int, C.c_size_t, P]),
+        "lb_nn_expand": (C.c_int, [P, P, C.c_double, P, C.c_int, C.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

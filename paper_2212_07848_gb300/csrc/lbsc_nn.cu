@@ -412,14 +412,17 @@ __global__ void mse_kernel(const bf16 *__restrict__ y, int C, const float *__res
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
 }
 
-// Rollout update: state (FP32) += y[.][0]; channel 0 of the next network input
-// x [n][Cx] = BF16(state), its other channels untouched.
+// Rollout update: state (FP32) += y[.][0]; the next network input x [n][Cx]
+// gets channel 0 = BF16(state) and channel 2 = the increment y[.][0] just
+// applied; its other channels are untouched.
 __global__ void residual_kernel(float *__restrict__ state, const bf16 *__restrict__ y, int C,
                                 bf16 *__restrict__ x, int Cx, size_t n) {
     GRID_STRIDE(i, n) {
-        const float v = state[i] + __bfloat162float(y[i * C]);
+        const bf16 d = y[i * C];
+        const float v = state[i] + __bfloat162float(d);
         state[i] = v;
         x[i * Cx] = __float2bfloat16(v);
+        if (Cx > 2) x[i * Cx + 2] = d;
     }
 }
 
@@ -439,14 +442,16 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, 
 }
 
 // Network input from an FP32 field: out[i][0] = BF16(src[i]), out[i][1] = gfeat,
-// out[i][2..C) = 0.
-__global__ void expand_kernel(const float *__restrict__ src, float gfeat, bf16 *__restrict__ out,
-                              int C, size_t n) {
+// out[i][2] = BF16(src[i] - prev[i]) (the last increment; 0 without prev),
+// out[i][3..C) = 0.
+__global__ void expand_kernel(const float *__restrict__ src, const float *__restrict__ prev,
+                              float gfeat, bf16 *__restrict__ out, int C, size_t n) {
     GRID_STRIDE(i, n) {
         bf16 *o = out + i * C;
         o[0] = __float2bfloat16(src[i]);
         if (C > 1) o[1] = __float2bfloat16(gfeat);
-        for (int c = 2; c < C; ++c) o[c] = __float2bfloat16(0.f);
+        if (C > 2) o[2] = __float2bfloat16(prev ? src[i] - prev[i] : 0.f);
+        for (int c = 3; c < C; ++c) o[c] = __float2bfloat16(0.f);
     }
 }
 
@@ -599,10 +604,11 @@ int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_
     NN_RET();
 }
 
-int lb_nn_expand(const float *src, double gfeat, void *out, int c, size_t n, void *stream) {
+int lb_nn_expand(const float *src, const float *prev, double gfeat, void *out, int c, size_t n,
+                 void *stream) {
     if (!src || !out || c < 1) return LB_ERR_ARG;
-    expand_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(src, (float)gfeat, (bf16 *)out,
-                                                                   c, n);
+    expand_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(src, prev, (float)gfeat,
+                                                                   (bf16 *)out, c, n);
     NN_RET();
 }
 

@@ -186,14 +186,22 @@ def generate(n_traj, size, steps, stride, G_range=(-5.2, -4.4), coarse=4, kT=1e-
     return frames, Gs, time.perf_counter() - t0
 
 
-def expand(L, field, G, out, stream=None):
-    """16-channel BF16 network input [..][m][m][16] from an FP32 field [..][m][m]."""
-    _check(L.lb_nn_expand(_p(field), gfeat(G), _p(out), CIN, field.numel(), stream), "expand")
+def expand(L, field, G, out, prev=None, stream=None):
+    """16-channel BF16 network input [..][m][m][16] from an FP32 field [..][m][m]:
+    the field, the coupling feature and (with `prev`) the field's last increment."""
+    _check(L.lb_nn_expand(_p(field), _p(prev), gfeat(G), _p(out), CIN, field.numel(), stream),
+           "expand")
 
 
-def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=0):
-    """Adam on random (trajectory, time) pairs of consecutive frames.  Returns
-    the losses logged every `log_every` iterations."""
+def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=1, lr_end=None,
+          pushforward=0.0):
+    """Adam on random (trajectory, time) pairs of consecutive frames, the frame
+    before each pair giving the last-increment input; the learning rate decays
+    from `lr` to `lr_end` on a cosine (constant without `lr_end`).  With
+    probability `pushforward` an iteration first advances the batch one stride
+    with the network itself (no gradient) and trains on that prediction as the
+    input (the pushforward trick: the network learns to correct its own
+    rollout errors).  Returns the losses logged every `log_every` iterations."""
     import torch
     L = net.L
     if net.nb != net.batch:
@@ -206,23 +214,34 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
     nf = frames.shape[1]
     losses = []
     for it in range(iters):
+        pf = pushforward > 0.0 and rng.random() < pushforward
         for j in range(nb):
             k = int(rng.choice(train_ids))
-            f = int(rng.integers(t_min, nf - 1))
-            base[j].copy_(frames[k, f])
+            f = int(rng.integers(max(t_min, 2) if pf else t_min, nf - 1))
+            src = f - 1 if pf else f
+            base[j].copy_(frames[k, src])
             tgt[j].copy_(frames[k, f + 1])
-            expand(L, frames[k, f], Gs[k], x[j], net.s)
+            expand(L, frames[k, src], Gs[k], x[j], frames[k, src - 1] if src > 0 else None, net.s)
+        if pf:
+            # one stride by the network itself: base becomes its prediction of
+            # frame f, x the matching input (channel 2 = the increment)
+            net.forward(x)
+            _check(L.lb_nn_residual(_p(base), _p(net.y), 16, _p(x), CIN, nb * m * m, net.s),
+                   "residual")
         net.zero_grad()
         net.forward(x)
         loss = net.loss_and_grad(x, tgt, base)
         net.backward(x)
-        net.adam(lr)
+        if lr_end is None:
+            net.adam(lr)
+        else:
+            net.adam(lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(iters - 1, 1))))
         if log_every and it % log_every == 0:
             losses.append(float(loss.item()))
     return losses
 
 
-def one_step_mse(net, frames, Gs, ids, t_min=0):
+def one_step_mse(net, frames, Gs, ids, t_min=1):
     """Mean one-stride MSE of the surrogate and of persistence (no change) over
     all consecutive frame pairs of the trajectories `ids`, `net.nb` pairs per
     forward pass (unused slots of the last pass repeat its last pair)."""
@@ -239,7 +258,7 @@ def one_step_mse(net, frames, Gs, ids, t_min=0):
         for j, (k, f) in enumerate(chunk):
             base[j].copy_(frames[k, f])
             tgt[j].copy_(frames[k, f + 1])
-            expand(L, frames[k, f], Gs[k], x[j], net.s)
+            expand(L, frames[k, f], Gs[k], x[j], frames[k, f - 1] if f > 0 else None, net.s)
         net.forward(x)
         loss = net.loss_and_grad(x, tgt, base, grad=False)
         used = len(pairs[i:i + nb])
@@ -252,23 +271,58 @@ def one_step_mse(net, frames, Gs, ids, t_min=0):
     return s_net / len(pairs), s_id / len(pairs)
 
 
-def rollout(net, frame0, G, strides):
-    """Apply the surrogate `strides` times from an FP32 field [m][m]; the state
-    stays FP32 (only the network input is BF16).  Returns the FP32 fields after
-    each stride as one tensor [strides][m][m]."""
+def rollout(net, frame0, G, strides, prev0=None):
+    """Apply the surrogate `strides` times from an FP32 field [m][m] (and the
+    field one stride earlier, for the last-increment input); the state stays
+    FP32 (only the network input is BF16).  Returns the FP32 fields after each
+    stride as one tensor [strides][m][m]."""
     import torch
     L, m = net.L, net.n
     if net.nb != 1:
         net._alloc(1)
     x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
     state = frame0.clone()
-    expand(L, state, G, x, net.s)
+    expand(L, state, G, x, prev0, net.s)
     out = torch.empty((strides, m, m), dtype=torch.float32, device="cuda")
     for s in range(strides):
         net.forward(x)
         _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, net.s), "residual")
         out[s].copy_(state)
     return out
+
+
+def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
+    """Judge the surrogate against the solver: from frame f0 of each trajectory
+    in `ids` (with frame f0 - 1 for the increment input) roll out `nroll`
+    strides and compare with the solver's frames f0+1 .. f0+nroll.  Returns
+    the ensemble-mean domain size L(t) of both, their largest relative gap,
+    the largest per-trajectory L gap, and two measures of the ensemble-mean
+    radial S(k, t) gap, each the worst over the rollout: the largest relative
+    gap over the peak shells (solver S at least a quarter of its maximum) and
+    the L1 gap sum |S_sur - S_sol| / sum S_sol over all shells."""
+    Ls, Lr, Ss, Sr, per = [], [], [], [], []
+    for k in ids:
+        out = rollout(net, frames[k, f0].clone(), float(Gs[k]), nroll,
+                      frames[k, f0 - 1] if f0 > 0 else None).cpu().numpy()
+        ref = frames[k, f0 + 1:f0 + 1 + nroll].cpu().numpy()
+        a = [radial_sk(f) for f in out]
+        b = [radial_sk(f) for f in ref]
+        Ls.append([v[1] for v in a])
+        Lr.append([v[1] for v in b])
+        Ss.append([v[0] for v in a])
+        Sr.append([v[0] for v in b])
+        per.append(np.max(np.abs(np.array(Ls[-1]) - np.array(Lr[-1])) / np.array(Lr[-1])))
+    Ls, Lr = np.mean(Ls, axis=0), np.mean(Lr, axis=0)
+    Ss, Sr = np.mean(Ss, axis=0), np.mean(Sr, axis=0)
+    s_peak, s_l1 = 0.0, 0.0
+    for t in range(nroll):
+        sel = Sr[t] >= 0.25 * Sr[t].max()
+        s_peak = max(s_peak, float(np.max(np.abs(Ss[t][sel] - Sr[t][sel]) / Sr[t][sel])))
+        s_l1 = max(s_l1, float(np.abs(Ss[t] - Sr[t]).sum() / Sr[t].sum()))
+    return {"L_surrogate": Ls.tolist(), "L_solver": Lr.tolist(),
+            "L_mean_max_rel_err": float(np.max(np.abs(Ls - Lr) / Lr)),
+            "L_traj_max_rel_err": float(np.max(per)), "Sk_peak_max_rel_err": s_peak,
+            "Sk_l1_rel_err": s_l1}
 
 
 def radial_sk(field):

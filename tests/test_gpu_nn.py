@@ -165,11 +165,16 @@ def test_coarse_expand_mse_residual():
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-6
     n = out.numel()
     x = torch.empty((n, 16), dtype=torch.bfloat16, device="cuda")
-    assert L.lb_nn_expand(_p(out), 0.75, _p(x), 16, n, None) == 0
+    prev = out * 0.5
+    assert L.lb_nn_expand(_p(out), _p(prev), 0.75, _p(x), 16, n, None) == 0
     torch.cuda.synchronize()
     xe = _np(x)
     assert np.array_equal(xe[:, 0], out.to(torch.bfloat16).float().cpu().numpy().ravel())
-    assert np.all(xe[:, 1] == 0.75) and np.all(xe[:, 2:] == 0)
+    assert np.array_equal(xe[:, 2], (out - prev).to(torch.bfloat16).float().cpu().numpy().ravel())
+    assert np.all(xe[:, 1] == 0.75) and np.all(xe[:, 3:] == 0)
+    assert L.lb_nn_expand(_p(out), None, 0.75, _p(x), 16, n, None) == 0
+    torch.cuda.synchronize()
+    assert np.all(_np(x)[:, 2:] == 0)
     y = _bf((n, 16), 0.1, seed=9)
     base = out.flatten().clone()
     tgt = base + 0.05 * torch.randn(n, device="cuda")
@@ -190,3 +195,4 @@ def test_coarse_expand_mse_residual():
     xr = _np(x)
     assert np.array_equal(xr[:, 0], state.to(torch.bfloat16).float().cpu().numpy())
     assert np.all(xr[:, 1] == 0.75)
+    assert np.array_equal(xr[:, 2], _np(y)[:, 0])          # the increment just applied

@@ -77,16 +77,16 @@ def test_rollout_stable_and_faster_than_solver(trained):
     S, net, frames, Gs, _, _ = trained
     from paper_2212_07848_gb300.lattice import Lattice
     k, f0, strides = 10, 3, 8
-    out = S.rollout(net, frames[k, f0].clone(), float(Gs[k]), strides)
+    out = S.rollout(net, frames[k, f0].clone(), float(Gs[k]), strides, frames[k, f0 - 1])
     torch.cuda.synchronize()
     o = out.cpu().numpy()
     assert np.all(np.isfinite(o)) and np.abs(o).max() < 3.0
     # time per stride of the surrogate against the 200 solver steps it stands for
     x0 = frames[k, f0].clone()
-    S.rollout(net, x0, float(Gs[k]), 2)
+    S.rollout(net, x0, float(Gs[k]), 2, frames[k, f0 - 1])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S.rollout(net, x0, float(Gs[k]), 20)
+    S.rollout(net, x0, float(Gs[k]), 20, frames[k, f0 - 1])
     torch.cuda.synchronize()
     t_net = (time.perf_counter() - t0) / 20
     lat = Lattice(256, 256, float(Gs[k]), 1.0, 1e-6)
