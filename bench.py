@@ -292,6 +292,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch
 
     from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300 import replicas as R
     from paper_2212_07848_gb300.lattice import Lattice
 
     torch.cuda.set_device(local_rank)
@@ -301,7 +302,7 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl")
 
     lat = Lattice(NX, NY, G, TAU, KT, stencil=4, precision="fp32", device=local_rank)
-    lat.init(RHO0, SEED + rank, 0.0)
+    lat.init(RHO0, R.replica_seed(SEED, rank), 0.0)
     lat.sk_config(LB_PER_STEP, LB_PER_STEP)
     stream = torch.cuda.ExternalStream(lat.stream())
     bins = np.empty(NBINS)
@@ -346,12 +347,9 @@ def run_gpu(args, rank, world, local_rank):
     lat.sync()
     ms = start.elapsed_time(end)
     k1_ms = sum(a.elapsed_time(b) for a, b in k1_events) / (args.steps * (LB_PER_STEP - 1))
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = R.max_over_ranks(ms, dist, device="cuda")
     sites = NX * NY
-    value = world * sites * LB_PER_STEP * args.steps / (ms_max * 1e-3) / 1e6
+    value = R.whole_job_rate(sites * LB_PER_STEP * args.steps, world, ms_max * 1e-3) / 1e6
 
     # end-to-end through the C ABI with host buffers: per step, upload the
     # state from pinned host memory, run the interval, read back the density
@@ -372,10 +370,8 @@ def run_gpu(args, rank, world, local_rank):
         abi.lb_structure_factor(h, bins, NBINS)
     lat.sync()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * sites * LB_PER_STEP * e2e_steps / float(te.item()) / 1e6
+    e2e_max = R.max_over_ranks(e2e_s, dist, device="cuda")
+    e2e_value = R.whole_job_rate(sites * LB_PER_STEP * e2e_steps, world, e2e_max) / 1e6
 
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_SITE * sites / (k1_ms * 1e-3) / 1e9
@@ -434,15 +430,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2212_07848_gb300.replicas import rank_info
+    rank, world, local_rank = rank_info(1)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
         from paper_2212_07848_gb300 import build
-        if rank == 0 or world == 1:
-            build.build()
+        if world == 1:
+            build.build()   # under torchrun the library is built before launch
         run_gpu(args, rank, world, local_rank)
 
 

@@ -43,7 +43,8 @@ EXPORTED = [
     "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
-    "lb_nn_to_bf16", "lb_nn_expand", "lb_nn_wgrad_workspace",
+    "lb_nn_to_bf16", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
+    "lb_nn_status",
 ]
 
 
@@ -142,6 +143,8 @@ def bind(L):
         "lb_nn_conv3x3": (C.c_int, [P, P, P, P] + [C.c_int] * 7 + [P]),
         "lb_nn_conv3x3_wgrad": (C.c_int, [P, P, P, P] + [C.c_int] * 5 + [P, C.c_size_t, P]),
         "lb_nn_wgrad_workspace": (C.c_size_t, [C.c_int] * 5),
+        "lb_nn_set_conv_path": (C.c_int, [C.c_int]),
+        "lb_nn_status": (C.c_int, []),
         "lb_nn_relu_mask": (C.c_int, [P, P, P, C.c_size_t, P]),
         "lb_nn_pool2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
         "lb_nn_up2": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),

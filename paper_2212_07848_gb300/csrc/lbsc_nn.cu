@@ -6,10 +6,13 @@
 // density of a quench by a fixed stride; the plain lattice Boltzmann step
 // stays the reference it is judged against.
 //
-// Convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16 in, FP32
-// accumulate): M = output pixels (a 128-pixel row segment per CTA), N =
-// output channels, K = 9 taps x input channels; the im2col tile is gathered
-// with circular (periodic) padding straight from NHWC into shared memory.
+// The forward convolution runs on tcgen05 (lbsc_nn_tc.cu) for its output
+// channel counts; the mma.sync kernels here serve the input gradient, the
+// weight gradient and the forward path when it is selected for comparison.
+// They are implicit GEMMs on mma.sync m16n8k16 (BF16 in, FP32 accumulate):
+// M = output pixels (128 consecutive pixels per CTA), N = output channels,
+// K = 9 taps x input channels; the im2col tile is gathered with circular
+// (periodic) padding straight from NHWC into shared memory.
 // The input gradient is the same kernel run on dY with the taps mirrored and
 // the weight matrix transposed; the weight gradient is a GEMM over pixels.
 #include <cuda_bf16.h>
@@ -20,6 +23,12 @@
 #include "lbsc.h"
 
 namespace lbsc {
+
+// tcgen05 forward convolution (lbsc_nn_tc.cu) and the path selection.
+extern int nn_conv_path;
+cudaError_t launch_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int nb,
+                              int h, int wd, int cin, int cout, int relu, cudaStream_t s);
+
 namespace {
 
 using bf16 = __nv_bfloat16;
@@ -479,6 +488,11 @@ int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int 
         cout % 16 || cin < 16 || cout < 16)
         return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (!dgrad && nn_conv_path != 1) {
+        const cudaError_t e = launch_conv3x3_tc(x, w, bias, y, nb, h, wd, cin, cout, relu, s);
+        if (e == cudaSuccess) return LB_OK;
+        if (e != cudaErrorNotSupported) return LB_ERR_CUDA;
+    }
     // GEMM K channels = channels of the kernel's input, N = of its output
     dim3 grid((unsigned)((size_t)h * wd / 128), nb, 1);
     const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;

@@ -67,6 +67,7 @@ class SurrogateNet:
 
     def _alloc(self, nb):
         t, n, bf = self.torch, self.n, self.torch.bfloat16
+        self._stride_graph = None   # a captured stride refers to the old buffers
         z = lambda h, c: t.empty((nb, h, h, c), dtype=bf, device="cuda")
         self.nb = nb
         self.a1, self.p1, self.a2, self.p2 = z(n, 32), z(n // 2, 32), z(n // 2, 64), z(n // 4, 64)
@@ -271,19 +272,66 @@ def one_step_mse(net, frames, Gs, ids, t_min=1):
     return s_net / len(pairs), s_id / len(pairs)
 
 
-def rollout(net, frame0, G, strides, prev0=None):
+class _StrideGraph:
+    """One surrogate stride (network forward + residual update) captured once
+    as a CUDA graph on a private stream, on fixed input/state buffers."""
+
+    def __init__(self, net):
+        import torch
+        self.torch = torch
+        m = net.n
+        self.net = net
+        self.stream = torch.cuda.Stream()
+        self.x = torch.zeros((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
+        self.state = torch.zeros((m, m), dtype=torch.float32, device="cuda")
+        saved = net.s
+        net.s = self.stream.cuda_stream
+        try:
+            torch.cuda.synchronize()
+            with torch.cuda.stream(self.stream):
+                net.forward(self.x)          # first launches (kernel attributes) outside capture
+            self.stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream):
+                net.forward(self.x)
+                _check(net.L.lb_nn_residual(_p(self.state), _p(net.y), 16, _p(self.x), CIN, m * m,
+                                            net.s), "residual")
+        finally:
+            net.s = saved
+
+    def run(self, frame0, G, strides, prev0, out):
+        torch = self.torch
+        net = self.net
+        with torch.cuda.stream(self.stream):
+            self.stream.wait_stream(torch.cuda.current_stream())
+            self.state.copy_(frame0)
+            expand(net.L, self.state, G, self.x, prev0, self.stream.cuda_stream)
+            for s in range(strides):
+                self.graph.replay()
+                out[s].copy_(self.state)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return out
+
+
+def rollout(net, frame0, G, strides, prev0=None, graph=True):
     """Apply the surrogate `strides` times from an FP32 field [m][m] (and the
     field one stride earlier, for the last-increment input); the state stays
     FP32 (only the network input is BF16).  Returns the FP32 fields after each
-    stride as one tensor [strides][m][m]."""
+    stride as one tensor [strides][m][m].  With `graph` each stride replays a
+    CUDA graph captured on the first call."""
     import torch
     L, m = net.L, net.n
     if net.nb != 1:
         net._alloc(1)
+        net._stride_graph = None
+    out = torch.empty((strides, m, m), dtype=torch.float32, device="cuda")
+    if graph:
+        if getattr(net, "_stride_graph", None) is None:
+            net._stride_graph = _StrideGraph(net)
+        return net._stride_graph.run(frame0, G, strides, prev0, out)
     x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
     state = frame0.clone()
     expand(L, state, G, x, prev0, net.s)
-    out = torch.empty((strides, m, m), dtype=torch.float32, device="cuda")
     for s in range(strides):
         net.forward(x)
         _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, net.s), "residual")

@@ -58,12 +58,16 @@ def _close_bf16(got, ref, tol=2e-3):
 
 
 CONV = [(2, 4, 128, 16, 32), (1, 3, 256, 64, 128), (2, 2, 128, 128, 64), (1, 2, 128, 32, 16),
-        (2, 16, 16, 64, 32)]   # last: tiles span rows (h w % 128 == 0 only)
+        (2, 16, 16, 64, 32),   # tiles span rows (h w % 128 == 0 only)
+        (1, 6, 128, 32, 128)]  # several 128-pixel tiles, widest tcgen05 N
 
 
+@pytest.mark.parametrize("path", [0, 1, 2])    # auto, mma.sync, tcgen05 (TMEM accumulator)
 @pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
-def test_conv_forward(nb, h, w, cin, cout):
+def test_conv_forward(nb, h, w, cin, cout, path):
+    from paper_2212_07848_gb300 import abi
     L = _lib()
+    assert L.lb_nn_set_conv_path(path) == 0
     x = _bf((nb, h, w, cin), seed=1)
     wt = _bf((9, cout, cin), 0.1, seed=2)
     b = torch.randn(cout, device="cuda")
@@ -73,6 +77,8 @@ def test_conv_forward(nb, h, w, cin, cout):
         torch.cuda.synchronize()
         ref = R.conv3x3(_np(x), _np(wt), b.cpu().numpy(), bool(relu))
         _close_bf16(_np(y), ref)
+    assert L.lb_nn_status() == abi.LB_OK             # no tensor-core wait gave up
+    assert L.lb_nn_set_conv_path(0) == 0
 
 
 @pytest.mark.parametrize("nb,h,w,cin,cout", CONV)

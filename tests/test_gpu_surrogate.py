@@ -81,6 +81,10 @@ def test_rollout_stable_and_faster_than_solver(trained):
     torch.cuda.synchronize()
     o = out.cpu().numpy()
     assert np.all(np.isfinite(o)) and np.abs(o).max() < 3.0
+    # the captured-graph rollout replays exactly the eager one
+    eager = S.rollout(net, frames[k, f0].clone(), float(Gs[k]), strides, frames[k, f0 - 1],
+                      graph=False)
+    assert torch.equal(eager, out)
     # time per stride of the surrogate against the 200 solver steps it stands for
     x0 = frames[k, f0].clone()
     S.rollout(net, x0, float(Gs[k]), 2, frames[k, f0 - 1])
