@@ -1,0 +1,57 @@
+"""Time one 3x3 convolution layer of the surrogate through the C ABI.
+
+    python -m paper_2212_07848_gb300.convbench --nb 8 --h 128 --cin 64 --cout 128 --path 0
+
+Runs the forward convolution (bias + ReLU) `--iters` times on random BF16
+inputs after `--warmup` calls and prints the mean time per call and the
+achieved TFLOP/s (2 * 9 * cin * cout FLOP per output pixel).  `--path`
+selects the kernel (0 automatic, 1 mma.sync, 2 tcgen05) as in
+`lb_nn_set_conv_path`.
+"""
+import argparse
+import ctypes as C
+
+from . import abi
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--nb", type=int, default=8)
+    ap.add_argument("--h", type=int, default=128)
+    ap.add_argument("--cin", type=int, default=64)
+    ap.add_argument("--cout", type=int, default=128)
+    ap.add_argument("--path", type=int, default=0)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--iters", type=int, default=3)
+    a = ap.parse_args()
+    import torch
+    L = abi.load()
+    p = lambda t: C.c_void_p(t.data_ptr())
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((a.nb, a.h, a.h, a.cin), generator=g).to(torch.bfloat16).cuda()
+    w = (0.1 * torch.randn((9, a.cout, a.cin), generator=g)).to(torch.bfloat16).cuda()
+    b = torch.zeros(a.cout, device="cuda")
+    y = torch.empty((a.nb, a.h, a.h, a.cout), dtype=torch.bfloat16, device="cuda")
+    if L.lb_nn_set_conv_path(a.path) != 0:
+        raise SystemExit("bad --path")
+    call = lambda: L.lb_nn_conv3x3(p(x), p(w), p(b), p(y), a.nb, a.h, a.h, a.cin, a.cout, 1, 0,
+                                   None)
+    for _ in range(a.warmup):
+        if call() != 0:
+            raise SystemExit("lb_nn_conv3x3 failed")
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(a.iters):
+        call()
+    e.record()
+    e.synchronize()
+    if L.lb_nn_status() != 0:
+        raise SystemExit("a tensor-core wait gave up")
+    ms = s.elapsed_time(e) / a.iters
+    flop = 2.0 * 9 * a.cin * a.cout * a.nb * a.h * a.h
+    print(f"{a.nb}x{a.h}^2 {a.cin}->{a.cout} path {a.path}: {ms * 1e3:.1f} us, "
+          f"{flop / ms / 1e9:.1f} TFLOP/s")
+
+
+if __name__ == "__main__":
+    main()
