@@ -142,12 +142,14 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
     """Batched ensemble vs the plain per-replica method on the same GPU: 256
     replicas with sides drawn from {64, 128, 256, 512}, G ~ U[-4.8, -3.6],
     rho0 = ln2 (1 + U[-0.1, 0.1]), kT = 1e-6, S(k) every 50 steps.  The
-    ensemble runs as one launch per step (captured graphs) with an autotuned
-    strip height; the plain method steps each replica's own context in turn
-    on one stream.  Both draw the same noise, so every replica's S(k) must
-    agree."""
+    ensemble runs with an autotuned strip height, once with one launch per
+    step and once with one persistent launch per window of steps (both from
+    captured graphs; the faster counts); the plain method steps each
+    replica's own context in turn on one stream.  All draw the same noise, so
+    every replica's S(k) must agree."""
     import torch
 
+    from paper_2212_07848_gb300 import abi
     from paper_2212_07848_gb300.ensemble import Ensemble
     from paper_2212_07848_gb300.lattice import Lattice
     rng = np.random.default_rng(seed)
@@ -157,18 +159,26 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
     reps = [(int(n), int(n), float(g), 1.0, 1e-6, float(r)) for n, g, r in zip(sizes, Gs, rhos)]
     sites = sum(r[0] * r[1] for r in reps)
     stream = torch.cuda.ExternalStream(stream_ptr)
-    ens = Ensemble(reps, seed=seed, stream=stream_ptr)
-    ens.init(0.0)
-    ens.sk_config(50, 50)
-    strip = ens.autotune(10)
-    ens.step(50)
-    ens.sync()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    ens.step(steps)
-    b.record(stream)
-    b.synchronize()
-    ens_ms = a.elapsed_time(b)
+    timings = {}
+    for mode in (abi.LB_ENS_PER_STEP, abi.LB_ENS_PERSISTENT):
+        e = Ensemble(reps, seed=seed, stream=stream_ptr)
+        e.set_launch(mode)
+        e.init(0.0)
+        e.sk_config(50, 50)
+        strip = e.autotune(10)
+        e.step(50)
+        e.sync()
+        a.record(stream)
+        e.step(steps)
+        b.record(stream)
+        b.synchronize()
+        timings[mode] = a.elapsed_time(b)
+        if mode == abi.LB_ENS_PERSISTENT:
+            ens = e
+        else:
+            e.close()
+    ens_ms = min(timings.values())
     lats = []
     for r, (nx, ny, g, tau, kT, rho0) in enumerate(reps):
         lat = Lattice(nx, ny, g, tau, kT, stream=stream_ptr)
@@ -192,6 +202,9 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
         lat.close()
     ens.close()
     return {"replicas": nrep, "sites": sites, "steps": steps, "strip_h": strip,
+            "per_step_launch_mlups": sites * steps / (timings[abi.LB_ENS_PER_STEP] * 1e-3) / 1e6,
+            "persistent_launch_mlups":
+                sites * steps / (timings[abi.LB_ENS_PERSISTENT] * 1e-3) / 1e6,
             "ensemble_mlups": sites * steps / (ens_ms * 1e-3) / 1e6,
             "sequential_mlups": sites * steps / (seq_ms * 1e-3) / 1e6,
             "speedup": seq_ms / ens_ms, "sk_max_rel_diff": worst,

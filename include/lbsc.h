@@ -284,7 +284,19 @@ int lb_ens_set_strip_height(lb_ens *e, int rows);
  * keep the fastest, and cache it in cache_path ("key strip" lines; may be
  * NULL).  *chosen (may be NULL) receives the strip height. */
 int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *chosen);
-/* Advance every replica n steps (asynchronous). */
+/* How lb_ens_step launches the steps.  LB_ENS_PER_STEP: one launch per step
+ * over every replica's tiles.  LB_ENS_PERSISTENT: each window of steps
+ * (32 plain steps, or one S(k) sampling interval) is one cooperative
+ * persistent launch in which a tile of a replica waits (bounded, 2 s) until
+ * all tiles of that replica finished the previous step; a timeout makes the
+ * next sync return LB_ERR_TIMEOUT.  Both give the same bits.
+ * LB_ERR_UNSUPPORTED if the device cannot launch cooperatively. */
+#define LB_ENS_PER_STEP 0
+#define LB_ENS_PERSISTENT 1
+int lb_ens_set_launch(lb_ens *e, int mode);
+int lb_ens_get_launch(const lb_ens *e);
+/* Advance every replica n steps (asynchronous); windows of steps replay
+ * captured CUDA graphs. */
 int lb_ens_step(lb_ens *e, int n);
 int lb_ens_sync(lb_ens *e);
 long long lb_ens_get_step(const lb_ens *e);

@@ -40,7 +40,8 @@ EXPORTED = [
     "lb_ens_create", "lb_ens_destroy", "lb_ens_init", "lb_ens_sk_config",
     "lb_ens_set_strip_height", "lb_ens_autotune", "lb_ens_step", "lb_ens_sync",
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
-    "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments",
+    "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments", "lb_ens_set_launch",
+    "lb_ens_get_launch",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
     "lb_nn_to_bf16", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
@@ -132,6 +133,8 @@ def bind(L):
         "lb_ens_set_strip_height": (C.c_int, [P, C.c_int]),
         "lb_ens_autotune": (C.c_int, [P, C.c_int, C.c_char_p, C.POINTER(C.c_int)]),
         "lb_ens_step": (C.c_int, [P, C.c_int]),
+        "lb_ens_set_launch": (C.c_int, [P, C.c_int]),
+        "lb_ens_get_launch": (C.c_int, [P]),
         "lb_ens_sync": (C.c_int, [P]),
         "lb_ens_get_step": (C.c_longlong, [P]),
         "lb_ens_num_tiles": (C.c_int, [P]),
@@ -339,6 +342,17 @@ def lb_ens_init(h, init_amp=0.0):
 
 def lb_ens_sk_config(h, every, start):
     _check(load().lb_ens_sk_config(h, int(every), int(start)), "lb_ens_sk_config")
+
+
+LB_ENS_PER_STEP, LB_ENS_PERSISTENT = 0, 1
+
+
+def lb_ens_set_launch(h, mode):
+    _check(load().lb_ens_set_launch(h, int(mode)), "lb_ens_set_launch")
+
+
+def lb_ens_get_launch(h):
+    return load().lb_ens_get_launch(h)
 
 
 def lb_ens_set_strip_height(h, rows):

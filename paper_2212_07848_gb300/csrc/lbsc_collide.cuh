@@ -30,21 +30,28 @@ __device__ __forceinline__ int wrap_once(int a, int n) {
 }
 
 // Pull streaming of one site: g_i(x) = f*_i(x - c_i).  32-bit element
-// indices (the context requires 9 nx ny < 2^32).
-template <typename T>
+// indices (the context requires 9 nx ny < 2^32).  CG: load through L2 only
+// (ld.global.cg) instead of the read-only path, for kernels in which the
+// source buffer was written earlier in the same launch.
+template <bool CG = false, typename T>
+__device__ __forceinline__ T ldsrc(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+template <bool CG = false, typename T>
 __device__ __forceinline__ void pull(const T *__restrict__ src, size_t plane_, int nx, int xc,
                                      int xm, int xp, int yc, int ym, int yp, T g[9]) {
     const uint32_t plane = (uint32_t)plane_;
     const uint32_t rc = (uint32_t)yc * nx, rm = (uint32_t)ym * nx, rp = (uint32_t)yp * nx;
-    g[0] = __ldg(src + (0u * plane + rc + xc));
-    g[1] = __ldg(src + (1u * plane + rc + xm));
-    g[2] = __ldg(src + (2u * plane + rm + xc));
-    g[3] = __ldg(src + (3u * plane + rc + xp));
-    g[4] = __ldg(src + (4u * plane + rp + xc));
-    g[5] = __ldg(src + (5u * plane + rm + xm));
-    g[6] = __ldg(src + (6u * plane + rm + xp));
-    g[7] = __ldg(src + (7u * plane + rp + xp));
-    g[8] = __ldg(src + (8u * plane + rp + xm));
+    g[0] = ldsrc<CG>(src + (0u * plane + rc + xc));
+    g[1] = ldsrc<CG>(src + (1u * plane + rc + xm));
+    g[2] = ldsrc<CG>(src + (2u * plane + rm + xc));
+    g[3] = ldsrc<CG>(src + (3u * plane + rc + xp));
+    g[4] = ldsrc<CG>(src + (4u * plane + rp + xc));
+    g[5] = ldsrc<CG>(src + (5u * plane + rm + xm));
+    g[6] = ldsrc<CG>(src + (6u * plane + rm + xp));
+    g[7] = ldsrc<CG>(src + (7u * plane + rp + xp));
+    g[8] = ldsrc<CG>(src + (8u * plane + rp + xm));
 }
 
 // 1/rho: FP32 from the reciprocal square root squared; FP64 correctly rounded.

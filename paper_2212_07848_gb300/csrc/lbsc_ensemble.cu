@@ -14,7 +14,9 @@
 // steps can be replayed for any step range.  S(k) of all replicas is sampled
 // by batched FFT kernels over (replica, row pair) and (replica, column tile)
 // descriptors.  An autotuner times candidate strip heights on a snapshot of
-// the state and caches the choice.
+// the state and caches the choice.  Alternatively (lb_ens_set_launch) a
+// window of steps runs as one persistent cooperative launch with per-replica
+// completion barriers, captured in the same graphs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -61,8 +63,40 @@ struct EnsKeys {
     uint32_t rk[20];
 };
 
+// Kernel parameters of one tile of replica R at step t (current buffer cur).
+__device__ __forceinline__ void fill_tile_params(KParams<float> &sp, const EnsRep &R,
+                                                 const EnsTile &tile, uint32_t t, int cur,
+                                                 bool sample, int *flag) {
+    sp.src = R.buf[cur];
+    sp.dst = R.buf[cur ^ 1];
+    sp.drho_out = sample ? R.drho : nullptr;
+    sp.flag = flag;
+    sp.nx = R.nx;
+    sp.ny = R.ny;
+    sp.strip_h = tile.y1 - tile.y0;
+    sp.psi_kind = R.psi_kind;
+    sp.noise = R.noise;
+    sp.step = t;
+    sp.replica = R.replica;
+    sp.rho0 = R.rho0;
+    sp.force_pref = R.force_pref;
+    sp.psi_c = R.psi_c;
+    sp.psi_b = R.psi_b;
+    sp.psi0 = R.psi0;
+    sp.gamma = R.gamma;
+    sp.gamma_b = R.gamma;
+    sp.gamma_g = R.gamma;
+    sp.c3a = R.c3a;
+    sp.c3b = R.c3b;
+    sp.c4a = R.c4a;
+    sp.c4b = R.c4b;
+    sp.c5a = R.c5a;
+    sp.c5b = R.c5b;
+    for (int k = 0; k < 6; ++k) sp.amp[k] = R.amp[k];
+}
+
 template <int ORDER>
-__global__ void __launch_bounds__(kStepTX + 32)
+__global__ void __launch_bounds__(kStepTX + 32, ORDER == 4 ? 6 : 4)
 ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles, int ntiles,
                 EnsClock *clk, int *flag, const EnsKeys keys, int sk_every, long long sk_start) {
     __shared__ KParams<float> sp;
@@ -77,32 +111,7 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
         const long long tn = (long long)t + 1;
         const bool sample =
             R.drho && sk_every > 0 && tn >= sk_start && (tn - sk_start) % sk_every == 0;
-        sp.src = R.buf[cur];
-        sp.dst = R.buf[cur ^ 1];
-        sp.drho_out = sample ? R.drho : nullptr;
-        sp.flag = flag;
-        sp.nx = R.nx;
-        sp.ny = R.ny;
-        sp.strip_h = tile.y1 - tile.y0;
-        sp.psi_kind = R.psi_kind;
-        sp.noise = R.noise;
-        sp.step = t;
-        sp.replica = R.replica;
-        sp.rho0 = R.rho0;
-        sp.force_pref = R.force_pref;
-        sp.psi_c = R.psi_c;
-        sp.psi_b = R.psi_b;
-        sp.psi0 = R.psi0;
-        sp.gamma = R.gamma;
-        sp.gamma_b = R.gamma;
-        sp.gamma_g = R.gamma;
-        sp.c3a = R.c3a;
-        sp.c3b = R.c3b;
-        sp.c4a = R.c4a;
-        sp.c4b = R.c4b;
-        sp.c5a = R.c5a;
-        sp.c5b = R.c5b;
-        for (int k = 0; k < 6; ++k) sp.amp[k] = R.amp[k];
+        fill_tile_params(sp, R, tile, t, cur, sample, flag);
         s_sample = sample ? 1 : 0;
         s_t = t;
         s_cur = cur;
@@ -123,6 +132,110 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
             clk->cur = s_cur ^ 1;
             __threadfence();
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent variant: one cooperative launch advances every replica by
+// `nsteps` steps.  CTA c takes tiles c, c + gridDim.x, ... of every step in
+// turn.  A tile of replica r at step s may start once all tiles of r have
+// finished step s - 1 (a per-replica completion counter, bounded wait), which
+// is all it reads; every CTA finishes all its step-(s-1) tiles before any
+// step-s tile, and all CTAs are resident, so the waits always end.  The
+// buffers alternate inside the launch, so pulls go through L2
+// (ld.global.cg), not the read-only path.  The last CTA to finish resets the
+// counters and advances the device clock.
+// ---------------------------------------------------------------------------
+struct EnsCtl {
+    uint32_t finished;
+    int abort;
+};
+constexpr uint64_t kEnsWaitNs = 2000000000ull;   // 2 s bound on a replica barrier
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ens_global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// 1: the counter reached target; 0: another CTA aborted; -1: timed out.
+__device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abort) {
+    if (ld_acquire_u32(cnt) >= target) return 1;
+    const uint64_t t0 = ens_global_ns();
+    for (;;) {
+        if (ld_acquire_u32(cnt) >= target) return 1;
+        if (*(volatile const int *)abort) return 0;
+        if (ens_global_ns() - t0 > kEnsWaitNs) return -1;
+        __nanosleep(100);
+    }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kStepTX + 32, ORDER == 4 ? 6 : 4)
+ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles,
+                   int ntiles, const int *__restrict__ rep_ntiles, uint32_t *done, int nrep,
+                   EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys, int nsteps,
+                   int sample_last) {
+    __shared__ KParams<float> sp;
+    __shared__ int s_go, s_last;
+    const uint32_t t0 = __ldcg(&clk->t);
+    const int cur0 = __ldcg(&clk->cur);
+    bool go = true;
+    for (int s = 0; s < nsteps && go; ++s) {
+        const bool sample = sample_last && s == nsteps - 1;
+        for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+            const EnsTile tile = tiles[i];
+            if (threadIdx.x == 0) {
+                int w = 1;
+                if (s > 0) w = wait_replica(&done[tile.r], (uint32_t)s * rep_ntiles[tile.r],
+                                            &ctl->abort);
+                if (w < 0) {
+                    atomicOr(flag, LB_STEP_TIMEOUT);
+                    atomicExch(&ctl->abort, 1);
+                }
+                if (w > 0) {
+                    const EnsRep &R = reps[tile.r];
+                    fill_tile_params(sp, R, tile, t0 + (uint32_t)s, cur0 ^ (s & 1),
+                                     sample && R.drho, flag);
+                }
+                s_go = w > 0;
+            }
+            __syncthreads();
+            if (!s_go) {
+                go = false;
+                break;
+            }
+            if (sp.drho_out)
+                step_strip<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            else
+                step_strip<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            __syncthreads();   // the tile's stores are done, and sp may be refilled
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&done[tile.r], 1u);
+            }
+        }
+    }
+    // the last CTA to finish resets the barriers and advances the clock
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl->finished, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int r = threadIdx.x; r < nrep; r += blockDim.x) done[r] = 0;
+        if (threadIdx.x == 0) {
+            ctl->finished = 0;
+            ctl->abort = 0;
+            clk->t = t0 + (uint32_t)nsteps;
+            clk->cur = cur0 ^ (nsteps & 1);
+            clk->done = 0;
+        }
+        __threadfence();
     }
 }
 
@@ -190,6 +303,11 @@ struct lb_ens {
     long long sk_start = 0, sk_count = 0;
     cudaGraphExec_t graph_plain = nullptr;     // kGraphSteps steps, no sampling
     cudaGraphExec_t graph_window = nullptr;    // sk_every steps, sampling at the last
+    int launch_mode = LB_ENS_PER_STEP;         // LB_ENS_PER_STEP or LB_ENS_PERSISTENT
+    int *d_rep_ntiles = nullptr;               // tiles per replica (persistent barriers)
+    uint32_t *d_done = nullptr;                // per-replica completion counters
+    EnsCtl *d_ctl = nullptr;
+    int persist_grid = 0;                      // co-resident CTAs of the persistent kernel
 };
 
 namespace {
@@ -250,16 +368,23 @@ int build_tiles(lb_ens *e) {
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long)e->reps[a].nx * e->reps[a].ny > (long)e->reps[b].nx * e->reps[b].ny;
     });
+    std::vector<int> per_rep(e->nrep, 0);
     for (int r : order) {
         const int nx = e->reps[r].nx, ny = e->reps[r].ny;
         const int h = std::min(e->strip_h, ny);
         for (int y0 = 0; y0 < ny; y0 += h)
-            for (int x0 = 0; x0 < nx; x0 += kStepTX) tiles.push_back({r, x0, y0, std::min(y0 + h, ny)});
+            for (int x0 = 0; x0 < nx; x0 += kStepTX) {
+                tiles.push_back({r, x0, y0, std::min(y0 + h, ny)});
+                per_rep[r] += 1;
+            }
     }
     if (e->d_tiles) cudaFree(e->d_tiles);
     e->d_tiles = nullptr;
     ENS_CHECK(cudaMalloc(&e->d_tiles, tiles.size() * sizeof(EnsTile)));
     ENS_CHECK(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
+                         cudaMemcpyHostToDevice));
+    if (!e->d_rep_ntiles) ENS_CHECK(cudaMalloc(&e->d_rep_ntiles, e->nrep * sizeof(int)));
+    ENS_CHECK(cudaMemcpy(e->d_rep_ntiles, per_rep.data(), e->nrep * sizeof(int),
                          cudaMemcpyHostToDevice));
     e->ntiles = (int)tiles.size();
     drop_graphs(e);
@@ -269,6 +394,33 @@ int build_tiles(lb_ens *e) {
 // One step of every replica; `sample` also runs the S(k) sample of all
 // replicas (the step kernel then writes delta rho: the device decides from
 // its own step counter, which agrees with the host's).
+template <int ORDER>
+cudaError_t launch_persist_t(lb_ens *e, int nsteps, int sample_last) {
+    void *args[] = {&e->d_reps, &e->d_tiles,  &e->ntiles, &e->d_rep_ntiles,
+                    &e->d_done, &e->nrep,     &e->d_ctl,  &e->d_clk,
+                    &e->d_flag, &e->keys,     &nsteps,    &sample_last};
+    const int grid = std::min(e->persist_grid, e->ntiles);
+    return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER>, dim3(grid),
+                                       dim3(kStepTX + 32), args, 0, e->stream);
+}
+
+// `nsteps` steps of every replica in one persistent launch (the last one
+// sampling if sample_last), then the S(k) sample when sampling.
+cudaError_t launch_ens_persistent(lb_ens *e, int nsteps, bool sample_last) {
+    const int sl = sample_last ? 1 : 0;
+    cudaError_t err = e->stencil == 4   ? launch_persist_t<4>(e, nsteps, sl)
+                      : e->stencil == 6 ? launch_persist_t<6>(e, nsteps, sl)
+                                        : launch_persist_t<8>(e, nsteps, sl);
+    if (err != cudaSuccess || !sample_last) return err;
+    ens_rows_kernel<<<e->nrows, 512, (size_t)e->max_nx * sizeof(float2), e->stream>>>(e->d_reps,
+                                                                                       e->d_rows);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    ens_cols_kernel<<<e->ncols, 512, (size_t)e->cpb * e->max_ny * sizeof(float2), e->stream>>>(
+        e->d_reps, e->d_cols, e->cpb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ens_step(lb_ens *e, bool sample) {
     const int sk_every = sample ? e->sk_every : 0;
     if (e->stencil == 4)
@@ -301,8 +453,11 @@ int capture(lb_ens *e, int steps, bool sample_last, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     ENS_CHECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
-    for (int s = 0; s < steps && err == cudaSuccess; ++s)
-        err = launch_ens_step(e, sample_last && s == steps - 1);
+    if (e->launch_mode == LB_ENS_PERSISTENT)
+        err = launch_ens_persistent(e, steps, sample_last);
+    else
+        for (int s = 0; s < steps && err == cudaSuccess; ++s)
+            err = launch_ens_step(e, sample_last && s == steps - 1);
     cudaError_t err2 = cudaStreamEndCapture(e->stream, &g);
     if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -327,6 +482,9 @@ void free_ens(lb_ens *e) {
     cudaFree(e->d_io);
     cudaFree(e->d_partials);
     cudaFree(e->d_out);
+    cudaFree(e->d_rep_ntiles);
+    cudaFree(e->d_done);
+    cudaFree(e->d_ctl);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
 }
 
@@ -404,6 +562,20 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
     if (err == cudaSuccess) err = cudaMalloc(&e->d_partials, 3 * (size_t)e->nred * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_out, 4 * sizeof(double));
     if (err == cudaSuccess) err = cudaMemset(e->d_flag, 0, sizeof(int));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_done, nrep * sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMemset(e->d_done, 0, nrep * sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl, sizeof(EnsCtl));
+    if (err == cudaSuccess) err = cudaMemset(e->d_ctl, 0, sizeof(EnsCtl));
+    if (err == cudaSuccess) {
+        int per_sm = 0, nsm = 0;
+        const void *k = stencil == 4   ? (const void *)ens_persist_kernel<4>
+                        : stencil == 6 ? (const void *)ens_persist_kernel<6>
+                                       : (const void *)ens_persist_kernel<8>;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStepTX + 32, 0);
+        if (err == cudaSuccess)
+            err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->dev);
+        e->persist_grid = per_sm * nsm;
+    }
     if (err != cudaSuccess) {
         free_ens(e);
         delete e;
@@ -534,6 +706,21 @@ int lb_ens_set_strip_height(lb_ens *e, int rows) {
     e->strip_h = rows;
     return build_tiles(e);
 }
+
+int lb_ens_set_launch(lb_ens *e, int mode) {
+    if (!e || (mode != LB_ENS_PER_STEP && mode != LB_ENS_PERSISTENT)) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    if (mode == LB_ENS_PERSISTENT) {
+        int coop = 0;
+        ENS_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, e->dev));
+        if (!coop || e->persist_grid < 1) return LB_ERR_UNSUPPORTED;
+    }
+    e->launch_mode = mode;
+    drop_graphs(e);
+    return LB_OK;
+}
+
+int lb_ens_get_launch(const lb_ens *e) { return e ? e->launch_mode : LB_ERR_ARG; }
 
 int lb_ens_step(lb_ens *e, int n) {
     if (!e || n < 0) return LB_ERR_ARG;

@@ -16,8 +16,9 @@ namespace lbsc {
 // of the lattice described by p (the CTA has kStepTX + 32 threads).  Shared
 // by the single-lattice kernel and the batched ensemble kernel.
 // rk: the Philox round keys (kept apart from p so that callers can serve
-// them from the constant bank).
-template <typename T, int ORDER, bool SAMPLE>
+// them from the constant bank).  CG: pull through L2 only (the source was
+// written earlier in the same launch, as in the persistent ensemble kernel).
+template <typename T, int ORDER, bool SAMPLE, bool CG = false>
 __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *__restrict__ rk,
                                            int x0, int y0, int y1) {
     using S = Stencil<ORDER>;
@@ -69,7 +70,7 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
         const int yc = wrap_once(y0 - H, ny);
         const int ym = yc == 0 ? ny - 1 : yc - 1;
         const int yp = yc == ny - 1 ? 0 : yc + 1;
-        if (active) pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+        if (active) pull<CG>(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
     }
 #pragma unroll 2
     for (int it = 0; it < it_end; ++it) {
@@ -81,7 +82,7 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
             const int yc = wrap_once(y0 - H + it + 1, ny);
             const int ym = yc == 0 ? ny - 1 : yc - 1;
             const int yp = yc == ny - 1 ? 0 : yc + 1;
-            pull(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+            pull<CG>(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
         }
         const int yy = y0 - H + it;
         if (active)

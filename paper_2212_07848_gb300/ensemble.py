@@ -35,6 +35,14 @@ class Ensemble:
     def sk_config(self, every, start):
         abi.lb_ens_sk_config(self._h, every, start)
 
+    def set_launch(self, mode):
+        """abi.LB_ENS_PER_STEP or abi.LB_ENS_PERSISTENT."""
+        abi.lb_ens_set_launch(self._h, mode)
+
+    @property
+    def launch(self):
+        return abi.lb_ens_get_launch(self._h)
+
     def set_strip_height(self, rows):
         abi.lb_ens_set_strip_height(self._h, rows)
 

@@ -26,10 +26,13 @@ def _single(r, rep, seed, amp, sk=None):
     return g
 
 
+@pytest.mark.parametrize("launch", [0, 1])        # per-step launches, persistent windows
 @pytest.mark.parametrize("strip", [8, 32])
-def test_replicas_match_single_lattices(strip):
+def test_replicas_match_single_lattices(strip, launch):
     from paper_2212_07848_gb300.ensemble import Ensemble
     e = Ensemble(REPS, seed=77)
+    e.set_launch(launch)
+    assert e.launch == launch
     e.set_strip_height(strip)
     e.init(0.01)
     e.sk_config(5, 10)
@@ -97,3 +100,32 @@ def test_autotune_keeps_state(tmp_path):
     c.init(0.0)
     assert c.autotune(5, cache) == s
     assert open(cache).read().count("\n") == 1
+
+
+def test_persistent_launch_many_tiles_per_cta():
+    """More tiles than resident CTAs (each CTA sweeps several tiles per step and
+    waits on the replica barriers): persistent windows give the per-step bits,
+    including the S(k) sampling windows."""
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    reps = [(1024, 1024, -4.4, 1.0, 1e-6, LN2), (512, 1024, -3.8, 0.9, 1e-6, 0.7),
+            (1024, 256, -4.0, 1.1, 1e-6, 0.68), (256, 256, -4.6, 1.0, 1e-6, LN2)]
+    a, b = Ensemble(reps, seed=9), Ensemble(reps, seed=9)
+    a.set_launch(abi.LB_ENS_PERSISTENT)
+    for e in (a, b):
+        e.set_strip_height(8)
+        e.init(0.01)
+        e.sk_config(16, 16)
+    assert a.num_tiles > 1000          # above the 6 x 152 resident CTAs
+    a.step(3)
+    a.step(16 * 4 + 5)      # sampling windows replayed as persistent launches
+    a.step(40)
+    b.step(3)
+    b.step(16 * 4 + 5)
+    b.step(40)
+    a.sync()                # raises on a barrier timeout or a non-finite value
+    for r in range(len(reps)):
+        assert np.array_equal(a.populations(r), b.populations(r)), r
+        Sa, na = a.structure_factor(r)
+        Sb, nb = b.structure_factor(r)
+        assert na == nb and np.array_equal(Sa, Sb), r
