@@ -76,7 +76,11 @@ __device__ __forceinline__ T sum9(const T g[9]) {
 // call, Box-Muller on a ring of 1024 angles) -> inverse
 // transform delta f_i = w_i sum_k e_ki m_k / b_k.  The inverse is factored
 // into symmetric sums and differences with the weights folded in.
-template <typename T>
+// UNIT: every relaxation rate is 1 (tau = tau_bulk = tau_ghost = 1, gamma = 0):
+// the non-conserved moments are replaced by their equilibrium, source and
+// noise, so m3..m8 of the pulled populations are not needed; the result is
+// bit-identical to the general path with gamma = 0.
+template <typename T, bool UNIT = false>
 __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<T> &p,
                                         const uint32_t *__restrict__ rk, uint32_t site, T f[9]) {
     // forward transform (integer coefficients, shared subexpressions)
@@ -102,11 +106,21 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T ux = jxh * inv_rho, uy = jyh * inv_rho;
     const T qxx = jxh * ux, qyy = jyh * uy, qxy = jxh * uy;          // rho u u
     const T pxx = ux * Fx, pyy = uy * Fy, pxy = fma(ux, Fy, uy * Fx);
-    const T gs = p.gamma, gg = p.gamma_g;
-    T m3s = fma(p.gamma_b, m3, fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy)));
-    T m4s = fma(gs, m4, fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy)));
-    T m5s = fma(gs, m5, fma(p.c5a, qxy, p.c5b * pxy));
-    T m6s = gg * m6, m7s = gg * m7, m8s = gg * m8;
+    T m3s, m4s, m5s, m6s, m7s, m8s;
+    if constexpr (UNIT) {
+        m3s = fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy));
+        m4s = fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy));
+        m5s = fma(p.c5a, qxy, p.c5b * pxy);
+        m6s = m7s = m8s = T(0);
+    } else {
+        const T gs = p.gamma, gg = p.gamma_g;
+        m3s = fma(p.gamma_b, m3, fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy)));
+        m4s = fma(gs, m4, fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy)));
+        m5s = fma(gs, m5, fma(p.c5a, qxy, p.c5b * pxy));
+        m6s = gg * m6;
+        m7s = gg * m7;
+        m8s = gg * m8;
+    }
     const T jxs = m1 + Fx, jys = m2 + Fy;
 
     if (p.noise) {

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbsc_collide.cuh"
 #include "lbsc_device.cuh"
 #include "lbsc_internal.cuh"
@@ -26,10 +28,11 @@
 
 namespace lbsc {
 
-template <typename T, int ORDER, bool SAMPLE>
+template <typename T, int ORDER, bool SAMPLE, bool UNIT = false>
 __global__ void __launch_bounds__(kStepTX + 32) step_kernel(const KParams<T> p) {
     const int y0 = blockIdx.y * p.strip_h;
-    step_strip<T, ORDER, SAMPLE>(p, p.rk, blockIdx.x * kStepTX, y0, min(y0 + p.strip_h, p.ny));
+    step_strip<T, ORDER, SAMPLE, false, UNIT>(p, p.rk, blockIdx.x * kStepTX, y0,
+                                              min(y0 + p.strip_h, p.ny));
 }
 
 
@@ -37,10 +40,22 @@ template <typename T, int ORDER>
 static cudaError_t launch_t(const StepArgs &a, cudaStream_t s) {
     KParams<T> k = make_params<T>(a);
     dim3 grid((a.nx + kStepTX - 1) / kStepTX, (a.ny + a.strip_h - 1) / a.strip_h);
-    if (a.drho_out)
+    // FP32 with every relaxation rate 1 (tau = 1 BGK, the usual setting) takes
+    // the kernel that skips the unused moments
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.gamma == 0.0 && a.gamma_b == 0.0 && a.gamma_g == 0.0) {
+            if (a.drho_out)
+                step_kernel<T, ORDER, true, true><<<grid, kStepTX + 32, 0, s>>>(k);
+            else
+                step_kernel<T, ORDER, false, true><<<grid, kStepTX + 32, 0, s>>>(k);
+            return cudaGetLastError();
+        }
+    }
+    if (a.drho_out) {
         step_kernel<T, ORDER, true><<<grid, kStepTX + 32, 0, s>>>(k);
-    else
+    } else {
         step_kernel<T, ORDER, false><<<grid, kStepTX + 32, 0, s>>>(k);
+    }
     return cudaGetLastError();
 }
 

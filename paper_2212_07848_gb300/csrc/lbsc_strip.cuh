@@ -18,7 +18,8 @@ namespace lbsc {
 // rk: the Philox round keys (kept apart from p so that callers can serve
 // them from the constant bank).  CG: pull through L2 only (the source was
 // written earlier in the same launch, as in the persistent ensemble kernel).
-template <typename T, int ORDER, bool SAMPLE, bool CG = false>
+// UNIT: all relaxation rates are 1 (see collide).
+template <typename T, int ORDER, bool SAMPLE, bool CG = false, bool UNIT = false>
 __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *__restrict__ rk,
                                            int x0, int y0, int y1) {
     using S = Stencil<ORDER>;
@@ -118,7 +119,7 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
         const T Fy = p.force_pref * psic * sy;
 
         T f[9];
-        collide(q[0], Fx, Fy, p, rk, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
+        collide<T, UNIT>(q[0], Fx, Fy, p, rk, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
 
         const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
         p.dst[o] = f[0];
