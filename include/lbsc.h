@@ -359,10 +359,14 @@ int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, flo
  * channel 0, 0 elsewhere. */
 int lb_nn_mse(const void *y, int c, const float *target, const float *base, size_t n, float *loss,
               void *dy, void *stream);
-/* Rollout update: FP32 state [n] += y[.][0]; channel 0 of the network input x
- * [n][cx] = BF16(state), channel 2 (when cx > 2) = the increment y[.][0] just
- * applied, other channels of x untouched. */
-int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, void *stream);
+/* Rollout update: FP32 state [n] += y[.][0] - m, channel 0 of the network
+ * input x [n][cx] = BF16(state), channel 2 (when cx > 2) = the increment just
+ * applied, other channels of x untouched.  With mean_buf (a caller-owned
+ * device float, or NULL for m = 0) m is the mean of y[.][0] over the n
+ * pixels, written to mean_buf first: the increment then has zero mean and the
+ * field's mass is conserved as the lattice conserves it. */
+int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, float *mean_buf,
+                   void *stream);
 /* Adam step (bias-corrected, `step` >= 1) on FP32 w with gradient g and moments
  * m, v; w_bf16 (may be NULL) receives the BF16 copy. */
 int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_t n, double lr,

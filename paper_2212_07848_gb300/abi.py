@@ -154,7 +154,7 @@ def bind(L):
         "lb_nn_add": (C.c_int, [P, P, P, C.c_size_t, P]),
         "lb_nn_coarse_grain": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]),
         "lb_nn_mse": (C.c_int, [P, C.c_int, P, P, C.c_size_t, P, P, P]),
-        "lb_nn_residual": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_size_t, P]),
+        "lb_nn_residual": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_size_t, P, P]),
         "lb_nn_adam": (C.c_int, [P, P, P, P, P, C.c_size_t, C.c_double, C.c_double, C.c_double,
                                  C.c_double, C.c_longlong, P]),
         "lb_nn_to_bf16": (C.c_int, [P, P, C.c_size_t, P]),

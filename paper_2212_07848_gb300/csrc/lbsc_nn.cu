@@ -421,17 +421,36 @@ __global__ void mse_kernel(const bf16 *__restrict__ y, int C, const float *__res
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
 }
 
-// Rollout update: state (FP32) += y[.][0]; the next network input x [n][Cx]
-// gets channel 0 = BF16(state) and channel 2 = the increment y[.][0] just
-// applied; its other channels are untouched.
+// Mean of channel 0 of y [n][C] (one block, fixed summation order).
+__global__ void __launch_bounds__(1024) mean_ch0_kernel(const bf16 *__restrict__ y, int C, size_t n,
+                                                       float *__restrict__ out) {
+    __shared__ float part[32];
+    float s = 0.f;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += __bfloat162float(y[i * C]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) out[0] = s / (float)n;
+    }
+}
+
+// Rollout update: state (FP32) += y[.][0] - mean (mean = *mean_in, or 0
+// without it: the increment projected to zero mean conserves the mass of the
+// field); the next network input x [n][Cx] gets channel 0 = BF16(state) and
+// channel 2 = the increment just applied; its other channels are untouched.
 __global__ void residual_kernel(float *__restrict__ state, const bf16 *__restrict__ y, int C,
-                                bf16 *__restrict__ x, int Cx, size_t n) {
+                                bf16 *__restrict__ x, int Cx, size_t n,
+                                const float *__restrict__ mean_in) {
+    const float mu = mean_in ? mean_in[0] : 0.f;
     GRID_STRIDE(i, n) {
-        const bf16 d = y[i * C];
-        const float v = state[i] + __bfloat162float(d);
+        const float d = __bfloat162float(y[i * C]) - mu;
+        const float v = state[i] + d;
         state[i] = v;
         x[i * Cx] = __float2bfloat16(v);
-        if (Cx > 2) x[i * Cx + 2] = d;
+        if (Cx > 2) x[i * Cx + 2] = __float2bfloat16(d);
     }
 }
 
@@ -602,10 +621,16 @@ int lb_nn_mse(const void *y, int c, const float *target, const float *base, size
     NN_RET();
 }
 
-int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, void *stream) {
+int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, float *mean_buf,
+                   void *stream) {
     if (!state || !y || !x || c < 1 || cx < 1) return LB_ERR_ARG;
-    residual_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(state, (const bf16 *)y, c,
-                                                                      (bf16 *)x, cx, n);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mean_buf) {
+        mean_ch0_kernel<<<1, 1024, 0, s>>>((const bf16 *)y, c, n, mean_buf);
+        if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    }
+    residual_kernel<<<blocks_for(n), 256, 0, s>>>(state, (const bf16 *)y, c, (bf16 *)x, cx, n,
+                                                  mean_buf);
     NN_RET();
 }
 

@@ -227,7 +227,7 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
             # one stride by the network itself: base becomes its prediction of
             # frame f, x the matching input (channel 2 = the increment)
             net.forward(x)
-            _check(L.lb_nn_residual(_p(base), _p(net.y), 16, _p(x), CIN, nb * m * m, net.s),
+            _check(L.lb_nn_residual(_p(base), _p(net.y), 16, _p(x), CIN, nb * m * m, None, net.s),
                    "residual")
         net.zero_grad()
         net.forward(x)
@@ -284,6 +284,7 @@ class _StrideGraph:
         self.stream = torch.cuda.Stream()
         self.x = torch.zeros((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
         self.state = torch.zeros((m, m), dtype=torch.float32, device="cuda")
+        self.mean = torch.zeros(1, dtype=torch.float32, device="cuda")
         saved = net.s
         net.s = self.stream.cuda_stream
         try:
@@ -295,7 +296,7 @@ class _StrideGraph:
             with torch.cuda.graph(self.graph, stream=self.stream):
                 net.forward(self.x)
                 _check(net.L.lb_nn_residual(_p(self.state), _p(net.y), 16, _p(self.x), CIN, m * m,
-                                            net.s), "residual")
+                                            _p(self.mean), net.s), "residual")
         finally:
             net.s = saved
 
@@ -316,9 +317,10 @@ class _StrideGraph:
 def rollout(net, frame0, G, strides, prev0=None, graph=True):
     """Apply the surrogate `strides` times from an FP32 field [m][m] (and the
     field one stride earlier, for the last-increment input); the state stays
-    FP32 (only the network input is BF16).  Returns the FP32 fields after each
-    stride as one tensor [strides][m][m].  With `graph` each stride replays a
-    CUDA graph captured on the first call."""
+    FP32 (only the network input is BF16) and each increment is projected to
+    zero mean, so the field's mass is conserved as on the lattice.  Returns the
+    FP32 fields after each stride as one tensor [strides][m][m].  With `graph`
+    each stride replays a CUDA graph captured on the first call."""
     import torch
     L, m = net.L, net.n
     if net.nb != 1:
@@ -330,13 +332,33 @@ def rollout(net, frame0, G, strides, prev0=None, graph=True):
             net._stride_graph = _StrideGraph(net)
         return net._stride_graph.run(frame0, G, strides, prev0, out)
     x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
+    mean = torch.zeros(1, dtype=torch.float32, device="cuda")
     state = frame0.clone()
     expand(L, state, G, x, prev0, net.s)
     for s in range(strides):
         net.forward(x)
-        _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, net.s), "residual")
+        _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, _p(mean), net.s),
+               "residual")
         out[s].copy_(state)
     return out
+
+
+def guarded_rollout(net, frame0, G, strides, prev0=None, mass_tol=1e-3, bound=None):
+    """Rollout with the checks that decide when the solver has to take over:
+    the lattice conserves mass exactly, so the coarse field's mean must stay
+    within `mass_tol` of its initial mean, and the field must stay inside
+    `bound` (default: 1.5 x the initial field's largest |value|, at least 1).
+    Returns (fields [n][m][m] accepted, n): n < strides means the surrogate
+    left its domain after n strides and the caller continues with the solver
+    from the last accepted state."""
+    out = rollout(net, frame0, G, strides, prev0)
+    means = out.mean(dim=(1, 2)).cpu().numpy()
+    peaks = out.abs().amax(dim=(1, 2)).cpu().numpy()
+    m0 = float(frame0.mean())
+    lim = bound if bound is not None else max(1.0, 1.5 * float(frame0.abs().max()))
+    ok = (np.abs(means - m0) <= mass_tol) & np.isfinite(means) & (peaks <= lim)
+    n = int(np.argmin(ok)) if not ok.all() else strides
+    return out[:n], n
 
 
 def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):

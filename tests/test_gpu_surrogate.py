@@ -104,3 +104,19 @@ def test_rollout_stable_and_faster_than_solver(trained):
     lat.close()
     print(f"surrogate {t_net * 1e3:.3f} ms/stride, solver {t_lb * 1e3:.3f} ms per 200 steps")
     assert t_net < t_lb
+
+
+def test_guarded_rollout_hands_back_to_the_solver(trained):
+    """Rollout increments have zero mean, so the field's mass stays at its
+    initial value to FP32 rounding and the mass guard accepts the rollout
+    whole; a bound the field cannot meet hands over to the solver at once."""
+    S, net, frames, Gs, _, _ = trained
+    k, f0 = 11, 4
+    fields, n = S.guarded_rollout(net, frames[k, f0].clone(), float(Gs[k]), 6, frames[k, f0 - 1],
+                                  mass_tol=1e-4, bound=10.0)
+    assert n == 6 and fields.shape[0] == 6
+    drift = (fields.double().mean(dim=(1, 2)) - frames[k, f0].double().mean()).abs().max()
+    assert float(drift) < 1e-5
+    fields, n = S.guarded_rollout(net, frames[k, f0].clone(), float(Gs[k]), 6, frames[k, f0 - 1],
+                                  mass_tol=0.0, bound=1e-9)
+    assert n == 0 and fields.shape[0] == 0
