@@ -28,6 +28,16 @@ class OrParams(C.Structure):
     ]
 
 
+class Or3Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("G", C.c_double), ("tau", C.c_double), ("kT", C.c_double),
+        ("rho0", C.c_double),
+        ("seed", C.c_uint64),
+        ("replica", C.c_uint32),
+    ]
+
+
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _I = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _U32 = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
@@ -73,6 +83,25 @@ def lib():
         L.or_stencil.argtypes = [C.c_int, _I, _I, _D]
         L.or_stencil.restype = C.c_int
         L.or_normals.argtypes = [C.POINTER(OrParams), C.c_uint32, C.c_uint32, _D]
+        L.or3_create.argtypes = [C.POINTER(Or3Params)]
+        L.or3_create.restype = C.c_void_p
+        L.or3_destroy.argtypes = [C.c_void_p]
+        L.or3_init.argtypes = [C.c_void_p, C.c_double, C.c_uint64, C.c_double]
+        L.or3_set_replica.argtypes = [C.c_void_p, C.c_uint32]
+        L.or3_get_step.argtypes = [C.c_void_p]
+        L.or3_get_step.restype = C.c_longlong
+        L.or3_set_populations.argtypes = [C.c_void_p, _D]
+        L.or3_get_populations.argtypes = [C.c_void_p, _D]
+        L.or3_density.argtypes = [C.c_void_p, _D]
+        L.or3_conserved.argtypes = [C.c_void_p, _D]
+        L.or3_sk_config.argtypes = [C.c_void_p, C.c_int, C.c_longlong]
+        L.or3_sk_get.argtypes = [C.c_void_p, _D]
+        L.or3_sk_get.restype = C.c_longlong
+        L.or3_step.argtypes = [C.c_void_p, C.c_int]
+        L.or3_lattice_constants.argtypes = [_I, _D]
+        L.or3_force_field.argtypes = [C.c_void_p, _D]
+        L.or3_moment_basis.argtypes = [_D, _D]
+        L.or3_normals.argtypes = [C.POINTER(Or3Params), C.c_uint32, C.c_uint32, _D]
         L.or_box_muller_ring.argtypes = [C.c_uint32, C.c_uint32, _D]
         L.or_threads.restype = C.c_int
         _lib = L
@@ -223,3 +252,94 @@ def box_muller_ring(radius_word, angle_index):
     z = np.zeros(2)
     lib().or_box_muller_ring(radius_word, angle_index, z)
     return z
+
+
+# ---------------------------------------------------------------------------
+# D3Q19 (the paper's three-dimensional setting)
+# ---------------------------------------------------------------------------
+def lattice3_constants():
+    """(c [19][3], w [19]) of the D3Q19 lattice in the oracle's order."""
+    c = np.zeros(57, np.int32)
+    w = np.zeros(19)
+    lib().or3_lattice_constants(c, w)
+    return c.reshape(19, 3), w
+
+
+def moment_basis3():
+    """(M [19 moments][19 velocities], b [19]) of the D3Q19 basis."""
+    m = np.zeros(361)
+    b = np.zeros(19)
+    lib().or3_moment_basis(m, b)
+    return m.reshape(19, 19), b
+
+
+def normals3(nx, ny, nz, seed, replica, site, t):
+    """The 15 thermal normals (modes 4..18) of a site and step."""
+    p = Or3Params(nx, ny, nz, 0.0, 1.0, 0.0, 0.0, seed, replica)
+    z = np.zeros(15)
+    lib().or3_normals(C.byref(p), site, t, z)
+    return z
+
+
+class OracleLattice3:
+    """One periodic nx x ny x nz D3Q19 lattice held by the FP64 oracle
+    (psi = 1 - exp(-rho), E4 force stencil, BGK + Guo, 15 noise modes)."""
+
+    def __init__(self, nx, ny, nz, G, tau, kT, replica=0):
+        self.p = Or3Params(nx, ny, nz, G, tau, kT, 0.0, 0, replica)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self._h = lib().or3_create(C.byref(self.p))
+        if not self._h:
+            raise ValueError("oracle: invalid parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or3_destroy(h)
+            self._h = None
+
+    def init(self, rho0, seed=0, init_amp=0.0):
+        self.p.rho0, self.p.seed = rho0, seed
+        lib().or3_init(self._h, rho0, seed, init_amp)
+
+    def set_replica(self, r):
+        lib().or3_set_replica(self._h, r)
+
+    @property
+    def t(self):
+        return lib().or3_get_step(self._h)
+
+    def set_populations(self, f):
+        lib().or3_set_populations(self._h, np.ascontiguousarray(f, np.float64).ravel())
+
+    def populations(self):
+        f = np.zeros(19 * self.nx * self.ny * self.nz)
+        lib().or3_get_populations(self._h, f)
+        return f.reshape(19, self.nz, self.ny, self.nx)
+
+    def density(self):
+        r = np.zeros(self.nx * self.ny * self.nz)
+        lib().or3_density(self._h, r)
+        return r.reshape(self.nz, self.ny, self.nx)
+
+    def conserved(self):
+        out = np.zeros(4)
+        lib().or3_conserved(self._h, out)
+        return out
+
+    def step(self, n=1):
+        lib().or3_step(self._h, int(n))
+
+    def force(self):
+        F = np.zeros(3 * self.nx * self.ny * self.nz)
+        lib().or3_force_field(self._h, F)
+        return F.reshape(3, self.nz, self.ny, self.nx)
+
+    def sk_config(self, every, start):
+        lib().or3_sk_config(self._h, int(every), int(start))
+
+    def structure_factor_axes(self):
+        """(S [nx/2 + ny/2 + nz/2] on the x, y and z axes, nsamples)."""
+        out = np.zeros(self.nx // 2 + self.ny // 2 + self.nz // 2)
+        n = lib().or3_sk_get(self._h, out)
+        return out, n
