@@ -308,6 +308,50 @@ int lb_ens_conserved(lb_ens *e, int r, double out[3]);
 int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
                             long long *nsamples_out);
 
+/* ---- three dimensions: D3Q19 ---------------------------------------------
+ * The paper's own setting: Eq. (12) on a D3Q19 lattice (c_s^2 = 1/3; weights
+ * 1/3, 1/18, 1/36; velocity order: rest; +x, -x, +y, -y, +z, -z; then the
+ * face diagonals of the xy, xz and yz planes as (+,+), (-,-), (+,-), (-,+)),
+ * psi = 1 - exp(-rho), the Shan-Chen force of Eq. (1) over the 18 neighbours
+ * with weights 1/6 (axes) and 1/12 (diagonals), BGK collision with Guo
+ * forcing in the 19-moment basis (1, c, c^2-1, 3cx^2-c^2, cy^2-cz^2, cxcy,
+ * cycz, czcx, (3c^2-5)c, (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz,
+ * 3c^4-6c^2+1, (2c^2-3)(3cx^2-c^2), (2c^2-3)(cy^2-cz^2)), and noise
+ * sqrt(mu rho b_k (1 - gamma^2)) z_k on the 15 modes k = 4..18 (the noise
+ * paragraph after Eq. (16): modes a > 3), z from Philox4x32-10 blocks 0-2 of
+ * counter (site, step, replica, block), site = x + nx (y + ny z).
+ * Storage: deviations [19][nz][ny][nx], FP32 or FP64; the context owns its
+ * device memory.  nx % 32 == 0, ny % 8 == 0, nz >= 3, 19 nx ny nz < 2^32,
+ * tau > 1/2, kT >= 0 (LB_ERR_ARG otherwise).  Calls are asynchronous on the
+ * context's stream except the read-outs, which synchronise. */
+typedef struct lb3_ctx lb3_ctx;
+int lb3_create(lb3_ctx **out, int nx, int ny, int nz, double G, double tau, double kT,
+               int precision, void *stream);
+void lb3_destroy(lb3_ctx *h);
+/* Homogeneous rho0 at rest, plus an optional density kick init_amp z(site)
+ * from Philox block 3 of step 0. */
+int lb3_init(lb3_ctx *h, double rho0, uint64_t seed, double init_amp);
+int lb3_set_replica(lb3_ctx *h, uint32_t replica);
+/* z planes marched by one CTA (performance only). */
+int lb3_set_strip(lb3_ctx *h, int planes);
+int lb3_step(lb3_ctx *h, int n);
+int lb3_sync(lb3_ctx *h);
+long long lb3_get_step(const lb3_ctx *h);
+/* rho [nz][ny][nx] and full populations f [19][nz][ny][nx] (host, FP64). */
+int lb3_density(lb3_ctx *h, double *host_out);
+int lb3_populations(lb3_ctx *h, double *host_out);
+int lb3_set_populations(lb3_ctx *h, const double *host_f);
+/* Total mass and momentum (FP64). */
+int lb3_conserved(lb3_ctx *h, double out[4]);
+/* S(k) on the three lattice axes, sampled after completed step n when
+ * n >= start and (n - start) % every == 0: S(k e_a) = |sum_x drho(x)
+ * e^{-i k x_a}|^2 / N for k = 2 pi m / n_a, m = 1 .. n_a/2.  The read-out
+ * host_out [nx/2 + ny/2 + nz/2] holds the means over the samples (x modes,
+ * then y, then z); LB_ERR_STATE before lb3_sk_config. */
+int lb3_sk_config(lb3_ctx *h, int every, long long start);
+int lb3_sk_reset(lb3_ctx *h);
+int lb3_structure_factor_axes(lb3_ctx *h, double *host_out, long long *nsamples_out);
+
 /* ---- learned surrogate building blocks ---------------------------------------
  * A small convolutional operator advances the 4x coarse-grained density of a
  * quench by a fixed stride; it is trained on trajectories of the solver

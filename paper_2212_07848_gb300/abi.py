@@ -42,6 +42,9 @@ EXPORTED = [
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
     "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments", "lb_ens_set_launch",
     "lb_ens_get_launch",
+    "lb3_create", "lb3_destroy", "lb3_init", "lb3_set_replica", "lb3_set_strip", "lb3_step",
+    "lb3_sync", "lb3_get_step", "lb3_density", "lb3_populations", "lb3_set_populations",
+    "lb3_conserved", "lb3_sk_config", "lb3_sk_reset", "lb3_structure_factor_axes",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
     "lb_nn_to_bf16", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
@@ -134,6 +137,22 @@ def bind(L):
         "lb_ens_autotune": (C.c_int, [P, C.c_int, C.c_char_p, C.POINTER(C.c_int)]),
         "lb_ens_step": (C.c_int, [P, C.c_int]),
         "lb_ens_set_launch": (C.c_int, [P, C.c_int]),
+        "lb3_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_double, C.c_double, C.c_int, P]),
+        "lb3_destroy": (None, [P]),
+        "lb3_init": (C.c_int, [P, C.c_double, C.c_uint64, C.c_double]),
+        "lb3_set_replica": (C.c_int, [P, C.c_uint32]),
+        "lb3_set_strip": (C.c_int, [P, C.c_int]),
+        "lb3_step": (C.c_int, [P, C.c_int]),
+        "lb3_sync": (C.c_int, [P]),
+        "lb3_get_step": (C.c_longlong, [P]),
+        "lb3_density": (C.c_int, [P, _D]),
+        "lb3_populations": (C.c_int, [P, _D]),
+        "lb3_set_populations": (C.c_int, [P, _D]),
+        "lb3_conserved": (C.c_int, [P, _D]),
+        "lb3_sk_config": (C.c_int, [P, C.c_int, C.c_longlong]),
+        "lb3_sk_reset": (C.c_int, [P]),
+        "lb3_structure_factor_axes": (C.c_int, [P, _D, C.POINTER(C.c_longlong)]),
         "lb_ens_get_launch": (C.c_int, [P]),
         "lb_ens_sync": (C.c_int, [P]),
         "lb_ens_get_step": (C.c_longlong, [P]),

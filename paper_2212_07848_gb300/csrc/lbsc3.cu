@@ -1,0 +1,818 @@
+// Fluctuating Shan-Chen step in three dimensions (D3Q19): the paper's own
+// setting, Eq. (12) with the force of Eq. (1) and noise on the moments
+// a > 3 (the noise paragraph after Eq. (16)).  Deviations delta f_i = f_i -
+// w_i rho0 are stored structure-of-arrays [19][nz][ny][nx], two buffers.
+//
+// Work decomposition: a CTA owns a 32 x 8 tile of (x, y) columns and marches
+// a strip of z planes.  Its 34 x 10 threads cover the tile and its one-column
+// halo ring: every thread pulls its column's populations for plane z + 1 and
+// writes that plane's pseudopotential deviation into a shared-memory ring of
+// four planes; after the barrier the 32 x 8 interior threads collide plane z
+// from the populations they pulled one plane earlier (kept in registers).
+// The force is Eq. (1) over the 18 D3Q19 neighbours with the fourth-order
+// isotropic weights 1/6 (axes) and 1/12 (face diagonals), summed as
+// antisymmetric pairs.  The collision runs in the 19-moment basis:
+// mass and momentum conserved (momentum + F), the six stress modes relaxed
+// to rho u u with the Guo source, the nine ghost modes relaxed to zero, and
+// noise sqrt(mu rho b_k (1 - gamma^2)) z_k on the fifteen modes 4..18 from
+// three Philox4x32-10 calls (ring Box-Muller).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbsc.h"
+#include "lbsc_device.cuh"
+#include "lbsc_internal.cuh"
+
+namespace lbsc {
+namespace {
+
+// D3Q19 velocities: rest; +x, -x, +y, -y, +z, -z; xy, xz, yz face diagonals
+// as (+,+), (-,-), (+,-), (-,+).  Opposite velocities are adjacent (1-2, ...).
+__host__ __device__ constexpr int cx3(int i) {
+    return i == 1 || i == 7 || i == 9 || i == 11 || i == 13 ? 1
+         : i == 2 || i == 8 || i == 10 || i == 12 || i == 14 ? -1 : 0;
+}
+__host__ __device__ constexpr int cy3(int i) {
+    return i == 3 || i == 7 || i == 10 || i == 15 || i == 17 ? 1
+         : i == 4 || i == 8 || i == 9 || i == 16 || i == 18 ? -1 : 0;
+}
+__host__ __device__ constexpr int cz3(int i) {
+    return i == 5 || i == 11 || i == 14 || i == 15 || i == 18 ? 1
+         : i == 6 || i == 12 || i == 13 || i == 16 || i == 17 ? -1 : 0;
+}
+__host__ __device__ constexpr double wq3(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// Moment polynomial k at velocity i (integer values).
+__host__ __device__ constexpr int mom3(int k, int i) {
+    const int x = cx3(i), y = cy3(i), z = cz3(i), c2 = x * x + y * y + z * z;
+    return k == 0 ? 1
+         : k == 1 ? x : k == 2 ? y : k == 3 ? z
+         : k == 4 ? c2 - 1
+         : k == 5 ? 3 * x * x - c2
+         : k == 6 ? y * y - z * z
+         : k == 7 ? x * y : k == 8 ? y * z : k == 9 ? z * x
+         : k == 10 ? (3 * c2 - 5) * x : k == 11 ? (3 * c2 - 5) * y : k == 12 ? (3 * c2 - 5) * z
+         : k == 13 ? (y * y - z * z) * x : k == 14 ? (z * z - x * x) * y
+         : k == 15 ? (x * x - y * y) * z
+         : k == 16 ? 3 * c2 * c2 - 6 * c2 + 1
+         : k == 17 ? (2 * c2 - 3) * (3 * x * x - c2)
+                   : (2 * c2 - 3) * (y * y - z * z);
+}
+// b_k = sum_i w_i e_ki^2, and the same values written out (checked against
+// each other at compile time) for the device code
+__host__ __device__ constexpr double norm3(int k) {
+    double b = 0.0;
+    for (int i = 0; i < 19; ++i) b += wq3(i) * mom3(k, i) * mom3(k, i);
+    return b;
+}
+__host__ __device__ constexpr double norm3_lit(int k) {
+    return k == 0 ? 1.0 : k <= 3 ? 1.0 / 3.0 : k == 4 ? 2.0 / 3.0 : k == 5 ? 4.0 / 3.0
+         : k == 6 ? 4.0 / 9.0 : k <= 9 ? 1.0 / 9.0 : k <= 12 ? 2.0 / 3.0 : k <= 15 ? 2.0 / 9.0
+         : k == 16 ? 2.0 : k == 17 ? 4.0 / 3.0 : 4.0 / 9.0;
+}
+constexpr bool norms_agree() {
+    for (int k = 0; k < 19; ++k) {
+        const double d = norm3(k) - norm3_lit(k);
+        if (d > 1e-15 || d < -1e-15) return false;
+    }
+    return true;
+}
+static_assert(norms_agree(), "moment norms");
+
+constexpr int kTX3 = 32, kTY3 = 8;
+constexpr int kBX3 = kTX3 + 2, kBY3 = kTY3 + 2;      // tile + halo ring
+constexpr int kThreads3 = kBX3 * kBY3;               // 340
+
+template <typename T> struct K3 {
+    const T *__restrict__ src;
+    T *__restrict__ dst;
+    T *__restrict__ drho_out;
+    int *__restrict__ flag;
+    int nx, ny, nz, strip_z, noise;
+    uint32_t step, replica;
+    T rho0, force_pref, psi_c, psi0, gamma, hsrc;
+    T amp[19];     // modes 4..18 used
+    uint32_t rk[20];
+};
+
+template <typename T>
+__device__ __forceinline__ void pull3(const T *__restrict__ src, uint32_t plane, int nx, int ny,
+                                      int nz, int x, int y, int z, T g[19]) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int xs = x - cx3(i), ys = y - cy3(i), zs = z - cz3(i);
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        g[i] = __ldg(src + (uint32_t)i * plane + ((uint32_t)zs * ny + ys) * nx + xs);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sum19(const T g[19]) {
+    T s = g[0];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) s += g[2 * p + 1] + g[2 * p + 2];
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T dpsi3(T drho, T psi_c) {
+    return -psi_c * dev_expm1(-drho);
+}
+
+// Collision of one site (moment space), Eq. (12) in 3D.
+template <typename T>
+__device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const K3<T> &p,
+                                         uint32_t site, T f[19]) {
+    // pair sums and differences: pair q = velocities 2q+1 (c) and 2q+2 (-c)
+    T s[10], d[10];
+    s[0] = g[0];
+    d[0] = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        s[q + 1] = g[2 * q + 1] + g[2 * q + 2];
+        d[q + 1] = g[2 * q + 1] - g[2 * q + 2];
+    }
+    // m_k = sum over pairs of e_k(c) (s or d): even polynomials use s, odd use d
+    T m[19];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        const bool odd = (k >= 1 && k <= 3) || (k >= 10 && k <= 15);
+        T acc = odd ? T(0) : T(mom3(k, 0)) * s[0];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int e = mom3(k, 2 * q + 1);
+            if (e != 0) acc = fma(T(e), odd ? d[q + 1] : s[q + 1], acc);
+        }
+        m[k] = acc;
+    }
+    const T rho = p.rho0 + m[0];
+    const T inv = T(1) / rho;
+    const T jx = fma(T(0.5), Fx, m[1]), jy = fma(T(0.5), Fy, m[2]), jz = fma(T(0.5), Fz, m[3]);
+    const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const T qxx = jx * ux, qyy = jy * uy, qzz = jz * uz;
+    const T qxy = jx * uy, qyz = jy * uz, qzx = jz * ux;
+    const T q2 = qxx + qyy + qzz;
+    const T pxx = ux * Fx, pyy = uy * Fy, pzz = uz * Fz;
+    const T p2 = pxx + pyy + pzz;
+    const T g_ = p.gamma, a = T(1) - p.gamma, h = p.hsrc;   // h = (1 + gamma) / 2
+    T ms[19];
+    ms[0] = m[0];
+    ms[1] = m[1] + Fx;
+    ms[2] = m[2] + Fy;
+    ms[3] = m[3] + Fz;
+    ms[4] = fma(g_, m[4], fma(a, q2, h * (T(2) * p2)));
+    ms[5] = fma(g_, m[5], fma(a, T(3) * qxx - q2, h * (T(6) * pxx - T(2) * p2)));
+    ms[6] = fma(g_, m[6], fma(a, qyy - qzz, h * (T(2) * (pyy - pzz))));
+    ms[7] = fma(g_, m[7], fma(a, qxy, h * fma(ux, Fy, uy * Fx)));
+    ms[8] = fma(g_, m[8], fma(a, qyz, h * fma(uy, Fz, uz * Fy)));
+    ms[9] = fma(g_, m[9], fma(a, qzx, h * fma(uz, Fx, ux * Fz)));
+#pragma unroll
+    for (int k = 10; k < 19; ++k) ms[k] = g_ * m[k];
+    if (p.noise) {
+        const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), p.rk);
+        const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), p.rk);
+        const uint4 r2 = philox4x32_10(make_uint4(site, p.step, p.replica, 2u), p.rk);
+        T c, sn, rad;
+#define NOISE_PAIR(R, WORD, SHIFT, KA, KB)                                                 \
+    box_ring_polar(uniform01<T>(R.WORD), (R.w >> SHIFT) & 1023u, rho, rad, c, sn);       \
+    ms[KA] = fma(p.amp[KA] * rad, c, ms[KA]);                                             \
+    ms[KB] = fma(p.amp[KB] * rad, sn, ms[KB]);
+        NOISE_PAIR(r0, x, 0, 4, 5)
+        NOISE_PAIR(r0, y, 10, 6, 7)
+        NOISE_PAIR(r0, z, 20, 8, 9)
+        NOISE_PAIR(r1, x, 0, 10, 11)
+        NOISE_PAIR(r1, y, 10, 12, 13)
+        NOISE_PAIR(r1, z, 20, 14, 15)
+        NOISE_PAIR(r2, x, 0, 16, 17)
+#undef NOISE_PAIR
+        // mode 18: the cosine of the pair (r2.y, bits 10-19 of r2.w)
+        box_ring_polar(uniform01<T>(r2.y), (r2.w >> 10) & 1023u, rho, rad, c, sn);
+        ms[18] = fma(p.amp[18] * rad, c, ms[18]);
+    }
+    // inverse: delta f_i = w_i sum_k e_ki m*_k / b_k, assembled per pair as
+    // (even part) +- (odd part)
+    T ev[10], od[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        const int i = q == 0 ? 0 : 2 * q - 1;
+        T e_acc = T(0), o_acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const int e = mom3(k, i);
+            if (e == 0) continue;
+            const bool odd = (k >= 1 && k <= 3) || (k >= 10 && k <= 15);
+            const T coef = T(wq3(i) * e / norm3_lit(k));
+            if (odd) o_acc = fma(coef, ms[k], o_acc);
+            else e_acc = fma(coef, ms[k], e_acc);
+        }
+        ev[q] = e_acc;
+        od[q] = o_acc;
+    }
+    f[0] = ev[0];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        f[2 * q + 1] = ev[q + 1] + od[q + 1];
+        f[2 * q + 2] = ev[q + 1] - od[q + 1];
+    }
+}
+
+template <typename T, bool SAMPLE>
+__global__ void __launch_bounds__(kThreads3) step3_kernel(const K3<T> p) {
+    __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
+    const int tx = threadIdx.x % kBX3, ty = threadIdx.x / kBX3;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const uint32_t plane = (uint32_t)nx * ny * nz;
+    int x = blockIdx.x * kTX3 - 1 + tx, y = blockIdx.y * kTY3 - 1 + ty;
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    const bool interior = tx >= 1 && tx <= kTX3 && ty >= 1 && ty <= kTY3;
+    const int z0 = blockIdx.z * p.strip_z, z1 = min(z0 + p.strip_z, nz);
+    const int it_end = (z1 - z0) + 2;
+
+    T qprev[19], qcur[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) qprev[i] = T(0);
+    for (int it = 0; it < it_end; ++it) {
+        int zz = z0 - 1 + it;
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        pull3(p.src, plane, nx, ny, nz, x, y, zz, qcur);
+        s_psi[it & 3][ty][tx] = dpsi3<T>(sum19(qcur), p.psi_c);
+        __syncthreads();
+        if (it >= 2 && interior) {
+            // collide plane zc = zz - 1 (pulled in the previous iteration)
+            const int zc = z0 - 2 + it;
+            const int sm = (it - 2) & 3, sc = (it - 1) & 3, sp = it & 3;
+            // Eq. (1): sum over the 18 neighbours as antisymmetric pairs
+            const T w1 = T(1.0 / 6.0), w2 = T(1.0 / 12.0);
+            T Sx = w1 * (s_psi[sc][ty][tx + 1] - s_psi[sc][ty][tx - 1]);
+            T Sy = w1 * (s_psi[sc][ty + 1][tx] - s_psi[sc][ty - 1][tx]);
+            T Sz = w1 * (s_psi[sp][ty][tx] - s_psi[sm][ty][tx]);
+            const T dxy1 = s_psi[sc][ty + 1][tx + 1] - s_psi[sc][ty - 1][tx - 1];   // (1,1,0)
+            const T dxy2 = s_psi[sc][ty - 1][tx + 1] - s_psi[sc][ty + 1][tx - 1];   // (1,-1,0)
+            const T dxz1 = s_psi[sp][ty][tx + 1] - s_psi[sm][ty][tx - 1];           // (1,0,1)
+            const T dxz2 = s_psi[sm][ty][tx + 1] - s_psi[sp][ty][tx - 1];           // (1,0,-1)
+            const T dyz1 = s_psi[sp][ty + 1][tx] - s_psi[sm][ty - 1][tx];           // (0,1,1)
+            const T dyz2 = s_psi[sm][ty + 1][tx] - s_psi[sp][ty - 1][tx];           // (0,1,-1)
+            Sx = fma(w2, (dxy1 + dxy2) + (dxz1 + dxz2), Sx);
+            Sy = fma(w2, (dxy1 - dxy2) + (dyz1 + dyz2), Sy);
+            Sz = fma(w2, (dxz1 - dxz2) + (dyz1 - dyz2), Sz);
+            const T psic = p.psi0 + s_psi[sc][ty][tx];
+            const T Fx = p.force_pref * psic * Sx, Fy = p.force_pref * psic * Sy,
+                    Fz = p.force_pref * psic * Sz;
+            const uint32_t site = ((uint32_t)zc * ny + y) * nx + x;
+            T f[19];
+            collide3(qprev, Fx, Fy, Fz, p, site, f);
+#pragma unroll
+            for (int i = 0; i < 19; ++i) p.dst[(uint32_t)i * plane + site] = f[i];
+            if (SAMPLE) p.drho_out[site] = sum19(qprev);
+            if (!isfinite(f[1] + f[7])) atomicOr(p.flag, LB_STEP_NONFINITE);
+        }
+#pragma unroll
+        for (int i = 0; i < 19; ++i) qprev[i] = qcur[i];
+        // slot (it + 1) & 3, written next, was last read in iteration it - 1,
+        // before this iteration's barrier
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Axis structure factor: per z plane the partial x and y profiles of delta
+// rho and the plane total; then the profiles are summed over planes in a
+// fixed order and Fourier transformed on the x, y and z axes.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void profile3_kernel(const T *__restrict__ drho, int nx, int ny, double *__restrict__ px,
+                                double *__restrict__ py, double *__restrict__ pz) {
+    // block = one z plane
+    const int z = blockIdx.x;
+    const T *pl = drho + (size_t)z * nx * ny;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        double s = 0.0;
+        for (int y = 0; y < ny; ++y) s += (double)pl[(size_t)y * nx + x];
+        px[(size_t)z * nx + x] = s;
+    }
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+        double s = 0.0;
+        for (int x = 0; x < nx; ++x) s += (double)pl[(size_t)y * nx + x];
+        py[(size_t)z * ny + y] = s;
+    }
+    __shared__ double red[256];
+    double s = 0.0;
+    for (size_t i = threadIdx.x; i < (size_t)nx * ny; i += blockDim.x) s += (double)pl[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pz[z] = red[0];
+}
+
+// one block: the profiles are summed over planes in a fixed order into
+// shared memory, then a thread per axis mode accumulates
+// |sum_c p(c) e^{-2 pi i m c / n}|^2 / N.
+__global__ void axis_dft3_kernel(const double *__restrict__ px, const double *__restrict__ py,
+                                 const double *__restrict__ pz, int nx, int ny, int nz,
+                                 double *__restrict__ acc) {
+    extern __shared__ double tot[];   // [nx] + [ny] + [nz]
+    for (int c = threadIdx.x; c < nx; c += blockDim.x) {
+        double v = 0.0;
+        for (int z = 0; z < nz; ++z) v += px[(size_t)z * nx + c];
+        tot[c] = v;
+    }
+    for (int c = threadIdx.x; c < ny; c += blockDim.x) {
+        double v = 0.0;
+        for (int z = 0; z < nz; ++z) v += py[(size_t)z * ny + c];
+        tot[nx + c] = v;
+    }
+    for (int c = threadIdx.x; c < nz; c += blockDim.x) tot[nx + ny + c] = pz[c];
+    __syncthreads();
+    const int nmodes = nx / 2 + ny / 2 + nz / 2;
+    const double N = (double)nx * ny * nz;
+    for (int t = threadIdx.x; t < nmodes; t += blockDim.x) {
+        int m, n, off;
+        if (t < nx / 2) { m = t + 1; n = nx; off = 0; }
+        else if (t < nx / 2 + ny / 2) { m = t - nx / 2 + 1; n = ny; off = nx; }
+        else { m = t - nx / 2 - ny / 2 + 1; n = nz; off = nx + ny; }
+        double re = 0.0, im = 0.0;
+        for (int c = 0; c < n; ++c) {
+            double sn, cs;
+            sincospi(2.0 * (double)(((long long)m * c) % n) / n, &sn, &cs);
+            re += tot[off + c] * cs;
+            im -= tot[off + c] * sn;
+        }
+        acc[t] += (re * re + im * im) / N;
+    }
+}
+
+template <typename T>
+__global__ void drho3_kernel(const T *__restrict__ df, T *__restrict__ out, size_t n) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+         s += (size_t)gridDim.x * blockDim.x) {
+        T g = df[s];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) g += df[(size_t)i * n + s];
+        out[s] = g;
+    }
+}
+
+// FP64 conserved sums (mass deviation, jx, jy, jz): fixed two-pass order.
+template <typename T>
+__global__ void conserved3_kernel(const T *__restrict__ df, size_t n, double *__restrict__ part) {
+    __shared__ double red[4][256];
+    double m = 0, jx = 0, jy = 0, jz = 0;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+         s += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const double v = (double)df[(size_t)i * n + s];
+            m += v;
+            jx += cx3(i) * v;
+            jy += cy3(i) * v;
+            jz += cz3(i) * v;
+        }
+    }
+    red[0][threadIdx.x] = m;
+    red[1][threadIdx.x] = jx;
+    red[2][threadIdx.x] = jy;
+    red[3][threadIdx.x] = jz;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) part[4 * blockIdx.x + c] = red[c][0];
+}
+
+struct InitKeys3 {
+    uint32_t rk[20];
+};
+
+// delta f_i = w_i amp z(site), z from Philox block 3 of step 0 (amp = 0: rest).
+template <typename T>
+__global__ void init3_kernel(T *__restrict__ df, size_t n, T amp, InitKeys3 keys,
+                             uint32_t replica) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+         s += (size_t)gridDim.x * blockDim.x) {
+        T d = T(0);
+        if (amp != T(0)) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)s, 0u, replica, 3u), keys.rk);
+            T z0, z1;
+            box_muller(uniform01<T>(r.x), uniform01<T>(r.y), z0, z1);
+            d = amp * z0;
+        }
+#pragma unroll
+        for (int i = 0; i < 19; ++i) df[(size_t)i * n + s] = T(wq3(i)) * d;
+    }
+}
+
+template <typename T>
+__global__ void widen3_kernel(const T *__restrict__ df, double rho0, double *__restrict__ out,
+                              size_t n, int mode) {
+    // mode 0: density rho0 + sum_i delta f_i; mode 1: full populations
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+         s += (size_t)gridDim.x * blockDim.x) {
+        if (mode == 0) {
+            double v = 0.0;
+            for (int i = 0; i < 19; ++i) v += (double)df[(size_t)i * n + s];
+            out[s] = rho0 + v;
+        } else {
+            for (int i = 0; i < 19; ++i)
+                out[(size_t)i * n + s] = (double)df[(size_t)i * n + s] + wq3(i) * rho0;
+        }
+    }
+}
+template <typename T>
+__global__ void narrow3_kernel(const double *__restrict__ f, double rho0, T *__restrict__ df,
+                               size_t n) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n;
+         s += (size_t)gridDim.x * blockDim.x)
+        for (int i = 0; i < 19; ++i)
+            df[(size_t)i * n + s] = (T)(f[(size_t)i * n + s] - wq3(i) * rho0);
+}
+
+int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+}  // namespace lbsc
+
+using namespace lbsc;
+
+struct lb3_ctx {
+    int nx = 0, ny = 0, nz = 0, precision = 0, dev = 0;
+    double G = 0, tau = 1, kT = 0, rho0 = 0;
+    size_t n = 0, esize = 4;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *df[2] = {nullptr, nullptr};
+    int cur = 0;
+    int *d_flag = nullptr;
+    double *d_part = nullptr;      // conserved partials
+    int nred = 0;
+    void *drho = nullptr;          // delta rho of a sampling step
+    double *d_prof = nullptr;      // [nz][nx] + [nz][ny] + [nz] plane profiles
+    double *d_acc = nullptr;       // axis S(k) sums [nx/2 + ny/2 + nz/2]
+    double *d_io = nullptr;        // n doubles for read-outs
+    int sk_every = 0;
+    long long sk_start = 0, sk_count = 0, t = 0;
+    uint64_t seed = 0;
+    uint32_t replica = 0;
+    int strip_z = 32;
+    bool inited = false;
+};
+
+namespace {
+
+#define L3_CHECK(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return e_ == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA; \
+    } while (0)
+
+template <typename T>
+K3<T> params3(const lb3_ctx *h, bool sample) {
+    K3<T> k;
+    memset(&k, 0, sizeof(k));
+    k.src = (const T *)h->df[h->cur];
+    k.dst = (T *)h->df[h->cur ^ 1];
+    k.drho_out = sample ? (T *)h->drho : nullptr;
+    k.flag = h->d_flag;
+    k.nx = h->nx;
+    k.ny = h->ny;
+    k.nz = h->nz;
+    k.strip_z = h->strip_z;
+    k.noise = h->kT > 0.0 ? 1 : 0;
+    k.step = (uint32_t)h->t;
+    k.replica = h->replica;
+    k.rho0 = (T)h->rho0;
+    k.force_pref = (T)(-h->G / 3.0);
+    k.psi_c = (T)exp(-h->rho0);
+    k.psi0 = (T)(-expm1(-h->rho0));
+    const double gam = 1.0 - 1.0 / h->tau;
+    k.gamma = (T)gam;
+    k.hsrc = (T)(0.5 * (1.0 + gam));
+    const double mu = h->kT * 3.0;
+    for (int kk = 4; kk < 19; ++kk) k.amp[kk] = (T)sqrt(mu * norm3(kk) * (1.0 - gam * gam));
+    philox_round_keys(h->seed, k.rk);
+    return k;
+}
+
+template <typename T>
+int step3_once(lb3_ctx *h, bool sample) {
+    const K3<T> k = params3<T>(h, sample);
+    dim3 grid(h->nx / kTX3, h->ny / kTY3, (h->nz + h->strip_z - 1) / h->strip_z);
+    if (sample)
+        step3_kernel<T, true><<<grid, kThreads3, 0, h->stream>>>(k);
+    else
+        step3_kernel<T, false><<<grid, kThreads3, 0, h->stream>>>(k);
+    L3_CHECK(cudaGetLastError());
+    return LB_OK;
+}
+
+int sample3(lb3_ctx *h) {
+    double *px = h->d_prof, *py = px + (size_t)h->nz * h->nx, *pz = py + (size_t)h->nz * h->ny;
+    if (h->precision == LB_FP32)
+        profile3_kernel<float><<<h->nz, 256, 0, h->stream>>>((const float *)h->drho, h->nx, h->ny,
+                                                             px, py, pz);
+    else
+        profile3_kernel<double><<<h->nz, 256, 0, h->stream>>>((const double *)h->drho, h->nx,
+                                                              h->ny, px, py, pz);
+    L3_CHECK(cudaGetLastError());
+    axis_dft3_kernel<<<1, 512, (size_t)(h->nx + h->ny + h->nz) * sizeof(double), h->stream>>>(
+        px, py, pz, h->nx, h->ny, h->nz, h->d_acc);
+    L3_CHECK(cudaGetLastError());
+    h->sk_count += 1;
+    return LB_OK;
+}
+
+int sync3(lb3_ctx *h) {
+    L3_CHECK(cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    L3_CHECK(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        L3_CHECK(cudaMemset(h->d_flag, 0, sizeof(int)));
+        return LB_ERR_NONFINITE;
+    }
+    return LB_OK;
+}
+
+void free3(lb3_ctx *h) {
+    cudaFree(h->df[0]);
+    cudaFree(h->df[1]);
+    cudaFree(h->d_flag);
+    cudaFree(h->d_part);
+    cudaFree(h->drho);
+    cudaFree(h->d_prof);
+    cudaFree(h->d_acc);
+    cudaFree(h->d_io);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb3_create(lb3_ctx **out, int nx, int ny, int nz, double G, double tau, double kT,
+               int precision, void *stream) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    if (nx < kTX3 || ny < kTY3 || nz < 3 || nx % kTX3 || ny % kTY3) return LB_ERR_ARG;
+    if (19.0 * (double)nx * ny * nz >= 4294967296.0) return LB_ERR_ARG;
+    if (!(tau > 0.5) || !(kT >= 0.0) || !isfinite(G)) return LB_ERR_ARG;
+    if (precision != LB_FP32 && precision != LB_FP64) return LB_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return LB_ERR_CUDA;
+    lb3_ctx *h = new (std::nothrow) lb3_ctx();
+    if (!h) return LB_ERR_NOMEM;
+    cudaGetDevice(&h->dev);
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->G = G;
+    h->tau = tau;
+    h->kT = kT;
+    h->precision = precision;
+    h->esize = precision == LB_FP32 ? 4 : 8;
+    h->n = (size_t)nx * ny * nz;
+    h->strip_z = nz < 32 ? nz : 32;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        h->own_stream = true;
+    } else {
+        delete h;
+        return LB_ERR_CUDA;
+    }
+    h->nred = 152 * 4;
+    const size_t nb = 19 * h->n * h->esize;
+    cudaError_t e = cudaMalloc(&h->df[0], nb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->df[1], nb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_part, 4 * h->nred * sizeof(double));
+    if (e != cudaSuccess) {
+        free3(h);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+void lb3_destroy(lb3_ctx *h) {
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free3(h);
+    delete h;
+}
+
+int lb3_init(lb3_ctx *h, double rho0, uint64_t seed, double init_amp) {
+    if (!h || !(rho0 > 0.0) || !isfinite(init_amp)) return LB_ERR_ARG;
+    L3_CHECK(cudaSetDevice(h->dev));
+    h->rho0 = rho0;
+    h->seed = seed;
+    h->t = 0;
+    h->cur = 0;
+    InitKeys3 k;
+    philox_round_keys(seed, k.rk);
+    if (h->precision == LB_FP32)
+        init3_kernel<float><<<grid_for(h->n), 256, 0, h->stream>>>((float *)h->df[0], h->n,
+                                                                    (float)init_amp, k, h->replica);
+    else
+        init3_kernel<double><<<grid_for(h->n), 256, 0, h->stream>>>((double *)h->df[0], h->n,
+                                                                     init_amp, k, h->replica);
+    L3_CHECK(cudaGetLastError());
+    if (h->d_acc) {
+        L3_CHECK(cudaMemsetAsync(h->d_acc, 0, (h->nx / 2 + h->ny / 2 + h->nz / 2) * sizeof(double),
+                                 h->stream));
+        h->sk_count = 0;
+    }
+    h->inited = true;
+    return LB_OK;
+}
+
+int lb3_set_replica(lb3_ctx *h, uint32_t replica) {
+    if (!h) return LB_ERR_ARG;
+    h->replica = replica;
+    return LB_OK;
+}
+
+int lb3_set_strip(lb3_ctx *h, int planes) {
+    if (!h || planes < 1 || planes > h->nz) return LB_ERR_ARG;
+    h->strip_z = planes;
+    return LB_OK;
+}
+
+int lb3_step(lb3_ctx *h, int n) {
+    if (!h || n < 0) return LB_ERR_ARG;
+    if (!h->inited) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    for (int s = 0; s < n; ++s) {
+        const long long tn = h->t + 1;
+        const bool sample = h->sk_every > 0 && h->d_acc && tn >= h->sk_start &&
+                            (tn - h->sk_start) % h->sk_every == 0;
+        const int rc = h->precision == LB_FP32 ? step3_once<float>(h, sample)
+                                               : step3_once<double>(h, sample);
+        if (rc) return rc;
+        h->cur ^= 1;
+        h->t = tn;
+        if (sample) {
+            const int r2 = sample3(h);
+            if (r2) return r2;
+        }
+    }
+    return LB_OK;
+}
+
+int lb3_sync(lb3_ctx *h) {
+    if (!h) return LB_ERR_ARG;
+    L3_CHECK(cudaSetDevice(h->dev));
+    return sync3(h);
+}
+
+long long lb3_get_step(const lb3_ctx *h) { return h ? h->t : -1; }
+
+static int ensure_io3(lb3_ctx *h) {
+    if (h->d_io) return LB_OK;
+    L3_CHECK(cudaMalloc(&h->d_io, 19 * h->n * sizeof(double)));
+    return LB_OK;
+}
+
+int lb3_density(lb3_ctx *h, double *host_out) {
+    if (!h || !host_out) return LB_ERR_ARG;
+    if (!h->inited) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    int rc = ensure_io3(h);
+    if (rc) return rc;
+    if (h->precision == LB_FP32)
+        widen3_kernel<float><<<grid_for(h->n), 256, 0, h->stream>>>(
+            (const float *)h->df[h->cur], h->rho0, h->d_io, h->n, 0);
+    else
+        widen3_kernel<double><<<grid_for(h->n), 256, 0, h->stream>>>(
+            (const double *)h->df[h->cur], h->rho0, h->d_io, h->n, 0);
+    L3_CHECK(cudaGetLastError());
+    L3_CHECK(cudaMemcpyAsync(host_out, h->d_io, h->n * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    return sync3(h);
+}
+
+int lb3_populations(lb3_ctx *h, double *host_out) {
+    if (!h || !host_out) return LB_ERR_ARG;
+    if (!h->inited) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    int rc = ensure_io3(h);
+    if (rc) return rc;
+    if (h->precision == LB_FP32)
+        widen3_kernel<float><<<grid_for(h->n), 256, 0, h->stream>>>(
+            (const float *)h->df[h->cur], h->rho0, h->d_io, h->n, 1);
+    else
+        widen3_kernel<double><<<grid_for(h->n), 256, 0, h->stream>>>(
+            (const double *)h->df[h->cur], h->rho0, h->d_io, h->n, 1);
+    L3_CHECK(cudaGetLastError());
+    L3_CHECK(cudaMemcpyAsync(host_out, h->d_io, 19 * h->n * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+    return sync3(h);
+}
+
+int lb3_set_populations(lb3_ctx *h, const double *host_f) {
+    if (!h || !host_f) return LB_ERR_ARG;
+    if (!h->inited) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    int rc = ensure_io3(h);
+    if (rc) return rc;
+    L3_CHECK(cudaMemcpyAsync(h->d_io, host_f, 19 * h->n * sizeof(double), cudaMemcpyHostToDevice,
+                             h->stream));
+    if (h->precision == LB_FP32)
+        narrow3_kernel<float><<<grid_for(h->n), 256, 0, h->stream>>>(h->d_io, h->rho0,
+                                                                      (float *)h->df[h->cur], h->n);
+    else
+        narrow3_kernel<double><<<grid_for(h->n), 256, 0, h->stream>>>(
+            h->d_io, h->rho0, (double *)h->df[h->cur], h->n);
+    L3_CHECK(cudaGetLastError());
+    return sync3(h);
+}
+
+int lb3_conserved(lb3_ctx *h, double out[4]) {
+    if (!h || !out) return LB_ERR_ARG;
+    if (!h->inited) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    if (h->precision == LB_FP32)
+        conserved3_kernel<float><<<h->nred, 256, 0, h->stream>>>((const float *)h->df[h->cur],
+                                                                  h->n, h->d_part);
+    else
+        conserved3_kernel<double><<<h->nred, 256, 0, h->stream>>>((const double *)h->df[h->cur],
+                                                                   h->n, h->d_part);
+    L3_CHECK(cudaGetLastError());
+    double *part = new (std::nothrow) double[4 * h->nred];
+    if (!part) return LB_ERR_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(part, h->d_part, 4 * h->nred * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    int rc = e == cudaSuccess ? sync3(h) : LB_ERR_CUDA;
+    if (rc == LB_OK) {
+        double s[4] = {0, 0, 0, 0};
+        for (int b = 0; b < h->nred; ++b)
+            for (int c = 0; c < 4; ++c) s[c] += part[4 * b + c];
+        out[0] = (double)h->n * h->rho0 + s[0];
+        out[1] = s[1];
+        out[2] = s[2];
+        out[3] = s[3];
+    }
+    delete[] part;
+    return rc;
+}
+
+int lb3_sk_config(lb3_ctx *h, int every, long long start) {
+    if (!h || every < 0 || start < 0) return LB_ERR_ARG;
+    L3_CHECK(cudaSetDevice(h->dev));
+    if (every > 0 && !h->d_acc) {
+        const int nm = h->nx / 2 + h->ny / 2 + h->nz / 2;
+        L3_CHECK(cudaMalloc(&h->drho, h->n * h->esize));
+        L3_CHECK(cudaMalloc(&h->d_prof, ((size_t)h->nz * (h->nx + h->ny + 1)) * sizeof(double)));
+        L3_CHECK(cudaMalloc(&h->d_acc, nm * sizeof(double)));
+        L3_CHECK(cudaMemsetAsync(h->d_acc, 0, nm * sizeof(double), h->stream));
+        h->sk_count = 0;
+    }
+    h->sk_every = every;
+    h->sk_start = start;
+    return LB_OK;
+}
+
+int lb3_sk_reset(lb3_ctx *h) {
+    if (!h) return LB_ERR_ARG;
+    if (h->d_acc) {
+        L3_CHECK(cudaSetDevice(h->dev));
+        L3_CHECK(cudaMemsetAsync(h->d_acc, 0, (h->nx / 2 + h->ny / 2 + h->nz / 2) * sizeof(double),
+                                 h->stream));
+    }
+    h->sk_count = 0;
+    return LB_OK;
+}
+
+int lb3_structure_factor_axes(lb3_ctx *h, double *host_out, long long *nsamples_out) {
+    if (!h || !host_out) return LB_ERR_ARG;
+    const int nm = h->nx / 2 + h->ny / 2 + h->nz / 2;
+    if (!h->d_acc) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    L3_CHECK(cudaMemcpyAsync(host_out, h->d_acc, nm * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    const int rc = sync3(h);
+    if (rc) return rc;
+    for (int m = 0; m < nm; ++m) host_out[m] = h->sk_count ? host_out[m] / (double)h->sk_count : 0.0;
+    if (nsamples_out) *nsamples_out = h->sk_count;
+    return LB_OK;
+}
+
+}  // extern "C"

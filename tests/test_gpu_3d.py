@@ -1,0 +1,100 @@
+"""The D3Q19 step on the GPU against the FP64 oracle: FP64 to 1e-12 and FP32
+to 1e-4 per site, with noise, force and ragged z strips; exact flat
+equilibrium; conservation; the axis S(k) against the oracle's on the same
+noise; and an FP32 ensemble of replicas against Eq. (16) on the axes."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import theory as T
+from pairs import LN2, max_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(nx, ny, nz, G, tau, kT, precision, rho0, seed, amp, replica=0, strip=None):
+    from paper_2212_07848_gb300.lattice3 import Lattice3
+    g = Lattice3(nx, ny, nz, G, tau, kT, precision=precision)
+    if strip:
+        g.set_strip(strip)
+    g.set_replica(replica)
+    g.init(rho0, seed, amp)
+    o = O.OracleLattice3(nx, ny, nz, G, tau, kT, replica=replica)
+    o.init(rho0, seed, amp)
+    return g, o
+
+
+@pytest.mark.parametrize("nx,ny,nz,G,tau,kT,rho0,amp,strip,steps", [
+    (32, 8, 6, -3.6, 1.0, 1e-4, LN2, 0.01, None, 200),
+    (64, 16, 12, -4.5, 0.8, 1e-5, 0.33, 0.005, 5, 100),     # several tiles, ragged strips
+    (32, 16, 7, -4.0, 1.3, 0.0, 0.7, 0.02, 3, 100),          # no noise, odd nz
+])
+def test_fp64_matches_oracle(nx, ny, nz, G, tau, kT, rho0, amp, strip, steps):
+    g, o = _pair(nx, ny, nz, G, tau, kT, "fp64", rho0, 17, amp, replica=2, strip=strip)
+    g.step(steps)
+    o.step(steps)
+    assert max_rel(g.populations(), o.populations()) < 1e-12
+    assert max_rel(g.density(), o.density()) < 1e-12
+
+
+def test_fp32_matches_oracle():
+    g, o = _pair(32, 16, 8, -4.2, 1.0, 1e-5, "fp32", 0.6, 4, 0.005)
+    g.step(100)
+    o.step(100)
+    assert max_rel(g.populations(), o.populations()) < 1e-4
+    assert max_rel(g.density(), o.density()) < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_flat_equilibrium_exact_and_conservation(precision):
+    from paper_2212_07848_gb300.lattice3 import Lattice3
+    g = Lattice3(32, 8, 8, -4.5, 0.9, 0.0, precision=precision)
+    g.init(0.4)
+    f0 = g.populations()
+    g.step(20)
+    assert np.array_equal(g.populations(), f0)
+    g = Lattice3(32, 16, 8, -3.8, 0.9, 1e-4, precision=precision)
+    g.init(LN2, 3, 0.02)
+    c0 = g.conserved()
+    g.step(300)
+    c1 = g.conserved()
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert abs(c1[0] - c0[0]) < tol * c0[0]
+    assert np.abs(c1[1:] - c0[1:]).max() < tol * c0[0]
+
+
+def test_axis_structure_factor_matches_oracle():
+    g, o = _pair(32, 8, 8, -3.6, 1.0, 1e-4, "fp64", LN2, 5, 0.0)
+    g.sk_config(1, 50)
+    o.sk_config(1, 50)
+    g.step(120)
+    o.step(120)
+    Sg, ng = g.structure_factor_axes()
+    So, no = o.structure_factor_axes()
+    assert ng == no == 71
+    assert np.abs(Sg - So).max() < 1e-9 * np.abs(So).max()
+
+
+def test_fp32_replicas_match_eq16_on_axes():
+    """Eight replicas of 32^3 (supercritical C1 state): axis modes agree with
+    Eq. (16) within 3% or 4 standard errors."""
+    from paper_2212_07848_gb300.lattice3 import Lattice3
+    L, G, kT, steps, start = 32, -3.6, 1e-5, 4000, 1001
+    vals = []
+    for r in range(8):
+        g = Lattice3(L, L, L, G, 1.0, kT)
+        g.set_replica(r)
+        g.init(LN2, 31, 0.0)
+        g.sk_config(1, start)
+        g.step(steps)
+        S, n = g.structure_factor_axes()
+        assert n == steps - start + 1
+        vals += [S[a * (L // 2):(a + 1) * (L // 2)] for a in range(3)]
+        g.close()
+    v = np.array(vals)
+    m = np.arange(1, L // 2 + 1)
+    th = T.sk_axis(2 * np.pi * m / L, LN2, G, kT)
+    mean, sem = v.mean(axis=0), v.std(axis=0, ddof=1) / np.sqrt(len(v))
+    sel = m >= 2
+    dev = np.abs(mean - th)
+    assert ((dev <= 0.03 * th) | (dev <= 4 * sem))[sel].all(), np.round(mean / th - 1, 3)
