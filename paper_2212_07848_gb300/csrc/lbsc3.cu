@@ -100,17 +100,15 @@ template <typename T> struct K3 {
     uint32_t rk[20];
 };
 
+// Pull of one site from precomputed wrapped offsets: xo[1 + d] = x + d,
+// yo[1 + d] = (y + d) nx and zo[1 + d] = (z + d) nx ny for d = -1, 0, 1.
 template <typename T>
-__device__ __forceinline__ void pull3(const T *__restrict__ src, uint32_t plane, int nx, int ny,
-                                      int nz, int x, int y, int z, T g[19]) {
+__device__ __forceinline__ void pull3(const T *__restrict__ src, uint32_t plane,
+                                      const uint32_t xo[3], const uint32_t yo[3],
+                                      const uint32_t zo[3], T g[19]) {
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        int xs = x - cx3(i), ys = y - cy3(i), zs = z - cz3(i);
-        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-        g[i] = __ldg(src + (uint32_t)i * plane + ((uint32_t)zs * ny + ys) * nx + xs);
-    }
+    for (int i = 0; i < 19; ++i)
+        g[i] = __ldg(src + ((uint32_t)i * plane + zo[1 - cz3(i)] + yo[1 - cy3(i)] + xo[1 - cx3(i)]));
 }
 
 template <typename T>
@@ -224,7 +222,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
 }
 
 template <typename T, bool SAMPLE>
-__global__ void __launch_bounds__(kThreads3) step3_kernel(const K3<T> p) {
+__global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
     __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
     const int tx = threadIdx.x % kBX3, ty = threadIdx.x / kBX3;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -236,13 +234,22 @@ __global__ void __launch_bounds__(kThreads3) step3_kernel(const K3<T> p) {
     const int z0 = blockIdx.z * p.strip_z, z1 = min(z0 + p.strip_z, nz);
     const int it_end = (z1 - z0) + 2;
 
+    // wrapped neighbour offsets of this column (constant along z)
+    const uint32_t xo[3] = {(uint32_t)(x == 0 ? nx - 1 : x - 1), (uint32_t)x,
+                            (uint32_t)(x == nx - 1 ? 0 : x + 1)};
+    const uint32_t yo[3] = {(uint32_t)(y == 0 ? ny - 1 : y - 1) * nx, (uint32_t)y * nx,
+                            (uint32_t)(y == ny - 1 ? 0 : y + 1) * nx};
+    const uint32_t nxy = (uint32_t)nx * ny;
+
     T qprev[19], qcur[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) qprev[i] = T(0);
     for (int it = 0; it < it_end; ++it) {
         int zz = z0 - 1 + it;
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-        pull3(p.src, plane, nx, ny, nz, x, y, zz, qcur);
+        const uint32_t zo[3] = {(uint32_t)(zz == 0 ? nz - 1 : zz - 1) * nxy, (uint32_t)zz * nxy,
+                                (uint32_t)(zz == nz - 1 ? 0 : zz + 1) * nxy};
+        pull3(p.src, plane, xo, yo, zo, qcur);
         s_psi[it & 3][ty][tx] = dpsi3<T>(sum19(qcur), p.psi_c);
         __syncthreads();
         if (it >= 2 && interior) {

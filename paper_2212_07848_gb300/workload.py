@@ -1,6 +1,7 @@
 """Run one synthetic lattice for a number of steps (profiling and sizing).
 
     python -m paper_2212_07848_gb300.workload --nx 2048 --ny 2048 --steps 5
+    python -m paper_2212_07848_gb300.workload --nx 256 --ny 256 --nz 256 --steps 5   # D3Q19
 
 Defaults to the critical quench of the benchmark (G = -5.0, rho0 = ln 2,
 kT = 1e-6, E4, FP32) on a smaller square lattice.  Prints the wall time.
@@ -23,7 +24,21 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--sk-every", type=int, default=0)
     ap.add_argument("--strip", type=int, default=0)
+    ap.add_argument("--nz", type=int, default=0, help="> 0: a D3Q19 lattice nx x ny x nz")
     a = ap.parse_args()
+    if a.nz > 0:
+        from .lattice3 import Lattice3
+        lat = Lattice3(a.nx, a.ny, a.nz, a.G, a.tau, a.kT, precision=a.precision)
+        if a.strip:
+            lat.set_strip(a.strip)
+        lat.init(a.rho0, 100, 0.0)
+        t0 = time.perf_counter()
+        lat.step(a.steps)
+        lat.sync()
+        dt = time.perf_counter() - t0
+        print(f"{a.nx}x{a.ny}x{a.nz} {a.precision} D3Q19: {a.steps} steps in {dt * 1e3:.2f} ms")
+        lat.close()
+        return
     from .lattice import Lattice
     lat = Lattice(a.nx, a.ny, a.G, a.tau, a.kT, stencil=a.stencil, precision=a.precision)
     if a.strip:
