@@ -406,9 +406,10 @@ int lb_nn_mse(const void *y, int c, const float *target, const float *base, size
 /* Rollout update: FP32 state [n] += y[.][0] - m, channel 0 of the network
  * input x [n][cx] = BF16(state), channel 2 (when cx > 2) = the increment just
  * applied, other channels of x untouched.  With mean_buf (a caller-owned
- * device float, or NULL for m = 0) m is the mean of y[.][0] over the n
- * pixels, written to mean_buf first: the increment then has zero mean and the
- * field's mass is conserved as the lattice conserves it. */
+ * device buffer of at least 513 floats, or NULL for m = 0) m is the mean of
+ * y[.][0] over the n pixels, written to mean_buf[0] first (mean_buf[1..] holds
+ * partial sums; fixed summation order): the increment then has zero mean and
+ * the field's mass is conserved as the lattice conserves it. */
 int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n, float *mean_buf,
                    void *stream);
 /* Adam step (bias-corrected, `step` >= 1) on FP32 w with gradient g and moments

@@ -421,20 +421,35 @@ __global__ void mse_kernel(const bf16 *__restrict__ y, int C, const float *__res
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
 }
 
-// Mean of channel 0 of y [n][C] (one block, fixed summation order).
-__global__ void __launch_bounds__(1024) mean_ch0_kernel(const bf16 *__restrict__ y, int C, size_t n,
-                                                       float *__restrict__ out) {
-    __shared__ float part[32];
-    float s = 0.f;
-    for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += __bfloat162float(y[i * C]);
+// Mean of channel 0 of y [n][C] in two passes with a fixed summation order:
+// block b writes the sum of its grid-stride share to part[b]; one block then
+// adds the nb partial sums and writes part[-1] = sum / n (part = buf + 1).
+constexpr int kMeanBlocks = 512;
+__device__ __forceinline__ float block_sum256(float s) {
+    __shared__ float red[8];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
+    s = 0.f;
     if (threadIdx.x < 32) {
-        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) out[0] = s / (float)n;
     }
+    return s;   // valid in thread 0
+}
+__global__ void __launch_bounds__(256) mean_part_kernel(const bf16 *__restrict__ y, int C, size_t n,
+                                                       float *__restrict__ part) {
+    float s = 0.f;
+    GRID_STRIDE(i, n) s += __bfloat162float(y[i * C]);
+    s = block_sum256(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void __launch_bounds__(256) mean_final_kernel(const float *__restrict__ part, int nb,
+                                                        size_t n, float *__restrict__ out) {
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+    s = block_sum256(s);
+    if (threadIdx.x == 0) out[0] = s / (float)n;
 }
 
 // Rollout update: state (FP32) += y[.][0] - mean (mean = *mean_in, or 0
@@ -626,7 +641,10 @@ int lb_nn_residual(float *state, const void *y, int c, void *x, int cx, size_t n
     if (!state || !y || !x || c < 1 || cx < 1) return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (mean_buf) {
-        mean_ch0_kernel<<<1, 1024, 0, s>>>((const bf16 *)y, c, n, mean_buf);
+        size_t want = (n + 2047) / 2048;
+        const int nb = (int)(want < 1 ? 1 : (want > (size_t)kMeanBlocks ? kMeanBlocks : want));
+        mean_part_kernel<<<nb, 256, 0, s>>>((const bf16 *)y, c, n, mean_buf + 1);
+        mean_final_kernel<<<1, 256, 0, s>>>(mean_buf + 1, nb, n, mean_buf);
         if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
     }
     residual_kernel<<<blocks_for(n), 256, 0, s>>>(state, (const bf16 *)y, c, (bf16 *)x, cx, n,

@@ -284,7 +284,7 @@ class _StrideGraph:
         self.stream = torch.cuda.Stream()
         self.x = torch.zeros((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
         self.state = torch.zeros((m, m), dtype=torch.float32, device="cuda")
-        self.mean = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.mean = torch.zeros(513, dtype=torch.float32, device="cuda")
         saved = net.s
         net.s = self.stream.cuda_stream
         try:
@@ -332,7 +332,7 @@ def rollout(net, frame0, G, strides, prev0=None, graph=True):
             net._stride_graph = _StrideGraph(net)
         return net._stride_graph.run(frame0, G, strides, prev0, out)
     x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
-    mean = torch.zeros(1, dtype=torch.float32, device="cuda")
+    mean = torch.zeros(513, dtype=torch.float32, device="cuda")
     state = frame0.clone()
     expand(L, state, G, x, prev0, net.s)
     for s in range(strides):

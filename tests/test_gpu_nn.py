@@ -203,11 +203,11 @@ def test_coarse_expand_mse_residual():
     assert np.all(xr[:, 1] == 0.75)
     assert np.array_equal(xr[:, 2], _np(y)[:, 0])          # the increment just applied
     # zero-mean increments: the mass of the state is conserved
-    mean = torch.zeros(1, device="cuda")
+    mean = torch.zeros(513, device="cuda")
     state2 = base.clone()
     assert L.lb_nn_residual(_p(state2), _p(y), 16, _p(x), 16, n, _p(mean), None) == 0
     torch.cuda.synchronize()
     mu = _np(y)[:, 0].astype(np.float64).mean()
-    assert abs(float(mean.item()) - mu) < 1e-6 * max(1.0, abs(mu)) + 1e-7
+    assert abs(float(mean[0].item()) - mu) < 1e-6 * max(1.0, abs(mu)) + 1e-7
     assert abs(float(state2.double().sum() - base.double().sum())) < 1e-4
     assert np.abs(state2.cpu().numpy() - (base.cpu().numpy() + _np(y)[:, 0] - mu)).max() < 1e-6
