@@ -7,8 +7,8 @@
 // a strip of z planes.  Its 34 x 10 threads cover the tile and its one-column
 // halo ring: every thread pulls its column's populations for plane z + 1 and
 // writes that plane's pseudopotential deviation into a shared-memory ring of
-// four planes; after the barrier the 32 x 8 interior threads collide plane z
-// from the populations they pulled one plane earlier (kept in registers).
+// four planes; after the barrier the 32 x 8 interior threads pull plane z
+// again (L1 hits: they pulled it one iteration earlier) and collide it.
 // The force is Eq. (1) over the 18 D3Q19 neighbours with the fourth-order
 // isotropic weights 1/6 (axes) and 1/12 (face diagonals), summed as
 // antisymmetric pairs.  The collision runs in the 19-moment basis:
@@ -241,19 +241,22 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
                             (uint32_t)(y == ny - 1 ? 0 : y + 1) * nx};
     const uint32_t nxy = (uint32_t)nx * ny;
 
-    T qprev[19], qcur[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) qprev[i] = T(0);
+    uint32_t zprev[3] = {0u, 0u, 0u};   // offsets of the plane pulled one iteration ago
     for (int it = 0; it < it_end; ++it) {
         int zz = z0 - 1 + it;
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const uint32_t zo[3] = {(uint32_t)(zz == 0 ? nz - 1 : zz - 1) * nxy, (uint32_t)zz * nxy,
                                 (uint32_t)(zz == nz - 1 ? 0 : zz + 1) * nxy};
-        pull3(p.src, plane, xo, yo, zo, qcur);
-        s_psi[it & 3][ty][tx] = dpsi3<T>(sum19(qcur), p.psi_c);
+        {
+            T g[19];
+            pull3(p.src, plane, xo, yo, zo, g);
+            s_psi[it & 3][ty][tx] = dpsi3<T>(sum19(g), p.psi_c);
+        }
         __syncthreads();
         if (it >= 2 && interior) {
-            // collide plane zc = zz - 1 (pulled in the previous iteration)
+            // collide plane zc = zz - 1: its populations are pulled again (they
+            // were pulled in the previous iteration and come from L1), which
+            // keeps 19 values per thread out of the registers
             const int zc = z0 - 2 + it;
             const int sm = (it - 2) & 3, sc = (it - 1) & 3, sp = it & 3;
             // Eq. (1): sum over the 18 neighbours as antisymmetric pairs
@@ -274,15 +277,17 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
             const T Fx = p.force_pref * psic * Sx, Fy = p.force_pref * psic * Sy,
                     Fz = p.force_pref * psic * Sz;
             const uint32_t site = ((uint32_t)zc * ny + y) * nx + x;
-            T f[19];
-            collide3(qprev, Fx, Fy, Fz, p, site, f);
+            T g[19], f[19];
+            pull3(p.src, plane, xo, yo, zprev, g);
+            collide3(g, Fx, Fy, Fz, p, site, f);
 #pragma unroll
             for (int i = 0; i < 19; ++i) p.dst[(uint32_t)i * plane + site] = f[i];
-            if (SAMPLE) p.drho_out[site] = sum19(qprev);
+            if (SAMPLE) p.drho_out[site] = sum19(g);
             if (!isfinite(f[1] + f[7])) atomicOr(p.flag, LB_STEP_NONFINITE);
         }
-#pragma unroll
-        for (int i = 0; i < 19; ++i) qprev[i] = qcur[i];
+        zprev[0] = zo[0];
+        zprev[1] = zo[1];
+        zprev[2] = zo[2];
         // slot (it + 1) & 3, written next, was last read in iteration it - 1,
         // before this iteration's barrier
     }
