@@ -20,6 +20,8 @@
  *     (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz, 3c^4-6c^2+1,
  *     (2c^2-3)(3cx^2-c^2), (2c^2-3)(cy^2-cz^2), orthogonal under the weights;
  *     modes 0..3 conserved, 4..18 carry noise of variance mu rho b_k (1-gamma^2);
+ *   - pseudopotential: the three forms of the 2D oracle, 1 - exp(-rho) (kind 0),
+ *     Eq. (5) sqrt(Tc nc) exp(1 - nc/rho) (kind 1) and a exp(-b/rho) (kind 2);
  *   - force stencil (Eq. (1)): the 18 D3Q19 neighbours with w = 1/6 (axes) and
  *     1/12 (diagonals), normalised to sum_a w_a e_ax^2 = 1 (fourth-order
  *     isotropic), so p = rho c_s^2 + (G c_s^2 / 2) psi^2 as in 2D;
@@ -107,9 +109,19 @@ typedef struct or3_params {
     double rho0;
     uint64_t seed;
     uint32_t replica;
+    int psi_kind;            /* 0: 1-exp(-rho); 1: sqrt(Tc nc) exp(1-nc/rho) (Eq. (5));
+                                2: a exp(-b/rho) */
+    double psi_p1, psi_p2;   /* kind 1: (Tc, nc); kind 2: (a, b) */
 } or3_params;
 
-static double psi3(double rho) { return 1.0 - exp(-rho); }
+/* The pseudopotential of the chosen kind (the same three forms as in 2D). */
+static double psi3(const or3_params *p, double rho) {
+    switch (p->psi_kind) {
+    case 1: return sqrt(p->psi_p1 * p->psi_p2) * exp(1.0 - p->psi_p2 / rho);
+    case 2: return p->psi_p1 * exp(-p->psi_p2 / rho);
+    default: return 1.0 - exp(-rho);
+    }
+}
 
 static void draw3(const or3_params *p, uint32_t site, uint32_t step, uint32_t block,
                   uint32_t out[4]) {
@@ -328,7 +340,7 @@ static void step3(or3_lattice *h) {
     for (size_t s = 0; s < n; ++s) {
         double v = 0.0;
         for (int i = 0; i < 19; ++i) v += h->g[(size_t)i * n + s];
-        h->psi[s] = psi3(v);
+        h->psi[s] = psi3(p, v);
     }
     /* 3. force (Eq. (1) with the D3Q19 neighbours), collision, noise */
 #pragma omp parallel for schedule(static)
@@ -367,7 +379,7 @@ void or3_force_field(const or3_lattice *h, double *F) {
     size_t n = (size_t)nx * ny * nz;
     double *rho = (double *)malloc(sizeof(double) * n), *ps = (double *)malloc(sizeof(double) * n);
     or3_density(h, rho);
-    for (size_t s = 0; s < n; ++s) ps[s] = psi3(rho[s]);
+    for (size_t s = 0; s < n; ++s) ps[s] = psi3(p, rho[s]);
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {

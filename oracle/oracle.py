@@ -35,6 +35,8 @@ class Or3Params(C.Structure):
         ("rho0", C.c_double),
         ("seed", C.c_uint64),
         ("replica", C.c_uint32),
+        ("psi_kind", C.c_int),
+        ("psi_p1", C.c_double), ("psi_p2", C.c_double),
     ]
 
 
@@ -275,7 +277,7 @@ def moment_basis3():
 
 def normals3(nx, ny, nz, seed, replica, site, t):
     """The 15 thermal normals (modes 4..18) of a site and step."""
-    p = Or3Params(nx, ny, nz, 0.0, 1.0, 0.0, 0.0, seed, replica)
+    p = Or3Params(nx, ny, nz, 0.0, 1.0, 0.0, 0.0, seed, replica, 0, 0.0, 0.0)
     z = np.zeros(15)
     lib().or3_normals(C.byref(p), site, t, z)
     return z
@@ -283,10 +285,11 @@ def normals3(nx, ny, nz, seed, replica, site, t):
 
 class OracleLattice3:
     """One periodic nx x ny x nz D3Q19 lattice held by the FP64 oracle
-    (psi = 1 - exp(-rho), E4 force stencil, BGK + Guo, 15 noise modes)."""
+    (psi of kind 0, 1 or 2 as in 2D, E4 force stencil, BGK + Guo, 15 noise
+    modes)."""
 
-    def __init__(self, nx, ny, nz, G, tau, kT, replica=0):
-        self.p = Or3Params(nx, ny, nz, G, tau, kT, 0.0, 0, replica)
+    def __init__(self, nx, ny, nz, G, tau, kT, replica=0, psi_kind=0, psi_p1=0.0, psi_p2=0.0):
+        self.p = Or3Params(nx, ny, nz, G, tau, kT, 0.0, 0, replica, psi_kind, psi_p1, psi_p2)
         self.nx, self.ny, self.nz = nx, ny, nz
         self._h = lib().or3_create(C.byref(self.p))
         if not self._h:

@@ -175,26 +175,35 @@ def test_ideal_gas_structure_factor_is_flat():
     assert np.abs(S / ref - 1.0).max() < 0.15
 
 
-@pytest.mark.parametrize("axis", [0, 1, 2])
-def test_force_continuum_limit(axis):
+@pytest.mark.parametrize("axis,kind", [(0, 0), (1, 0), (2, 0), (0, 1), (2, 2)])
+def test_force_continuum_limit(axis, kind):
     """A weak sinusoidal density: the force approaches -G c_s^2 psi grad psi
-    with second-order accuracy in the wave number."""
+    with second-order accuracy in the wave number, for each pseudopotential
+    (kind 1: Eq. (5) with Tc = 5/12, nc = 1; kind 2: a = 1.3, b = 0.8)."""
+    p1, p2 = {0: (0.0, 0.0), 1: (5.0 / 12.0, 1.0), 2: (1.3, 0.8)}[kind]
+    rho0 = {0: LN2, 1: 1.0, 2: 0.9}[kind]
+    psi_f = {0: lambda r: 1 - np.exp(-r),
+             1: lambda r: np.sqrt(p1 * p2) * np.exp(1 - p2 / r),
+             2: lambda r: p1 * np.exp(-p2 / r)}[kind]
+    dpsi_f = {0: lambda r: np.exp(-r),
+              1: lambda r: psi_f(r) * p2 / r ** 2,
+              2: lambda r: psi_f(r) * p2 / r ** 2}[kind]
     errs = []
     for L in (16, 32):
         shape = [4, 4, 4]
         shape[axis] = L
         nx, ny, nz = shape
-        o = O.OracleLattice3(nx, ny, nz, -4.0, 1.0, 0.0)
-        o.init(LN2)
+        o = O.OracleLattice3(nx, ny, nz, -4.0, 1.0, 0.0, psi_kind=kind, psi_p1=p1, psi_p2=p2)
+        o.init(rho0)
         c, w = O.lattice3_constants()
         zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         coord = (xx, yy, zz)[axis]
         k = 2 * np.pi / L
-        rho = LN2 + 0.05 * np.sin(k * coord)
+        rho = rho0 + 0.05 * np.sin(k * coord)
         o.set_populations(w[:, None, None, None] * rho[None])
         F = o.force()
-        psi = 1 - np.exp(-rho)
-        dpsi = np.exp(-rho) * 0.05 * k * np.cos(k * coord)
+        psi = psi_f(rho)
+        dpsi = dpsi_f(rho) * 0.05 * k * np.cos(k * coord)
         ref = 4.0 / 3.0 * psi * dpsi
         errs.append(np.abs(F[axis] - ref).max() / np.abs(ref).max())
         others = [b for b in range(3) if b != axis]
