@@ -312,7 +312,7 @@ int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
  * The paper's own setting: Eq. (12) on a D3Q19 lattice (c_s^2 = 1/3; weights
  * 1/3, 1/18, 1/36; velocity order: rest; +x, -x, +y, -y, +z, -z; then the
  * face diagonals of the xy, xz and yz planes as (+,+), (-,-), (+,-), (-,+)),
- * psi = 1 - exp(-rho), the Shan-Chen force of Eq. (1) over the 18 neighbours
+ * psi of kind LB_PSI_* (default 1 - exp(-rho)), the Shan-Chen force of Eq. (1) over the 18 neighbours
  * with weights 1/6 (axes) and 1/12 (diagonals), BGK collision with Guo
  * forcing in the 19-moment basis (1, c, c^2-1, 3cx^2-c^2, cy^2-cz^2, cxcy,
  * cycz, czcx, (3c^2-5)c, (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz,
@@ -331,6 +331,9 @@ void lb3_destroy(lb3_ctx *h);
 /* Homogeneous rho0 at rest, plus an optional density kick init_amp z(site)
  * from Philox block 3 of step 0. */
 int lb3_init(lb3_ctx *h, double rho0, uint64_t seed, double init_amp);
+/* Pseudopotential (LB_PSI_*, parameters as in lb_params; default
+ * LB_PSI_EXP); takes effect from the next step. */
+int lb3_set_psi(lb3_ctx *h, int psi_kind, double psi_p1, double psi_p2);
 int lb3_set_replica(lb3_ctx *h, uint32_t replica);
 /* z planes marched by one CTA (performance only). */
 int lb3_set_strip(lb3_ctx *h, int planes);

@@ -42,7 +42,7 @@ EXPORTED = [
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
     "lb_ens_conserved", "lb_ens_structure_factor", "lb_sk_moments", "lb_ens_set_launch",
     "lb_ens_get_launch",
-    "lb3_create", "lb3_destroy", "lb3_init", "lb3_set_replica", "lb3_set_strip", "lb3_step",
+    "lb3_create", "lb3_destroy", "lb3_init", "lb3_set_psi", "lb3_set_replica", "lb3_set_strip", "lb3_step",
     "lb3_sync", "lb3_get_step", "lb3_density", "lb3_populations", "lb3_set_populations",
     "lb3_conserved", "lb3_sk_config", "lb3_sk_reset", "lb3_structure_factor_axes",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
@@ -141,6 +141,7 @@ def bind(L):
                                  C.c_double, C.c_double, C.c_int, P]),
         "lb3_destroy": (None, [P]),
         "lb3_init": (C.c_int, [P, C.c_double, C.c_uint64, C.c_double]),
+        "lb3_set_psi": (C.c_int, [P, C.c_int, C.c_double, C.c_double]),
         "lb3_set_replica": (C.c_int, [P, C.c_uint32]),
         "lb3_set_strip": (C.c_int, [P, C.c_int]),
         "lb3_step": (C.c_int, [P, C.c_int]),

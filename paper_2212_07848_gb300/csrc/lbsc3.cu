@@ -93,9 +93,9 @@ template <typename T> struct K3 {
     T *__restrict__ dst;
     T *__restrict__ drho_out;
     int *__restrict__ flag;
-    int nx, ny, nz, strip_z, noise;
+    int nx, ny, nz, strip_z, noise, psi_kind;
     uint32_t step, replica;
-    T rho0, force_pref, psi_c, psi0, gamma, hsrc;
+    T rho0, force_pref, psi_c, psi_b, psi0, gamma, hsrc;
     T amp[19];     // modes 4..18 used
     uint32_t rk[20];
 };
@@ -117,11 +117,6 @@ __device__ __forceinline__ T sum19(const T g[19]) {
 #pragma unroll
     for (int p = 0; p < 9; ++p) s += g[2 * p + 1] + g[2 * p + 2];
     return s;
-}
-
-template <typename T>
-__device__ __forceinline__ T dpsi3(T drho, T psi_c) {
-    return -psi_c * dev_expm1(-drho);
 }
 
 // Collision of one site (moment space), Eq. (12) in 3D.
@@ -250,7 +245,7 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
         {
             T g[19];
             pull3(p.src, plane, xo, yo, zo, g);
-            s_psi[it & 3][ty][tx] = dpsi3<T>(sum19(g), p.psi_c);
+            s_psi[it & 3][ty][tx] = delta_psi<T>(sum19(g), p.psi_kind, p.rho0, p.psi_c, p.psi_b);
         }
         __syncthreads();
         if (it >= 2 && interior) {
@@ -464,6 +459,8 @@ using namespace lbsc;
 struct lb3_ctx {
     int nx = 0, ny = 0, nz = 0, precision = 0, dev = 0;
     double G = 0, tau = 1, kT = 0, rho0 = 0;
+    int psi_kind = LB_PSI_EXP;
+    double psi_p1 = 0, psi_p2 = 0;
     size_t n = 0, esize = 4;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -510,8 +507,16 @@ K3<T> params3(const lb3_ctx *h, bool sample) {
     k.replica = h->replica;
     k.rho0 = (T)h->rho0;
     k.force_pref = (T)(-h->G / 3.0);
-    k.psi_c = (T)exp(-h->rho0);
-    k.psi0 = (T)(-expm1(-h->rho0));
+    k.psi_kind = h->psi_kind;
+    double psi0;
+    switch (h->psi_kind) {
+    case LB_PSI_CRITICAL: psi0 = sqrt(h->psi_p1 * h->psi_p2) * exp(1.0 - h->psi_p2 / h->rho0); break;
+    case LB_PSI_AEXP: psi0 = h->psi_p1 * exp(-h->psi_p2 / h->rho0); break;
+    default: psi0 = -expm1(-h->rho0);
+    }
+    k.psi0 = (T)psi0;
+    k.psi_c = (T)(h->psi_kind == LB_PSI_EXP ? exp(-h->rho0) : psi0);
+    k.psi_b = (T)(h->psi_kind == LB_PSI_EXP ? 0.0 : h->psi_p2);
     const double gam = 1.0 - 1.0 / h->tau;
     k.gamma = (T)gam;
     k.hsrc = (T)(0.5 * (1.0 + gam));
@@ -653,6 +658,15 @@ int lb3_init(lb3_ctx *h, double rho0, uint64_t seed, double init_amp) {
         h->sk_count = 0;
     }
     h->inited = true;
+    return LB_OK;
+}
+
+int lb3_set_psi(lb3_ctx *h, int psi_kind, double p1, double p2) {
+    if (!h || psi_kind < LB_PSI_EXP || psi_kind > LB_PSI_AEXP) return LB_ERR_ARG;
+    if (psi_kind != LB_PSI_EXP && !(p1 > 0.0 && p2 > 0.0)) return LB_ERR_ARG;
+    h->psi_kind = psi_kind;
+    h->psi_p1 = p1;
+    h->psi_p2 = p2;
     return LB_OK;
 }
 

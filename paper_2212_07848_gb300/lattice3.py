@@ -10,9 +10,11 @@ from . import abi
 class Lattice3:
     """Fluctuating Shan-Chen D3Q19 lattice: nx (multiple of 32), ny (multiple
     of 8), nz (>= 3), G (< 0 attractive), tau (> 1/2), kT (>= 0), precision
-    "fp32" or "fp64", stream (an int cudaStream_t or None)."""
+    "fp32" or "fp64", stream (an int cudaStream_t or None), pseudopotential
+    psi_kind with psi_p1, psi_p2 as for the 2D lattice."""
 
-    def __init__(self, nx, ny, nz, G, tau=1.0, kT=0.0, precision="fp32", stream=None):
+    def __init__(self, nx, ny, nz, G, tau=1.0, kT=0.0, precision="fp32", stream=None,
+                 psi_kind=0, psi_p1=0.0, psi_p2=0.0):
         L = abi.load()
         self.nx, self.ny, self.nz = nx, ny, nz
         h = C.c_void_p()
@@ -22,6 +24,8 @@ class Lattice3:
         if rc != 0:
             raise abi.LbError(rc, "lb3_create")
         self._h = h
+        if psi_kind:
+            self._ck(L.lb3_set_psi(h, psi_kind, psi_p1, psi_p2), "lb3_set_psi")
 
     def close(self):
         if getattr(self, "_h", None):

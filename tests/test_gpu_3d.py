@@ -12,14 +12,17 @@ from pairs import LN2, max_rel
 pytestmark = pytest.mark.gpu
 
 
-def _pair(nx, ny, nz, G, tau, kT, precision, rho0, seed, amp, replica=0, strip=None):
+def _pair(nx, ny, nz, G, tau, kT, precision, rho0, seed, amp, replica=0, strip=None, kind=0,
+          p1=0.0, p2=0.0):
     from paper_2212_07848_gb300.lattice3 import Lattice3
-    g = Lattice3(nx, ny, nz, G, tau, kT, precision=precision)
+    g = Lattice3(nx, ny, nz, G, tau, kT, precision=precision, psi_kind=kind, psi_p1=p1,
+                 psi_p2=p2)
     if strip:
         g.set_strip(strip)
     g.set_replica(replica)
     g.init(rho0, seed, amp)
-    o = O.OracleLattice3(nx, ny, nz, G, tau, kT, replica=replica)
+    o = O.OracleLattice3(nx, ny, nz, G, tau, kT, replica=replica, psi_kind=kind, psi_p1=p1,
+                         psi_p2=p2)
     o.init(rho0, seed, amp)
     return g, o
 
@@ -35,6 +38,18 @@ def test_fp64_matches_oracle(nx, ny, nz, G, tau, kT, rho0, amp, strip, steps):
     o.step(steps)
     assert max_rel(g.populations(), o.populations()) < 1e-12
     assert max_rel(g.density(), o.density()) < 1e-12
+
+
+@pytest.mark.parametrize("kind,p1,p2,rho0", [(1, 5.0 / 12.0, 1.0, 0.5), (2, 1.3, 0.8, 0.9)])
+def test_pseudopotential_kinds_match_oracle(kind, p1, p2, rho0):
+    """Eq. (5) (kind 1, T_hat = 0.8 at G = -3, a stable gas) and a exp(-b/rho)
+    (kind 2), both on stable homogeneous states."""
+    for prec, tol, steps in (("fp64", 1e-12, 150), ("fp32", 1e-4, 100)):
+        g, o = _pair(32, 8, 8, -3.0, 1.0, 1e-5, prec, rho0, 9, 0.01, kind=kind, p1=p1, p2=p2)
+        g.step(steps)
+        o.step(steps)
+        assert max_rel(g.populations(), o.populations()) < tol, prec
+        assert max_rel(g.density(), o.density()) < tol, prec
 
 
 def test_fp32_matches_oracle():
