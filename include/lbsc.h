@@ -400,6 +400,23 @@ int lb_nn_add(const void *a, const void *b, void *y, size_t n, void *stream);
  * nx and ny and scale != 0. */
 int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, float *out,
                        void *stream);
+/* Coarse-grained momentum of the same state: FP32 jx, jy [ny/f][nx/f] = (mean
+ * of sum_i c_i df_i over each f x f block) / scale, the post-collision
+ * momentum of the stored populations.  LB_ERR_ARG as lb_nn_coarse_grain. */
+int lb_nn_coarse_momentum(const float *df, int nx, int ny, int f, double scale, float *jx,
+                          float *jy, void *stream);
+/* One more input channel: out[.][ch] = BF16(src[.]) and, with prev (may be
+ * NULL), out[.][ch + 2] = BF16(src - prev), the layout lb_nn_residual keeps
+ * (value at ch, last increment at ch + 2) when it is given out + ch.  Other
+ * channels are untouched.  LB_ERR_ARG unless ch (and ch + 2 with prev) < c. */
+int lb_nn_expand_channel(const float *src, const float *prev, void *out, int c, int ch, size_t n,
+                         void *stream);
+/* Weighted residual MSE of channel ch: prediction = base + y[.][ch];
+ * *loss += weight * mean((prediction - target)^2); dy (may be NULL) gets
+ * the gradient in channel ch only, every other channel of dy is untouched
+ * (so several channels' losses add up after lb_nn_mse has zeroed the rest). */
+int lb_nn_mse_channel(const void *y, int c, int ch, const float *target, const float *base,
+                      size_t n, double weight, float *loss, void *dy, void *stream);
 /* Residual MSE over n pixels: prediction = base + y[.][0] (FP32 base, BF16 y
  * [n][c]); *loss += mean((prediction - target)^2) (accumulates: zero it first);
  * dy (may be NULL) [n][c] = d loss / d y: 2 (prediction - target) / n on
@@ -433,6 +450,16 @@ int lb_nn_set_conv_path(int path);
 int lb_nn_status(void);
 /* BF16 copy of FP32 values. */
 int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream);
+/* Increment as the divergence of a predicted flux, so that the surrogate
+ * conserves mass locally as the lattice does (the continuity equation behind
+ * Eq. (12)'s conserved density): forward (backward = 0) reads J = (y[.][0],
+ * y[.][1]) from BF16 y [nb][h][w][c] and writes BF16 out [nb][h][w]
+ *   out[i][j] = -(Jx[i][j] - Jx[i][j-1] + Jy[i][j] - Jy[i-1][j])
+ * (periodic wrap); backward (1) reads BF16 d out [nb][h][w] and writes the
+ * adjoint into BF16 dy [nb][h][w][c] (channels 0 and 1; the others 0).
+ * LB_ERR_ARG unless c >= 2 and the sizes are positive. */
+int lb_nn_flux_div(const void *in, void *out, int c, int nb, int h, int w_, int backward,
+                   void *stream);
 
 /* Static message for a status code. */
 const char *lb_strerror(int code);

@@ -75,17 +75,50 @@ def net_forward(x, w, b):
     return y, dict(a1=a1, p1=p1, a2=a2, p2=p2, a3=a3, u3=u3, a4=a4, u4=u4)
 
 
-def net_loss(y, base, target):
-    """Residual MSE: mean over pixels of (base + y[..., 0] - target)^2."""
-    d = base + y[..., 0] - target
-    return float(np.mean(d * d)), d
+def flux_div(y):
+    """Increment as minus the divergence of the flux J = (y[..., 0], y[..., 1])
+    with backward differences on the periodic grid: -(dJx/dx + dJy/dy)."""
+    jx, jy = y[..., 0].astype(np.float64), y[..., 1].astype(np.float64)
+    return -((jx - shift(jx[..., None], 0, -1)[..., 0]) + (jy - shift(jy[..., None], -1, 0)[..., 0]))
 
 
-def net_backward(x, w, acts, d):
+def flux_div_backward(dinc, c):
+    """Adjoint of flux_div: the gradient with respect to y [..][c] (channels 0
+    and 1; the others 0) of sum(dinc * flux_div(y))."""
+    d = dinc[..., None].astype(np.float64)
+    dy = np.zeros(dinc.shape + (c,))
+    dy[..., 0] = -(d - shift(d, 0, 1))[..., 0]
+    dy[..., 1] = -(d - shift(d, 1, 0))[..., 0]
+    return dy
+
+
+def net_loss(y, base, target, flux=False, jweight=None):
+    """Residual MSE: mean over pixels of (base + inc - target)^2 with the
+    increment inc = y[..., 0], or flux_div(y) with `flux`.  With `jweight`
+    (the momentum state) base and target are [3][..] (density, jx, jy) and
+    jweight times the MSE of base[a] + y[..., a + 1] - target[a], a = 1, 2, is
+    added.  Returns (loss, residuals)."""
+    b0, t0 = (base[0], target[0]) if jweight is not None else (base, target)
+    inc = flux_div(y) if flux else y[..., 0]
+    if jweight is None:
+        d = b0 + inc - t0
+        return float(np.mean(d * d)), d
+    d = np.stack([b0 + inc - t0] + [base[a] + y[..., a + 1] - target[a] for a in (1, 2)])
+    return float(np.mean(d[0] ** 2) + jweight * (np.mean(d[1] ** 2) + np.mean(d[2] ** 2))), d
+
+
+def net_backward(x, w, acts, d, flux=False, jweight=None):
     """Parameter gradients of net_loss by reverse-mode differentiation of
     net_forward (chain rule layer by layer).  Returns (dw list, db list)."""
-    dy = np.zeros(d.shape + (w[4].shape[1],))
-    dy[..., 0] = 2.0 * d / d.size
+    d0 = d[0] if jweight is not None else d
+    if flux:
+        dy = flux_div_backward(2.0 * d0 / d0.size, w[4].shape[1])
+    else:
+        dy = np.zeros(d0.shape + (w[4].shape[1],))
+        dy[..., 0] = 2.0 * d0 / d0.size
+    if jweight is not None:
+        for a in (1, 2):
+            dy[..., a + 1] += 2.0 * jweight * d[a] / d[a].size
     dw, db = [None] * 5, [None] * 5
     ins = [x, acts["p1"], acts["p2"], acts["u3"], acts["u4"]]
 

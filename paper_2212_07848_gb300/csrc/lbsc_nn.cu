@@ -403,6 +403,58 @@ __global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int 
     }
 }
 
+// Coarse-grained momentum j = sum_i c_i df_i (D2Q9 order 0:(0,0) 1:(1,0)
+// 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)); the w_i rho0
+// part of the populations carries no momentum.
+__global__ void coarse_mom_kernel(const float *__restrict__ df, int nx, int ny, int f, float scale,
+                                  float *__restrict__ jx_out, float *__restrict__ jy_out) {
+    const int cx = nx / f, cy = ny / f;
+    const size_t plane = (size_t)nx * ny;
+    GRID_STRIDE(i, (size_t)cx * cy) {
+        const int X = (int)(i % cx), Y = (int)(i / cx);
+        float sx = 0.f, sy = 0.f;
+        for (int yy = 0; yy < f; ++yy)
+            for (int xx = 0; xx < f; ++xx) {
+                const size_t site = (size_t)(Y * f + yy) * nx + X * f + xx;
+                const float f1 = df[plane + site], f2 = df[2 * plane + site];
+                const float f3 = df[3 * plane + site], f4 = df[4 * plane + site];
+                const float f5 = df[5 * plane + site], f6 = df[6 * plane + site];
+                const float f7 = df[7 * plane + site], f8 = df[8 * plane + site];
+                sx += (f1 - f3) + (f5 - f7) + (f8 - f6);
+                sy += (f2 - f4) + (f5 - f7) + (f6 - f8);
+            }
+        jx_out[i] = sx / (f * f) / scale;
+        jy_out[i] = sy / (f * f) / scale;
+    }
+}
+
+// One more channel of a network input: out[.][ch] = BF16(src), and with
+// prev out[.][ch + 2] = BF16(src - prev) (the layout lb_nn_residual keeps).
+__global__ void expand_ch_kernel(const float *__restrict__ src, const float *__restrict__ prev,
+                                 bf16 *__restrict__ out, int C, int ch, size_t n) {
+    GRID_STRIDE(i, n) {
+        out[i * C + ch] = __float2bfloat16(src[i]);
+        if (prev) out[i * C + ch + 2] = __float2bfloat16(src[i] - prev[i]);
+    }
+}
+
+// Weighted residual MSE of one output channel: prediction = base + y[.][ch],
+// loss += weight * mean((prediction - target)^2), dy[.][ch] = its gradient
+// (no other channel of dy is touched).
+__global__ void mse_ch_kernel(const bf16 *__restrict__ y, int C, int ch,
+                              const float *__restrict__ tgt, const float *__restrict__ base,
+                              size_t n, float weight, float *__restrict__ loss,
+                              bf16 *__restrict__ dy) {
+    float s = 0.f;
+    GRID_STRIDE(i, n) {
+        const float d = base[i] + __bfloat162float(y[i * C + ch]) - tgt[i];
+        s += d * d;
+        if (dy) dy[i * C + ch] = __float2bfloat16(2.f * weight * d / (float)n);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, weight * s / (float)n);
+}
+
 // Residual MSE: prediction = base + y[.][0] (FP32 base, BF16 increment),
 // loss += mean((prediction - target)^2), dy = d loss / d y (channel 0; 0 elsewhere).
 __global__ void mse_kernel(const bf16 *__restrict__ y, int C, const float *__restrict__ tgt,
@@ -495,6 +547,44 @@ __global__ void expand_kernel(const float *__restrict__ src, const float *__rest
         if (C > 1) o[1] = __float2bfloat16(gfeat);
         if (C > 2) o[2] = __float2bfloat16(prev ? src[i] - prev[i] : 0.f);
         for (int c = 3; c < C; ++c) o[c] = __float2bfloat16(0.f);
+    }
+}
+
+// Increment as the divergence of a flux: J = (y[..][0], y[..][1]) on the
+// pixels of [nb][h][w], backward differences with periodic wrap,
+//   inc[b][i][j] = -(Jx[i][j] - Jx[i][j-1] + Jy[i][j] - Jy[i-1][j]),
+// so every increment conserves the field's mass pixel by pixel (a sum over
+// the periodic image telescopes to zero).
+__global__ void flux_div_kernel(const bf16 *__restrict__ y, int C, bf16 *__restrict__ inc, int H,
+                                int W, size_t n) {
+    GRID_STRIDE(p, n) {
+        const int j = (int)(p % W);
+        const size_t row = p / W;
+        const int i = (int)(row % H);
+        const size_t img = (row - i) * W;
+        const size_t pxm = img + (size_t)i * W + (j == 0 ? W - 1 : j - 1);
+        const size_t pym = img + (size_t)(i == 0 ? H - 1 : i - 1) * W + j;
+        const float jx = __bfloat162float(y[p * C]), jxm = __bfloat162float(y[pxm * C]);
+        const float jy = __bfloat162float(y[p * C + 1]), jym = __bfloat162float(y[pym * C + 1]);
+        inc[p] = __float2bfloat16(-((jx - jxm) + (jy - jym)));
+    }
+}
+// Its adjoint: dy[..][0] = -(dinc[i][j] - dinc[i][j+1]),
+// dy[..][1] = -(dinc[i][j] - dinc[i+1][j]), the other channels 0.
+__global__ void flux_div_bwd_kernel(const bf16 *__restrict__ dinc, bf16 *__restrict__ dy, int C,
+                                    int H, int W, size_t n) {
+    GRID_STRIDE(p, n) {
+        const int j = (int)(p % W);
+        const size_t row = p / W;
+        const int i = (int)(row % H);
+        const size_t img = (row - i) * W;
+        const size_t pxp = img + (size_t)i * W + (j == W - 1 ? 0 : j + 1);
+        const size_t pyp = img + (size_t)(i == H - 1 ? 0 : i + 1) * W + j;
+        const float d = __bfloat162float(dinc[p]);
+        bf16 *o = dy + p * C;
+        o[0] = __float2bfloat16(-(d - __bfloat162float(dinc[pxp])));
+        o[1] = __float2bfloat16(-(d - __bfloat162float(dinc[pyp])));
+        for (int c = 2; c < C; ++c) o[c] = __float2bfloat16(0.f);
     }
 }
 
@@ -628,6 +718,30 @@ int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, flo
     NN_RET();
 }
 
+int lb_nn_coarse_momentum(const float *df, int nx, int ny, int f, double scale, float *jx,
+                          float *jy, void *stream) {
+    if (!df || !jx || !jy || f < 1 || nx % f || ny % f || !(scale != 0.0)) return LB_ERR_ARG;
+    coarse_mom_kernel<<<blocks_for((size_t)(nx / f) * (ny / f)), 256, 0, (cudaStream_t)stream>>>(
+        df, nx, ny, f, (float)scale, jx, jy);
+    NN_RET();
+}
+
+int lb_nn_expand_channel(const float *src, const float *prev, void *out, int c, int ch, size_t n,
+                         void *stream) {
+    if (!src || !out || ch < 0 || ch >= c || (prev && ch + 2 >= c)) return LB_ERR_ARG;
+    expand_ch_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(src, prev, (bf16 *)out, c,
+                                                                      ch, n);
+    NN_RET();
+}
+
+int lb_nn_mse_channel(const void *y, int c, int ch, const float *target, const float *base,
+                      size_t n, double weight, float *loss, void *dy, void *stream) {
+    if (!y || !target || !base || !loss || ch < 0 || ch >= c) return LB_ERR_ARG;
+    mse_ch_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)y, c, ch, target, base, n, (float)weight, loss, (bf16 *)dy);
+    NN_RET();
+}
+
 int lb_nn_mse(const void *y, int c, const float *target, const float *base, size_t n, float *loss,
               void *dy, void *stream) {
     if (!y || !target || !base || !loss || c < 1) return LB_ERR_ARG;
@@ -666,6 +780,19 @@ int lb_nn_expand(const float *src, const float *prev, double gfeat, void *out, i
     if (!src || !out || c < 1) return LB_ERR_ARG;
     expand_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(src, prev, (float)gfeat,
                                                                    (bf16 *)out, c, n);
+    NN_RET();
+}
+
+int lb_nn_flux_div(const void *in, void *out, int c, int nb, int h, int w, int backward,
+                   void *stream) {
+    if (!in || !out || c < 2 || nb < 1 || h < 1 || w < 1) return LB_ERR_ARG;
+    const size_t n = (size_t)nb * h * w;
+    if (!backward)
+        flux_div_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+            (const bf16 *)in, c, (bf16 *)out, h, w, n);
+    else
+        flux_div_bwd_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+            (const bf16 *)in, (bf16 *)out, c, h, w, n);
     NN_RET();
 }
 

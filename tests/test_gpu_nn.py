@@ -211,3 +211,82 @@ def test_coarse_expand_mse_residual():
     assert abs(float(mean[0].item()) - mu) < 1e-6 * max(1.0, abs(mu)) + 1e-7
     assert abs(float(state2.double().sum() - base.double().sum())) < 1e-4
     assert np.abs(state2.cpu().numpy() - (base.cpu().numpy() + _np(y)[:, 0] - mu)).max() < 1e-6
+
+
+def test_flux_divergence_forward_and_adjoint():
+    """lb_nn_flux_div against the CPU reference on a ragged 3 x 40 x 24 x 16
+    batch: forward to the BF16 rounding of its output, backward likewise,
+    channels beyond the flux exactly 0."""
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    nb, h, w, c = 3, 40, 24, 16
+    y = _bf((nb, h, w, c), seed=51)
+    inc = torch.empty((nb, h, w), dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_flux_div(_p(y), _p(inc), c, nb, h, w, 0, None) == 0
+    d = _bf((nb, h, w), seed=52)
+    dy = torch.full((nb, h, w, c), 7.0, dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_flux_div(_p(d), _p(dy), c, nb, h, w, 1, None) == 0
+    assert L.lb_nn_flux_div(_p(y), _p(inc), 1, nb, h, w, 0, None) == -1
+    torch.cuda.synchronize()
+    _close_bf16(_np(inc), R.flux_div(_np(y)))
+    ref = R.flux_div_backward(_np(d), c)
+    _close_bf16(_np(dy)[..., :2], ref[..., :2])
+    assert not _np(dy)[..., 2:].any()
+
+
+def test_momentum_state_kernels():
+    """lb_nn_coarse_momentum against block means of sum_i c_i df_i, and the
+    channel forms of expand, MSE and the residual update (through a
+    channel-offset pointer) that carry the momentum state."""
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    nx, ny, f = 96, 64, 4
+    df = torch.randn((9, ny, nx), device="cuda") * 0.01
+    jx = torch.empty((ny // f, nx // f), device="cuda")
+    jy = torch.empty_like(jx)
+    assert L.lb_nn_coarse_momentum(_p(df), nx, ny, f, 0.25, _p(jx), _p(jy), None) == 0
+    assert L.lb_nn_coarse_momentum(_p(df), nx, ny, 5, 0.25, _p(jx), _p(jy), None) == abi.LB_ERR_ARG
+    c = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)])
+    d = df.cpu().double().numpy()
+    for a, got in ((0, jx), (1, jy)):
+        j = np.tensordot(c[:, a].astype(float), d, axes=1)
+        ref = j.reshape(ny // f, f, nx // f, f).mean(axis=(1, 3)) / 0.25
+        torch.cuda.synchronize()
+        assert np.abs(got.cpu().numpy() - ref).max() < 1e-5 * np.abs(ref).max()
+    n = jx.numel()
+    x = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda")
+    prev = jx * 0.5
+    assert L.lb_nn_expand_channel(_p(jx), _p(prev), _p(x), 16, 3, n, None) == 0
+    assert L.lb_nn_expand_channel(_p(jy), None, _p(x), 16, 4, n, None) == 0
+    assert L.lb_nn_expand_channel(_p(jy), _p(prev), _p(x), 16, 14, n, None) == abi.LB_ERR_ARG
+    torch.cuda.synchronize()
+    xe = _np(x)
+    assert np.array_equal(xe[:, 3], jx.to(torch.bfloat16).float().cpu().numpy().ravel())
+    assert np.array_equal(xe[:, 5], (jx - prev).to(torch.bfloat16).float().cpu().numpy().ravel())
+    assert np.array_equal(xe[:, 4], jy.to(torch.bfloat16).float().cpu().numpy().ravel())
+    assert np.all(xe[:, [0, 1, 2, 6]] == 0) and np.all(xe[:, 7:] == 0)
+    y = _bf((n, 16), 0.1, seed=19)
+    base = jx.flatten().clone()
+    tgt = base + 0.05 * torch.randn(n, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    dy = torch.full((n, 16), 3.0, dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_mse_channel(_p(y), 16, 2, _p(tgt), _p(base), n, 0.5, _p(loss), _p(dy),
+                               None) == 0
+    torch.cuda.synchronize()
+    e = base.cpu().double().numpy() + _np(y)[:, 2] - tgt.cpu().double().numpy()
+    assert abs(float(loss.item()) - 0.5 * np.mean(e * e)) < 1e-5 * np.mean(e * e)
+    ge = _np(dy)
+    assert np.abs(ge[:, 2] - e / n).max() < 1e-2 * np.abs(e / n).max()
+    assert np.all(ge[:, [0, 1]] == 3.0) and np.all(ge[:, 3:] == 3.0)     # untouched
+    # residual on channel 2 of y into channel 3 of x (increment lands in 5)
+    state = base.clone()
+    yc = C.c_void_p(y.data_ptr() + 2 * 2)
+    xc = C.c_void_p(x.data_ptr() + 2 * 3)
+    assert L.lb_nn_residual(_p(state), yc, 16, xc, 16, n, None, None) == 0
+    torch.cuda.synchronize()
+    sref = base.cpu().numpy() + _np(y)[:, 2]
+    assert np.abs(state.cpu().numpy() - sref).max() < 1e-6
+    xr = _np(x)
+    assert np.array_equal(xr[:, 3], state.to(torch.bfloat16).float().cpu().numpy())
+    assert np.array_equal(xr[:, 5], _np(y)[:, 2])
+    assert np.array_equal(xr[:, 4], xe[:, 4])

@@ -4,6 +4,7 @@ gradients as the adjoints of the forward map, pooling and upsampling as
 mutual adjoints, and the whole-network backward pass against central finite
 differences of the loss."""
 import numpy as np
+import pytest
 
 from oracle import surrogate_ref as R
 
@@ -51,11 +52,15 @@ def _net(seed, n=8):
     return x, w, b, base, tgt
 
 
-def test_network_backward_matches_finite_differences():
+@pytest.mark.parametrize("flux,jw", [(False, None), (True, None), (True, 0.7)])
+def test_network_backward_matches_finite_differences(flux, jw):
     x, w, b, base, tgt = _net(30)
+    if jw is not None:                       # density, jx, jy state
+        base = np.stack([base, _rand(base.shape, 23), _rand(base.shape, 24)])
+        tgt = np.stack([tgt, _rand(tgt.shape, 25), _rand(tgt.shape, 26)])
     y, acts = R.net_forward(x, w, b)
-    _, d = R.net_loss(y, base, tgt)
-    dw, db = R.net_backward(x, w, acts, d)
+    _, d = R.net_loss(y, base, tgt, flux, jw)
+    dw, db = R.net_backward(x, w, acts, d, flux, jw)
     rng = np.random.default_rng(0)
     h = 1e-5
     for i in range(5):
@@ -63,18 +68,41 @@ def test_network_backward_matches_finite_differences():
             idx = tuple(int(rng.integers(s)) for s in w[i].shape)
             old = w[i][idx]
             w[i][idx] = old + h
-            lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+            lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt, flux, jw)
             w[i][idx] = old - h
-            lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+            lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt, flux, jw)
             w[i][idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - dw[i][idx]) <= 1e-4 * abs(fd) + 1e-9, (i, idx, fd, dw[i][idx])
         j = int(rng.integers(b[i].size))
         old = b[i][j]
         b[i][j] = old + h
-        lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt, flux, jw)
         b[i][j] = old - h
-        lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt, flux, jw)
         b[i][j] = old
         fd = (lp - lm) / (2 * h)
         assert abs(fd - db[i][j]) <= 1e-4 * abs(fd) + 1e-9, (i, j, fd, db[i][j])
+
+
+def test_flux_divergence_definition_conservation_and_adjoint():
+    """flux_div against its definition written as loops on a 3 x 5 grid, the
+    telescoping sum (every increment has zero mean per image), zero increment
+    for a uniform flux, and the adjoint identity of its backward."""
+    y = _rand((2, 3, 5, 4), 41)
+    inc = R.flux_div(y)
+    H, W = 3, 5
+    for b in range(2):
+        for i in range(H):
+            for j in range(W):
+                ref = -((y[b, i, j, 0] - y[b, i, (j - 1) % W, 0]) +
+                        (y[b, i, j, 1] - y[b, (i - 1) % H, j, 1]))
+                assert abs(inc[b, i, j] - ref) < 1e-14
+    assert np.abs(inc.sum(axis=(1, 2))).max() < 1e-13
+    u = np.zeros((1, 3, 5, 4))
+    u[..., 0], u[..., 1] = 0.7, -1.3
+    assert np.abs(R.flux_div(u)).max() == 0.0
+    d = _rand((2, 3, 5), 42)
+    lhs = np.sum(inc * d)
+    rhs = np.sum(y * R.flux_div_backward(d, 4))
+    assert abs(lhs - rhs) < 1e-12
