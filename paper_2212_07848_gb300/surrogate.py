@@ -9,9 +9,16 @@ Network (NHWC BF16 activations, FP32 master weights, periodic boundaries):
     a2 = relu(conv(pool(a1), 32 -> 64))     at N/2
     a3 = relu(conv(pool(a2), 64 -> 128))    at N/4
     a4 = relu(conv(up(a3), 128 -> 64))      at N/2
-    y  = conv(up(a4 + a2), 64 -> 16)        at N; prediction = x[..., 0] + y[..., 0]
+    y  = conv(up(a4 + a2), 64 -> 16)        at N
+    prediction = x[..., 0] + inc, inc = y[..., 0], or in the flux form
+    inc = -div(y[..., 0], y[..., 1]) (the increment conserves mass locally as
+    the lattice does, so rollout errors cannot pile up at long wavelengths)
 Input channel 0 is the coarse density deviation rho - rho0, channel 1 the
-coupling feature (G + 4.8) / 0.4, the rest zero.  Every operation is a
+coupling feature (G + 4.8) / 0.4, channel 2 the last density increment; with
+`momentum` the coarse momentum (jx, jy) / J_SCALE is state too: input
+channels 3, 4 (and its last increments 5, 6), output channels 2, 3 its
+increments, so the network sees the flow that carries mass between domains.
+The other channels are zero.  Every operation is a
 kernel of liblbsc.so (tensor-core convolutions, elementwise pieces, Adam);
 torch only provides device memory.
 """
@@ -27,8 +34,16 @@ CIN = 16
 LAYERS = [(16, 32), (32, 64), (64, 128), (128, 64), (64, 16)]   # (cin, cout)
 
 
+J_SCALE = 0.01     # coarse momentum is stored and fed as j / J_SCALE
+
+
 def _p(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _pc(t, ch):
+    """Pointer to channel ch of a BF16 NHWC tensor (its first pixel)."""
+    return C.c_void_p(t.data_ptr() + 2 * ch)
 
 
 def _check(rc, what):
@@ -41,10 +56,11 @@ def gfeat(G):
 
 
 class SurrogateNet:
-    def __init__(self, n, batch, seed=0, stream=None):
+    def __init__(self, n, batch, seed=0, stream=None, flux=False, momentum=False, jweight=1.0):
         import torch
         self.torch = torch
-        self.n, self.batch = n, batch
+        self.n, self.batch, self.flux = n, batch, flux
+        self.momentum, self.jweight = momentum, jweight
         self.L = abi.load()
         self.s = stream
         g = torch.Generator(device="cpu").manual_seed(seed)
@@ -73,6 +89,7 @@ class SurrogateNet:
         self.a1, self.p1, self.a2, self.p2 = z(n, 32), z(n // 2, 32), z(n // 2, 64), z(n // 4, 64)
         self.a3, self.u3, self.a4, self.s4 = z(n // 4, 128), z(n // 2, 128), z(n // 2, 64), z(n // 2, 64)
         self.u4, self.y = z(n, 64), z(n, 16)
+        self.inc, self.dinc = (z(n, 1), z(n, 1)) if self.flux else (None, None)
         # gradients
         self.dy, self.du4, self.ds4, self.dz4 = z(n, 16), z(n, 64), z(n // 2, 64), z(n // 2, 64)
         self.du3, self.da3, self.dz3, self.dp2 = z(n // 2, 128), z(n // 4, 128), z(n // 4, 128), z(n // 4, 64)
@@ -102,7 +119,18 @@ class SurrogateNet:
         _check(L.lb_nn_add(_p(self.a4), _p(self.a2), _p(self.s4), self.s4.numel(), self.s), "add")
         _check(L.lb_nn_up2(_p(self.s4), _p(self.u4), nb, n // 2, n // 2, 64, 0, self.s), "up")
         self._conv(self.u4, 4, self.y, 0, n)
+        if self.flux:
+            _check(L.lb_nn_flux_div(_p(self.y), _p(self.inc), 16, nb, n, n, 0, self.s), "flux")
         return self.y
+
+    @property
+    def out(self):
+        """The density increment of the last forward: [nb][n][n][out_c], channel 0."""
+        return self.inc if self.flux else self.y
+
+    @property
+    def out_c(self):
+        return 1 if self.flux else 16
 
     def backward(self, x):
         """Accumulate parameter gradients from self.dy (dL/dy)."""
@@ -146,21 +174,38 @@ class SurrogateNet:
                                      self.s), "adam")
 
     def loss_and_grad(self, x, target, base, grad=True):
-        """MSE of the residual prediction base + y[..., 0] against the FP32
-        target; fills self.dy when `grad`.  Returns the loss as a device tensor."""
+        """MSE of the residual prediction base + increment against the FP32
+        target; fills self.dy when `grad` (through the flux divergence's
+        adjoint in the flux form).  With `momentum`, target and base are
+        [3][nb][n][n] (density, jx, jy) and the momentum MSE of output channels
+        2 and 3, weighted by jweight, is added.  Returns the loss as a device
+        tensor."""
         loss = self.torch.zeros(1, device="cuda")
-        npx = self.nb * self.n * self.n
-        _check(self.L.lb_nn_mse(_p(self.y), 16, _p(target), _p(base), npx, _p(loss),
-                                _p(self.dy) if grad else None, self.s), "mse")
+        n, nb = self.n, self.nb
+        npx = nb * n * n
+        t0, b0 = (target[0], base[0]) if self.momentum else (target, base)
+        d_out = self.dinc if self.flux else self.dy
+        _check(self.L.lb_nn_mse(_p(self.out), self.out_c, _p(t0), _p(b0), npx, _p(loss),
+                                _p(d_out) if grad else None, self.s), "mse")
+        if grad and self.flux:
+            _check(self.L.lb_nn_flux_div(_p(self.dinc), _p(self.dy), 16, nb, n, n, 1, self.s),
+                   "flux backward")
+        if self.momentum:
+            for a in (1, 2):
+                _check(self.L.lb_nn_mse_channel(_p(self.y), 16, a + 1, _p(target[a]), _p(base[a]),
+                                                npx, self.jweight, _p(loss),
+                                                _p(self.dy) if grad else None, self.s), "mse j")
         return loss
 
 
 def generate(n_traj, size, steps, stride, G_range=(-5.2, -4.4), coarse=4, kT=1e-6, seed0=1000,
-             rho0=math.log(2.0), stencil=4):
+             rho0=math.log(2.0), stencil=4, momentum=False):
     """Quench trajectories of the lattice solver from a homogeneous density
     rho0 with thermal noise, coarse-grained every `stride` steps.  Returns
-    (frames FP32 [n_traj][steps // stride + 1][size/coarse][size/coarse] of
-    rho - rho0, the couplings G, seconds spent)."""
+    (frames, the couplings G, seconds spent): frames FP32
+    [n_traj][steps // stride + 1][size/coarse][size/coarse] of rho - rho0, or
+    with `momentum` [n_traj][nf][3][m][m] holding rho - rho0, jx / J_SCALE and
+    jy / J_SCALE."""
     import torch
 
     from .lattice import Lattice
@@ -169,18 +214,23 @@ def generate(n_traj, size, steps, stride, G_range=(-5.2, -4.4), coarse=4, kT=1e-
     Gs = rng.uniform(G_range[0], G_range[1], n_traj)
     nf = steps // stride + 1
     m = size // coarse
-    frames = torch.empty((n_traj, nf, m, m), dtype=torch.float32, device="cuda")
+    shape = (n_traj, nf, 3, m, m) if momentum else (n_traj, nf, m, m)
+    frames = torch.empty(shape, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(n_traj):
         lat = Lattice(size, size, float(Gs[k]), 1.0, kT, stencil=stencil)
         lat.init(rho0, seed0 + k, 0.0)
+        df = C.c_void_p(lat.device_ptr(abi.LB_PTR_POPULATIONS))
+        st = C.c_void_p(lat.stream())
         for f in range(nf):
             if f:
                 lat.step(stride)
-            _check(L.lb_nn_coarse_grain(C.c_void_p(lat.device_ptr(abi.LB_PTR_POPULATIONS)), size,
-                                        size, coarse, 1.0, _p(frames[k, f]),
-                                        C.c_void_p(lat.stream())), "coarse")
+            rho = frames[k, f, 0] if momentum else frames[k, f]
+            _check(L.lb_nn_coarse_grain(df, size, size, coarse, 1.0, _p(rho), st), "coarse")
+            if momentum:
+                _check(L.lb_nn_coarse_momentum(df, size, size, coarse, J_SCALE, _p(frames[k, f, 1]),
+                                               _p(frames[k, f, 2]), st), "coarse momentum")
         lat.sync()
         lat.close()
     torch.cuda.synchronize()
@@ -192,6 +242,32 @@ def expand(L, field, G, out, prev=None, stream=None):
     the field, the coupling feature and (with `prev`) the field's last increment."""
     _check(L.lb_nn_expand(_p(field), _p(prev), gfeat(G), _p(out), CIN, field.numel(), stream),
            "expand")
+
+
+def expand_state(L, frame, G, out, prev=None, stream=None):
+    """Network input from one frame: [m][m] (density only) or [3][m][m]
+    (density, jx, jy: momentum in channels 3, 4 and its last increment in 5, 6)."""
+    if frame.dim() == 2:
+        return expand(L, frame, G, out, prev, stream)
+    expand(L, frame[0], G, out, prev[0] if prev is not None else None, stream)
+    for a in (1, 2):
+        _check(L.lb_nn_expand_channel(_p(frame[a]), _p(prev[a]) if prev is not None else None,
+                                      _p(out), CIN, a + 2, frame[a].numel(), stream), "expand j")
+
+
+def advance(net, state, x, npx, mean=None):
+    """Apply the network's last output to the FP32 state (density [..] or
+    [3][..]) and refresh the matching input channels of x: the density by
+    the increment (projected to zero mean when `mean` is a buffer), the
+    momentum by output channels 2, 3 (likewise; the lattice conserves it)."""
+    L, s = net.L, net.s
+    rho = state[0] if net.momentum else state
+    _check(L.lb_nn_residual(_p(rho), _p(net.out), net.out_c, _p(x), CIN, npx, _p(mean), s),
+           "residual")
+    if net.momentum:
+        for a in (1, 2):
+            _check(L.lb_nn_residual(_p(state[a]), _pc(net.y, a + 1), 16, _pc(x, a + 2), CIN, npx,
+                                    _p(mean), s), "residual j")
 
 
 def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=1, lr_end=None,
@@ -208,9 +284,15 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
     if net.nb != net.batch:
         net._alloc(net.batch)
     nb, m = net.nb, net.n
+    mom = frames.dim() == 5
+    if mom != net.momentum:
+        raise ValueError("frames and network disagree on the momentum state")
     x = torch.empty((nb, m, m, CIN), dtype=torch.bfloat16, device="cuda")
-    base = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
-    tgt = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    shape = (3, nb, m, m) if mom else (nb, m, m)
+    base = torch.empty(shape, dtype=torch.float32, device="cuda")
+    tgt = torch.empty(shape, dtype=torch.float32, device="cuda")
+    bview = (lambda j: base[:, j]) if mom else (lambda j: base[j])
+    tview = (lambda j: tgt[:, j]) if mom else (lambda j: tgt[j])
     rng = np.random.default_rng(seed)
     nf = frames.shape[1]
     losses = []
@@ -220,15 +302,15 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
             k = int(rng.choice(train_ids))
             f = int(rng.integers(max(t_min, 2) if pf else t_min, nf - 1))
             src = f - 1 if pf else f
-            base[j].copy_(frames[k, src])
-            tgt[j].copy_(frames[k, f + 1])
-            expand(L, frames[k, src], Gs[k], x[j], frames[k, src - 1] if src > 0 else None, net.s)
+            bview(j).copy_(frames[k, src])
+            tview(j).copy_(frames[k, f + 1])
+            expand_state(L, frames[k, src], Gs[k], x[j], frames[k, src - 1] if src > 0 else None,
+                         net.s)
         if pf:
             # one stride by the network itself: base becomes its prediction of
-            # frame f, x the matching input (channel 2 = the increment)
+            # frame f, x the matching input (with the increments just applied)
             net.forward(x)
-            _check(L.lb_nn_residual(_p(base), _p(net.y), 16, _p(x), CIN, nb * m * m, None, net.s),
-                   "residual")
+            advance(net, base, x, nb * m * m)
         net.zero_grad()
         net.forward(x)
         loss = net.loss_and_grad(x, tgt, base)
@@ -243,37 +325,38 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
 
 
 def one_step_mse(net, frames, Gs, ids, t_min=1):
-    """Mean one-stride MSE of the surrogate and of persistence (no change) over
-    all consecutive frame pairs of the trajectories `ids`, `net.nb` pairs per
-    forward pass (unused slots of the last pass repeat its last pair)."""
+    """Mean one-stride MSE of the surrogate's density and of persistence (no
+    change) over all consecutive frame pairs of the trajectories `ids`,
+    `net.nb` pairs per forward pass (unused slots of the last pass repeat its
+    last pair)."""
     import torch
     L, nb, m = net.L, net.nb, net.n
+    mom = frames.dim() == 5
     x = torch.empty((nb, m, m, CIN), dtype=torch.bfloat16, device="cuda")
     base = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
     tgt = torch.empty((nb, m, m), dtype=torch.float32, device="cuda")
+    rho = (lambda fr: fr[0]) if mom else (lambda fr: fr)
     pairs = [(k, f) for k in ids for f in range(t_min, frames.shape[1] - 1)]
     s_net, s_id = 0.0, 0.0
     for i in range(0, len(pairs), nb):
         chunk = pairs[i:i + nb]
         chunk = chunk + [chunk[-1]] * (nb - len(chunk))
         for j, (k, f) in enumerate(chunk):
-            base[j].copy_(frames[k, f])
-            tgt[j].copy_(frames[k, f + 1])
-            expand(L, frames[k, f], Gs[k], x[j], frames[k, f - 1] if f > 0 else None, net.s)
+            base[j].copy_(rho(frames[k, f]))
+            tgt[j].copy_(rho(frames[k, f + 1]))
+            expand_state(L, frames[k, f], Gs[k], x[j], frames[k, f - 1] if f > 0 else None, net.s)
         net.forward(x)
-        loss = net.loss_and_grad(x, tgt, base, grad=False)
         used = len(pairs[i:i + nb])
         d2 = ((tgt - base) ** 2).mean(dim=(1, 2))
-        y0 = net.y[..., 0].float()
+        y0 = net.out[..., 0].float()
         e2 = ((base + y0 - tgt) ** 2).mean(dim=(1, 2))
         s_net += float(e2[:used].sum())
         s_id += float(d2[:used].sum())
-        del loss
     return s_net / len(pairs), s_id / len(pairs)
 
 
 class _StrideGraph:
-    """One surrogate stride (network forward + residual update) captured once
+    """One surrogate stride (network forward + state update) captured once
     as a CUDA graph on a private stream, on fixed input/state buffers."""
 
     def __init__(self, net):
@@ -283,7 +366,8 @@ class _StrideGraph:
         self.net = net
         self.stream = torch.cuda.Stream()
         self.x = torch.zeros((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
-        self.state = torch.zeros((m, m), dtype=torch.float32, device="cuda")
+        shape = (3, m, m) if net.momentum else (m, m)
+        self.state = torch.zeros(shape, dtype=torch.float32, device="cuda")
         self.mean = torch.zeros(513, dtype=torch.float32, device="cuda")
         saved = net.s
         net.s = self.stream.cuda_stream
@@ -295,32 +379,33 @@ class _StrideGraph:
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, stream=self.stream):
                 net.forward(self.x)
-                _check(net.L.lb_nn_residual(_p(self.state), _p(net.y), 16, _p(self.x), CIN, m * m,
-                                            _p(self.mean), net.s), "residual")
+                advance(net, self.state, self.x, m * m, self.mean)
         finally:
             net.s = saved
 
     def run(self, frame0, G, strides, prev0, out):
         torch = self.torch
         net = self.net
+        rho = self.state[0] if net.momentum else self.state
         with torch.cuda.stream(self.stream):
             self.stream.wait_stream(torch.cuda.current_stream())
             self.state.copy_(frame0)
-            expand(net.L, self.state, G, self.x, prev0, self.stream.cuda_stream)
+            expand_state(net.L, self.state, G, self.x, prev0, self.stream.cuda_stream)
             for s in range(strides):
                 self.graph.replay()
-                out[s].copy_(self.state)
+                out[s].copy_(rho)
         torch.cuda.current_stream().wait_stream(self.stream)
         return out
 
 
 def rollout(net, frame0, G, strides, prev0=None, graph=True):
-    """Apply the surrogate `strides` times from an FP32 field [m][m] (and the
-    field one stride earlier, for the last-increment input); the state stays
-    FP32 (only the network input is BF16) and each increment is projected to
-    zero mean, so the field's mass is conserved as on the lattice.  Returns the
-    FP32 fields after each stride as one tensor [strides][m][m].  With `graph`
-    each stride replays a CUDA graph captured on the first call."""
+    """Apply the surrogate `strides` times from an FP32 frame ([m][m], or
+    [3][m][m] with momentum) and the frame one stride earlier (for the
+    last-increment inputs); the state stays FP32 (only the network input is
+    BF16) and each increment is projected to zero mean, so the field's mass
+    (and momentum) is conserved as on the lattice.  Returns the FP32 density
+    after each stride as one tensor [strides][m][m].  With `graph` each
+    stride replays a CUDA graph captured on the first call."""
     import torch
     L, m = net.L, net.n
     if net.nb != 1:
@@ -334,12 +419,11 @@ def rollout(net, frame0, G, strides, prev0=None, graph=True):
     x = torch.empty((1, m, m, CIN), dtype=torch.bfloat16, device="cuda")
     mean = torch.zeros(513, dtype=torch.float32, device="cuda")
     state = frame0.clone()
-    expand(L, state, G, x, prev0, net.s)
+    expand_state(L, state, G, x, prev0, net.s)
     for s in range(strides):
         net.forward(x)
-        _check(L.lb_nn_residual(_p(state), _p(net.y), 16, _p(x), CIN, m * m, _p(mean), net.s),
-               "residual")
-        out[s].copy_(state)
+        advance(net, state, x, m * m, mean)
+        out[s].copy_(state[0] if net.momentum else state)
     return out
 
 
@@ -352,10 +436,11 @@ def guarded_rollout(net, frame0, G, strides, prev0=None, mass_tol=1e-3, bound=No
     left its domain after n strides and the caller continues with the solver
     from the last accepted state."""
     out = rollout(net, frame0, G, strides, prev0)
+    rho0 = frame0[0] if frame0.dim() == 3 else frame0
     means = out.mean(dim=(1, 2)).cpu().numpy()
     peaks = out.abs().amax(dim=(1, 2)).cpu().numpy()
-    m0 = float(frame0.mean())
-    lim = bound if bound is not None else max(1.0, 1.5 * float(frame0.abs().max()))
+    m0 = float(rho0.mean())
+    lim = bound if bound is not None else max(1.0, 1.5 * float(rho0.abs().max()))
     ok = (np.abs(means - m0) <= mass_tol) & np.isfinite(means) & (peaks <= lim)
     n = int(np.argmin(ok)) if not ok.all() else strides
     return out[:n], n
@@ -374,7 +459,8 @@ def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
     for k in ids:
         out = rollout(net, frames[k, f0].clone(), float(Gs[k]), nroll,
                       frames[k, f0 - 1] if f0 > 0 else None).cpu().numpy()
-        ref = frames[k, f0 + 1:f0 + 1 + nroll].cpu().numpy()
+        ref = frames[k, f0 + 1:f0 + 1 + nroll]
+        ref = (ref[:, 0] if frames.dim() == 5 else ref).cpu().numpy()
         a = [radial_sk(f) for f in out]
         b = [radial_sk(f) for f in ref]
         Ls.append([v[1] for v in a])
@@ -392,7 +478,7 @@ def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
     return {"L_surrogate": Ls.tolist(), "L_solver": Lr.tolist(),
             "L_mean_max_rel_err": float(np.max(np.abs(Ls - Lr) / Lr)),
             "L_traj_max_rel_err": float(np.max(per)), "Sk_peak_max_rel_err": s_peak,
-            "Sk_l1_rel_err": s_l1}
+            "Sk_l1_rel_err": s_l1, "Sk_surrogate": Ss, "Sk_solver": Sr}
 
 
 def radial_sk(field):

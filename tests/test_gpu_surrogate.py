@@ -19,10 +19,12 @@ def _rel(got, ref):
     return float(np.sqrt(np.mean((got - ref) ** 2)) / (np.sqrt(np.mean(ref ** 2)) + 1e-30))
 
 
-def test_network_gradients_match_reference():
+@pytest.mark.parametrize("flux,mom", [(False, False), (True, False), (True, True)])
+def test_network_gradients_match_reference(flux, mom):
+    """Plain increment, flux form, and flux form with the momentum state."""
     from paper_2212_07848_gb300.surrogate import LAYERS, SurrogateNet
     n, nb = 64, 2
-    net = SurrogateNet(n, nb, seed=3)
+    net = SurrogateNet(n, nb, seed=3, flux=flux, momentum=mom, jweight=0.7)
     g = torch.Generator(device="cpu").manual_seed(4)
     for i in range(len(LAYERS)):                   # a non-trivial output layer and biases
         net.w[i].copy_(torch.randn(net.w[i].shape, generator=g).cuda()
@@ -32,6 +34,17 @@ def test_network_gradients_match_reference():
     x = torch.randn((nb, n, n, 16), generator=g).to(torch.bfloat16).cuda()
     base = torch.randn((nb, n, n), generator=g).cuda()
     tgt = torch.randn((nb, n, n), generator=g).cuda()
+    if flux:
+        # A smooth residual: the flux adjoint differentiates d, and the coarse
+        # layers then sum the derivative over blocks, which for a white-noise d
+        # would cancel down to the BF16 rounding of the intermediate gradients.
+        yy, xx = torch.meshgrid(torch.arange(n), torch.arange(n), indexing="ij")
+        sm = sum(torch.sin(2 * math.pi * (kx * xx + ky * yy) / n + ph)
+                 for kx, ky, ph in ((1, 0, 0.3), (0, 2, 1.1), (1, 1, 2.0), (3, 1, 0.7)))
+        tgt = base - 10.0 * sm.float().cuda()[None]
+    if mom:                                   # density, jx, jy planes
+        base = torch.stack([base] + [torch.randn((nb, n, n), generator=g).cuda() for _ in range(2)])
+        tgt = torch.stack([tgt] + [torch.randn((nb, n, n), generator=g).cuda() for _ in range(2)])
     net.zero_grad()
     net.forward(x)
     loss = net.loss_and_grad(x, tgt, base)
@@ -42,13 +55,19 @@ def test_network_gradients_match_reference():
     b = [t.cpu().numpy().astype(np.float64) for t in net.b]
     xr = x.float().cpu().numpy().astype(np.float64)
     y, acts = R.net_forward(xr, w, b)
-    ref_loss, d = R.net_loss(y, base.cpu().numpy(), tgt.cpu().numpy())
-    dw, db = R.net_backward(xr, w, acts, d)
+    jw = 0.7 if mom else None
+    ref_loss, d = R.net_loss(y, base.cpu().numpy(), tgt.cpu().numpy(), flux, jw)
+    dw, db = R.net_backward(xr, w, acts, d, flux, jw)
     assert _rel(net.y.float().cpu().numpy(), y) < 2e-2
+    if flux:
+        inc = net.out[..., 0].float().cpu().numpy()
+        assert _rel(inc, R.flux_div(net.y.float().cpu().numpy())) < 1e-2
+        assert _rel(inc, R.flux_div(y)) < 5e-2
     assert abs(float(loss.item()) - ref_loss) < 1e-2 * ref_loss
+    tol = 8e-2 if flux else 5e-2        # the flux adjoint differences BF16 gradients
     for i in range(len(LAYERS)):
-        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < 5e-2, i
-        assert _rel(net.db[i].cpu().numpy(), db[i]) < 5e-2, i
+        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < tol, i
+        assert _rel(net.db[i].cpu().numpy(), db[i]) < tol, i
 
 
 @pytest.fixture(scope="module")
