@@ -64,10 +64,13 @@ def test_network_gradients_match_reference(flux, mom):
         assert _rel(inc, R.flux_div(net.y.float().cpu().numpy())) < 1e-2
         assert _rel(inc, R.flux_div(y)) < 5e-2
     assert abs(float(loss.item()) - ref_loss) < 1e-2 * ref_loss
-    tol = 8e-2 if flux else 5e-2        # the flux adjoint differences BF16 gradients
+    # The flux adjoint differences BF16 gradients, and its output sums to zero
+    # over each image, so the bias gradients (pixel sums) are small residues
+    # of cancellation that only the ReLU masks leave: looser bounds there.
+    tol, tol_b = (8e-2, 1.5e-1) if flux else (5e-2, 5e-2)
     for i in range(len(LAYERS)):
         assert _rel(net.dw[i].cpu().numpy(), dw[i]) < tol, i
-        assert _rel(net.db[i].cpu().numpy(), db[i]) < tol, i
+        assert _rel(net.db[i].cpu().numpy(), db[i]) < tol_b, i
 
 
 @pytest.fixture(scope="module")
