@@ -211,7 +211,7 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
             "sizes": "uniform {64,128,256,512}^2, G~U[-4.8,-3.6], rho0=ln2(1+U[-0.1,0.1])"}
 
 
-def surrogate_leg(ntraj=40, ntest=8, size=2048, steps=6000, stride=200, iters=3000, batch=8,
+def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=9000, batch=8,
                   seed=11):
     """Learned surrogate against the solver it stands in for: quench
     trajectories at size^2 (G ~ U[-5.2, -4.4], rho0 = ln2, kT = 1e-6)

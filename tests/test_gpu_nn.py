@@ -142,8 +142,9 @@ def test_pool_up_relu_adam():
     torch.cuda.synchronize()
     assert np.array_equal(_np(m), np.where(_np(a) > 0, _np(a), 0.0))
     n = 513
-    w = torch.randn(n, device="cuda")
-    g = torch.randn(n, device="cuda")
+    gen = torch.Generator(device="cpu").manual_seed(10)
+    w = torch.randn(n, generator=gen).cuda()
+    g = torch.randn(n, generator=gen).cuda()
     mo = torch.zeros(n, device="cuda")
     v = torch.zeros(n, device="cuda")
     wb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
@@ -154,7 +155,8 @@ def test_pool_up_relu_adam():
     mm, vv = 0.1 * gg, 0.001 * gg * gg
     ref = w0 - 1e-3 * (mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8)
     assert np.abs(w.cpu().numpy() - ref).max() < 1e-6
-    assert np.abs(_np(wb) - ref).max() < 1e-2
+    # the BF16 copy rounds to nearest: within half a unit in the last place
+    assert np.all(np.abs(_np(wb) - ref) <= 2.0 ** -9 * np.abs(ref) + 1e-6)
 
 
 def test_coarse_expand_mse_residual():
