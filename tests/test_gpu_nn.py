@@ -155,8 +155,8 @@ def test_pool_up_relu_adam():
     mm, vv = 0.1 * gg, 0.001 * gg * gg
     ref = w0 - 1e-3 * (mm / 0.1) / (np.sqrt(vv / 0.001) + 1e-8)
     assert np.abs(w.cpu().numpy() - ref).max() < 1e-6
-    # the BF16 copy rounds to nearest: within half a unit in the last place
-    assert np.all(np.abs(_np(wb) - ref) <= 2.0 ** -9 * np.abs(ref) + 1e-6)
+    # the BF16 copy rounds to nearest: within half an ulp, at most 2^-8 relative
+    assert np.all(np.abs(_np(wb) - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6)
 
 
 def test_coarse_expand_mse_residual():
