@@ -70,6 +70,13 @@ def test_network_gradients_match_reference(flux, mom):
     tol, tol_b = (8e-2, 1.5e-1) if flux else (5e-2, 5e-2)
     for i in range(len(LAYERS)):
         assert _rel(net.dw[i].cpu().numpy(), dw[i]) < tol, i
+        if flux and i == len(LAYERS) - 1:
+            # exactly 0 in exact arithmetic for the flux channels: bound the
+            # sum of P BF16-rounded dy values by its rounding error
+            dyg = net.dy.float().cpu().numpy().reshape(-1, LAYERS[i][1])
+            bound = 4.0 * np.sqrt(dyg.shape[0]) * 2.0 ** -8 * np.sqrt((dyg ** 2).mean(axis=0))
+            assert np.all(np.abs(net.db[i].cpu().numpy() - db[i]) <= bound + 1e-12)
+            continue
         assert _rel(net.db[i].cpu().numpy(), db[i]) < tol_b, i
 
 
