@@ -71,11 +71,13 @@ def test_network_gradients_match_reference(flux, mom):
     for i in range(len(LAYERS)):
         assert _rel(net.dw[i].cpu().numpy(), dw[i]) < tol, i
         if flux and i == len(LAYERS) - 1:
-            # exactly 0 in exact arithmetic for the flux channels: bound the
-            # sum of P BF16-rounded dy values by its rounding error
+            # exactly 0 in exact arithmetic for the flux channels 0, 1: bound
+            # the sum of P BF16-rounded dy values by its rounding error (the
+            # momentum channels 2, 3 also get 2% of their value)
             dyg = net.dy.float().cpu().numpy().reshape(-1, LAYERS[i][1])
             bound = 4.0 * np.sqrt(dyg.shape[0]) * 2.0 ** -8 * np.sqrt((dyg ** 2).mean(axis=0))
-            assert np.all(np.abs(net.db[i].cpu().numpy() - db[i]) <= bound + 1e-12)
+            err = np.abs(net.db[i].cpu().numpy() - db[i])
+            assert np.all(err <= bound + 2e-2 * np.abs(db[i]) + 1e-12), err
             continue
         assert _rel(net.db[i].cpu().numpy(), db[i]) < tol_b, i
 
