@@ -23,6 +23,8 @@
 
 #include <new>
 
+#include <type_traits>
+
 #include "lbsc.h"
 #include "lbsc_device.cuh"
 #include "lbsc_internal.cuh"
@@ -119,8 +121,20 @@ __device__ __forceinline__ T sum19(const T g[19]) {
     return s;
 }
 
+// 1/rho: FP32 from the reciprocal square root squared (a few ulp); FP64
+// correctly rounded.
+__device__ __forceinline__ float inv3(float rho) {
+    const float r = rsqrtf(rho);
+    return r * r;
+}
+__device__ __forceinline__ double inv3(double rho) { return 1.0 / rho; }
+
 // Collision of one site (moment space), Eq. (12) in 3D.
-template <typename T>
+// UNIT: every relaxation rate is 1 (gamma = 0): the non-conserved moments of
+// the pulled populations are not needed (stress modes become their
+// equilibrium plus source, ghosts zero, before the noise); the result is
+// that of the general path with gamma = 0.
+template <typename T, bool UNIT = false>
 __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const K3<T> &p,
                                          uint32_t site, T f[19]) {
     // pair sums and differences: pair q = velocities 2q+1 (c) and 2q+2 (-c)
@@ -135,7 +149,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
     // m_k = sum over pairs of e_k(c) (s or d): even polynomials use s, odd use d
     T m[19];
 #pragma unroll
-    for (int k = 0; k < 19; ++k) {
+    for (int k = 0; k < (UNIT ? 4 : 19); ++k) {
         const bool odd = (k >= 1 && k <= 3) || (k >= 10 && k <= 15);
         T acc = odd ? T(0) : T(mom3(k, 0)) * s[0];
 #pragma unroll
@@ -146,7 +160,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         m[k] = acc;
     }
     const T rho = p.rho0 + m[0];
-    const T inv = T(1) / rho;
+    const T inv = inv3(rho);
     const T jx = fma(T(0.5), Fx, m[1]), jy = fma(T(0.5), Fy, m[2]), jz = fma(T(0.5), Fz, m[3]);
     const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const T qxx = jx * ux, qyy = jy * uy, qzz = jz * uz;
@@ -160,14 +174,21 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
     ms[1] = m[1] + Fx;
     ms[2] = m[2] + Fy;
     ms[3] = m[3] + Fz;
-    ms[4] = fma(g_, m[4], fma(a, q2, h * (T(2) * p2)));
-    ms[5] = fma(g_, m[5], fma(a, T(3) * qxx - q2, h * (T(6) * pxx - T(2) * p2)));
-    ms[6] = fma(g_, m[6], fma(a, qyy - qzz, h * (T(2) * (pyy - pzz))));
-    ms[7] = fma(g_, m[7], fma(a, qxy, h * fma(ux, Fy, uy * Fx)));
-    ms[8] = fma(g_, m[8], fma(a, qyz, h * fma(uy, Fz, uz * Fy)));
-    ms[9] = fma(g_, m[9], fma(a, qzx, h * fma(uz, Fx, ux * Fz)));
+    ms[4] = fma(a, q2, h * (T(2) * p2));
+    ms[5] = fma(a, T(3) * qxx - q2, h * (T(6) * pxx - T(2) * p2));
+    ms[6] = fma(a, qyy - qzz, h * (T(2) * (pyy - pzz)));
+    ms[7] = fma(a, qxy, h * fma(ux, Fy, uy * Fx));
+    ms[8] = fma(a, qyz, h * fma(uy, Fz, uz * Fy));
+    ms[9] = fma(a, qzx, h * fma(uz, Fx, ux * Fz));
+    if constexpr (UNIT) {
 #pragma unroll
-    for (int k = 10; k < 19; ++k) ms[k] = g_ * m[k];
+        for (int k = 10; k < 19; ++k) ms[k] = T(0);
+    } else {
+#pragma unroll
+        for (int k = 4; k < 10; ++k) ms[k] = fma(g_, m[k], ms[k]);
+#pragma unroll
+        for (int k = 10; k < 19; ++k) ms[k] = g_ * m[k];
+    }
     if (p.noise) {
         const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), p.rk);
         const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), p.rk);
@@ -216,7 +237,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
     }
 }
 
-template <typename T, bool SAMPLE>
+template <typename T, bool SAMPLE, bool UNIT = false>
 __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
     __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
     const int tx = threadIdx.x % kBX3, ty = threadIdx.x / kBX3;
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
             const uint32_t site = ((uint32_t)zc * ny + y) * nx + x;
             T g[19], f[19];
             pull3(p.src, plane, xo, yo, zprev, g);
-            collide3(g, Fx, Fy, Fz, p, site, f);
+            collide3<T, UNIT>(g, Fx, Fy, Fz, p, site, f);
 #pragma unroll
             for (int i = 0; i < 19; ++i) p.dst[(uint32_t)i * plane + site] = f[i];
             if (SAMPLE) p.drho_out[site] = sum19(g);
@@ -530,6 +551,16 @@ template <typename T>
 int step3_once(lb3_ctx *h, bool sample) {
     const K3<T> k = params3<T>(h, sample);
     dim3 grid(h->nx / kTX3, h->ny / kTY3, (h->nz + h->strip_z - 1) / h->strip_z);
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->tau == 1.0) {       // gamma = 0: the unit-relaxation path
+            if (sample)
+                step3_kernel<T, true, true><<<grid, kThreads3, 0, h->stream>>>(k);
+            else
+                step3_kernel<T, false, true><<<grid, kThreads3, 0, h->stream>>>(k);
+            L3_CHECK(cudaGetLastError());
+            return LB_OK;
+        }
+    }
     if (sample)
         step3_kernel<T, true><<<grid, kThreads3, 0, h->stream>>>(k);
     else
