@@ -211,23 +211,45 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         ms[18] = fma(p.amp[18] * rad, c, ms[18]);
     }
     // inverse: delta f_i = w_i sum_k e_ki m*_k / b_k, assembled per pair as
-    // (even part) +- (odd part)
+    // (even part) +- (odd part).  Each part is split so that velocities of the
+    // same family share work: the even part is a sum over the modes whose
+    // polynomial depends on the squares c_a^2 only (the same for every
+    // velocity of a family) plus the cross modes c_a c_b; the odd part is
+    // sum_a c_a P_a with P_a over the modes odd in c_a, whose coefficients
+    // again depend on the squares only.
+    constexpr int kEvenSq[7] = {0, 4, 16, 5, 6, 17, 18};
+    constexpr int kCross[3] = {7, 8, 9};
+    constexpr int kOddAxis[3][3] = {{1, 10, 13}, {2, 11, 14}, {3, 12, 15}};
     T ev[10], od[10];
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
         const int i = q == 0 ? 0 : 2 * q - 1;
-        T e_acc = T(0), o_acc = T(0);
+        const int ci[3] = {cx3(i), cy3(i), cz3(i)};
+        T e_sq = T(0), e_x = T(0);
 #pragma unroll
-        for (int k = 0; k < 19; ++k) {
-            const int e = mom3(k, i);
-            if (e == 0) continue;
-            const bool odd = (k >= 1 && k <= 3) || (k >= 10 && k <= 15);
-            const T coef = T(wq3(i) * e / norm3_lit(k));
-            if (odd) o_acc = fma(coef, ms[k], o_acc);
-            else e_acc = fma(coef, ms[k], e_acc);
+        for (int j = 0; j < 7; ++j) {
+            const int k = kEvenSq[j], e = mom3(k, i);
+            if (e != 0) e_sq = fma(T(wq3(i) * e / norm3_lit(k)), ms[k], e_sq);
         }
-        ev[q] = e_acc;
-        od[q] = o_acc;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = kCross[j], e = mom3(k, i);
+            if (e != 0) e_x = fma(T(wq3(i) * e / norm3_lit(k)), ms[k], e_x);
+        }
+        T o = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (ci[a] == 0) continue;
+            T pa = T(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int k = kOddAxis[a][j], h = mom3(k, i) * ci[a];   // e_k / c_a
+                if (h != 0) pa = fma(T(wq3(i) * h / norm3_lit(k)), ms[k], pa);
+            }
+            o = ci[a] > 0 ? o + pa : o - pa;
+        }
+        ev[q] = e_sq + e_x;
+        od[q] = o;
     }
     f[0] = ev[0];
 #pragma unroll
@@ -236,6 +258,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         f[2 * q + 2] = ev[q + 1] - od[q + 1];
     }
 }
+
 
 template <typename T, bool SAMPLE, bool UNIT = false>
 __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
