@@ -411,6 +411,13 @@ int lb_nn_coarse_momentum(const float *df, int nx, int ny, int f, double scale, 
  * channels are untouched.  LB_ERR_ARG unless ch (and ch + 2 with prev) < c. */
 int lb_nn_expand_channel(const float *src, const float *prev, void *out, int c, int ch, size_t n,
                          void *stream);
+/* Block MSE of the residual d = base + y[.][0] - target over images
+ * [nb][h][w]: *loss += weight * mean over block x block tiles of (tile mean
+ * of d)^2, a measure of the error at wavelengths longer than the tile; dy
+ * (may be NULL) gets its gradient ADDED to channel 0 (call after lb_nn_mse,
+ * which overwrites dy).  LB_ERR_ARG unless block divides h and w. */
+int lb_nn_mse_blocks(const void *y, int c, const float *target, const float *base, int nb, int h,
+                     int w_, int block, double weight, float *loss, void *dy, void *stream);
 /* Weighted residual MSE of channel ch: prediction = base + y[.][ch];
  * *loss += weight * mean((prediction - target)^2); dy (may be NULL) gets
  * the gradient in channel ch only, every other channel of dy is untouched

@@ -403,6 +403,49 @@ __global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int 
     }
 }
 
+// Block MSE: the residual d = base + y[.][0] - target averaged over each
+// B x B block of each image [nb][h][w]; loss += weight * mean over blocks of
+// (block mean)^2 and dy[.][0] += its gradient, 2 weight mean_b / (nblocks B^2),
+// on every pixel of block b.  One CTA per block (blocks are disjoint, so the
+// read-modify-write of dy needs no atomics).
+__global__ void __launch_bounds__(256) mse_block_kernel(const bf16 *__restrict__ y, int C,
+                                                        const float *__restrict__ tgt,
+                                                        const float *__restrict__ base, int H,
+                                                        int W, int B, float weight,
+                                                        float inv_nblocks, float *__restrict__ loss,
+                                                        bf16 *__restrict__ dy) {
+    const int bw = W / B, bh = H / B;
+    const int blk = blockIdx.x;
+    const int img = blk / (bw * bh), r = blk % (bw * bh);
+    const int by = r / bw, bx = r % bw;
+    const size_t img0 = (size_t)img * H * W;
+    const int npx = B * B;
+    float s = 0.f;
+    for (int t = threadIdx.x; t < npx; t += blockDim.x) {
+        const size_t p = img0 + (size_t)(by * B + t / B) * W + bx * B + t % B;
+        s += base[p] + __bfloat162float(y[p * C]) - tgt[p];
+    }
+    __shared__ float red[8];
+    __shared__ float mean_s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+        const float m = a / (float)npx;
+        mean_s = m;
+        atomicAdd(loss, weight * m * m * inv_nblocks);
+    }
+    __syncthreads();
+    if (!dy) return;
+    const float g = 2.f * weight * mean_s * inv_nblocks / (float)npx;
+    for (int t = threadIdx.x; t < npx; t += blockDim.x) {
+        const size_t p = img0 + (size_t)(by * B + t / B) * W + bx * B + t % B;
+        dy[p * C] = __float2bfloat16(__bfloat162float(dy[p * C]) + g);
+    }
+}
+
 // Coarse-grained momentum j = sum_i c_i df_i (D2Q9 order 0:(0,0) 1:(1,0)
 // 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)); the w_i rho0
 // part of the populations carries no momentum.
@@ -715,6 +758,18 @@ int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, flo
     if (!df || !out || f < 1 || nx % f || ny % f || !(scale != 0.0)) return LB_ERR_ARG;
     coarse_kernel<<<blocks_for((size_t)(nx / f) * (ny / f)), 256, 0, (cudaStream_t)stream>>>(
         df, nx, ny, f, (float)scale, out);
+    NN_RET();
+}
+
+int lb_nn_mse_blocks(const void *y, int c, const float *target, const float *base, int nb, int h,
+                     int w, int block, double weight, float *loss, void *dy, void *stream) {
+    if (!y || !target || !base || !loss || c < 1 || nb < 1 || block < 1 || h % block ||
+        w % block)
+        return LB_ERR_ARG;
+    const int nblocks = nb * (h / block) * (w / block);
+    mse_block_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(
+        (const bf16 *)y, c, target, base, h, w, block, (float)weight, 1.f / (float)nblocks, loss,
+        (bf16 *)dy);
     NN_RET();
 }
 

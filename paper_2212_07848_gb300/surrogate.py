@@ -56,11 +56,15 @@ def gfeat(G):
 
 
 class SurrogateNet:
-    def __init__(self, n, batch, seed=0, stream=None, flux=False, momentum=False, jweight=1.0):
+    def __init__(self, n, batch, seed=0, stream=None, flux=False, momentum=False, jweight=1.0,
+                 block_loss=()):
         import torch
         self.torch = torch
         self.n, self.batch, self.flux = n, batch, flux
         self.momentum, self.jweight = momentum, jweight
+        # (block, weight) pairs: the density residual averaged over block x
+        # block tiles enters the loss with that weight (long-wavelength error)
+        self.block_loss = tuple(block_loss)
         self.L = abi.load()
         self.s = stream
         g = torch.Generator(device="cpu").manual_seed(seed)
@@ -187,6 +191,10 @@ class SurrogateNet:
         d_out = self.dinc if self.flux else self.dy
         _check(self.L.lb_nn_mse(_p(self.out), self.out_c, _p(t0), _p(b0), npx, _p(loss),
                                 _p(d_out) if grad else None, self.s), "mse")
+        for blk, wgt in self.block_loss:
+            _check(self.L.lb_nn_mse_blocks(_p(self.out), self.out_c, _p(t0), _p(b0), nb, n, n, blk,
+                                           wgt, _p(loss), _p(d_out) if grad else None, self.s),
+                   "block mse")
         if grad and self.flux:
             _check(self.L.lb_nn_flux_div(_p(self.dinc), _p(self.dy), 16, nb, n, n, 1, self.s),
                    "flux backward")

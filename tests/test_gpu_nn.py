@@ -292,3 +292,31 @@ def test_momentum_state_kernels():
     assert np.array_equal(xr[:, 3], state.to(torch.bfloat16).float().cpu().numpy())
     assert np.array_equal(xr[:, 5], _np(y)[:, 2])
     assert np.array_equal(xr[:, 4], xe[:, 4])
+
+
+def test_block_mse():
+    """lb_nn_mse_blocks against numpy: the loss from 8 x 8 tile means of the
+    residual on a 2 x 32 x 48 batch, and its gradient added to dy."""
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    nb, h, w, c, B = 2, 32, 48, 16, 8
+    n = nb * h * w
+    y = _bf((n, c), 0.1, seed=61)
+    base = torch.randn(n, device="cuda") * 0.1
+    tgt = torch.randn(n, device="cuda") * 0.1
+    loss = torch.zeros(1, device="cuda")
+    dy = torch.full((n, c), 0.5, dtype=torch.bfloat16, device="cuda")
+    assert L.lb_nn_mse_blocks(_p(y), c, _p(tgt), _p(base), nb, h, w, B, 3.0, _p(loss), _p(dy),
+                              None) == 0
+    assert L.lb_nn_mse_blocks(_p(y), c, _p(tgt), _p(base), nb, h, w, 7, 3.0, _p(loss), _p(dy),
+                              None) == abi.LB_ERR_ARG
+    torch.cuda.synchronize()
+    d = (base.cpu().double().numpy() + _np(y)[:, 0] - tgt.cpu().double().numpy())
+    tiles = d.reshape(nb, h // B, B, w // B, B).mean(axis=(2, 4))
+    ref_loss = 3.0 * np.mean(tiles ** 2)
+    assert abs(float(loss.item()) - ref_loss) < 1e-4 * ref_loss
+    g = 2 * 3.0 * tiles / tiles.size / (B * B)
+    gref = 0.5 + np.repeat(np.repeat(g, B, axis=1), B, axis=2).reshape(-1)
+    got = _np(dy)
+    assert np.abs(got[:, 0] - gref).max() <= 2.0 ** -8 * np.abs(gref).max()
+    assert np.all(got[:, 1:] == 0.5)
