@@ -306,6 +306,7 @@ def test_block_mse():
     tgt = torch.randn(n, device="cuda") * 0.1
     loss = torch.zeros(1, device="cuda")
     dy = torch.full((n, c), 0.5, dtype=torch.bfloat16, device="cuda")
+    dy[:, 0] = 0.0
     assert L.lb_nn_mse_blocks(_p(y), c, _p(tgt), _p(base), nb, h, w, B, 3.0, _p(loss), _p(dy),
                               None) == 0
     assert L.lb_nn_mse_blocks(_p(y), c, _p(tgt), _p(base), nb, h, w, 7, 3.0, _p(loss), _p(dy),
@@ -316,7 +317,7 @@ def test_block_mse():
     ref_loss = 3.0 * np.mean(tiles ** 2)
     assert abs(float(loss.item()) - ref_loss) < 1e-4 * ref_loss
     g = 2 * 3.0 * tiles / tiles.size / (B * B)
-    gref = 0.5 + np.repeat(np.repeat(g, B, axis=1), B, axis=2).reshape(-1)
+    gref = np.repeat(np.repeat(g, B, axis=1), B, axis=2).reshape(-1)
     got = _np(dy)
-    assert np.abs(got[:, 0] - gref).max() <= 2.0 ** -8 * np.abs(gref).max()
+    assert np.abs(got[:, 0] - gref).max() <= 1e-2 * np.abs(gref).max()
     assert np.all(got[:, 1:] == 0.5)
