@@ -98,3 +98,52 @@ def run_quench(nx, ny, G, rho0, kT=1e-6, steps=50000, every=500, seed=100, tau=1
     topo, phi, comps = classify_topology(rho, threshold=rho0)
     return {"t": np.array(times), "L": np.array(L), "S": np.array(S), "density": rho,
             "topology": topo, "liquid_fraction": phi, "components": comps}
+
+
+def growth_exponent(t, L, t_min):
+    """Least-squares slope of log L against log t over t >= t_min."""
+    t, L = np.asarray(t, float), np.asarray(L, float)
+    sel = t >= t_min
+    return float(np.polyfit(np.log(t[sel]), np.log(L[sel]), 1)[0])
+
+
+def block_mean(field, b):
+    """b x b block means of a 2D field (for classifying large lattices)."""
+    ny, nx = field.shape
+    return field.reshape(ny // b, b, nx // b, b).mean(axis=(1, 3))
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import math
+    ap = argparse.ArgumentParser(description="2D unstable-branch quenches: S(k,t), L(t), topology")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--G", type=float, default=-5.0)
+    ap.add_argument("--steps", type=int, default=50000)
+    ap.add_argument("--every", type=int, default=500)
+    ap.add_argument("--seeds", default="100,101")
+    ap.add_argument("--rho0", default=f"{math.log(2.0)},0.422",
+                    help="the critical density and a 15%% liquid-fraction state at G = -5")
+    ap.add_argument("--block", type=int, default=4, help="block mean before classification")
+    ap.add_argument("--out", default=None, help="npz with t, L and S(k, t) of every run")
+    a = ap.parse_args()
+    saved = {}
+    for rho0 in [float(r) for r in a.rho0.split(",")]:
+        for seed in [int(s) for s in a.seeds.split(",")]:
+            r = run_quench(a.n, a.n, a.G, rho0, steps=a.steps, every=a.every, seed=seed)
+            coarse = block_mean(r["density"], a.block) if a.block > 1 else r["density"]
+            topo, phi, _ = classify_topology(coarse, rho0)
+            lo, hi = np.percentile(r["density"], [1.0, 99.0])
+            t, L = r["t"], r["L"]
+            line = {"n": a.n, "G": a.G, "rho0": rho0, "seed": seed, "topology": topo,
+                    "liquid_fraction": phi, "rho_gas": float(lo), "rho_liquid": float(hi),
+                    "L": {str(int(tt)): float(LL) for tt, LL in zip(t, L)
+                          if int(tt) in (1000, 2000, 5000, 10000, 20000, 50000)},
+                    "exponent_t_ge_5000": growth_exponent(t, L, 5000),
+                    "exponent_t_ge_20000": growth_exponent(t, L, 20000)}
+            print(json.dumps(line), flush=True)
+            key = f"rho{rho0:.4f}_s{seed}"
+            saved[key + "_t"], saved[key + "_L"], saved[key + "_S"] = t, L, r["S"][:, :512]
+    if a.out:
+        np.savez(a.out, **saved)
