@@ -366,6 +366,46 @@ static void step3(or3_lattice *h) {
         sk_sample3(h);
 }
 
+/* One step evaluated at chosen sites only, from a full-lattice input state
+ * f_in [19][nz][ny][nx] (full populations) at step t: the same pull, density,
+ * pseudopotential, force and collision as step3, with the density of each
+ * force neighbour computed on demand.  For checking large lattices site by
+ * site.  Returns -1 if a site is out of range. */
+static double density3_after_streaming(const or3_params *p, const double *f_in, int x, int y,
+                                       int z) {
+    double s = 0.0;
+    for (int i = 0; i < 19; ++i)
+        s += f_in[IDX3(i, wrap3(x - C3[i][0], p->nx), wrap3(y - C3[i][1], p->ny),
+                       wrap3(z - C3[i][2], p->nz), p)];
+    return s;
+}
+
+int or3_step_sites(const or3_params *p, long long t, const double *f_in, int nsites,
+                   const int *xs, const int *ys, const int *zs, double *out) {
+    setup3();
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    for (int k = 0; k < nsites; ++k) {
+        int x = xs[k], y = ys[k], z = zs[k];
+        if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) return -1;
+        double g[19], S[3] = {0, 0, 0}, F[3];
+        for (int i = 0; i < 19; ++i)
+            g[i] = f_in[IDX3(i, wrap3(x - C3[i][0], nx), wrap3(y - C3[i][1], ny),
+                             wrap3(z - C3[i][2], nz), p)];
+        for (int a = 1; a < 19; ++a) {
+            double wa = C3[a][0] * C3[a][0] + C3[a][1] * C3[a][1] + C3[a][2] * C3[a][2] == 1
+                            ? 1.0 / 6.0 : 1.0 / 12.0;
+            double pn = psi3(p, density3_after_streaming(p, f_in, wrap3(x + C3[a][0], nx),
+                                                         wrap3(y + C3[a][1], ny),
+                                                         wrap3(z + C3[a][2], nz)));
+            for (int b = 0; b < 3; ++b) S[b] += wa * pn * C3[a][b];
+        }
+        double pc = psi3(p, density3_after_streaming(p, f_in, x, y, z));
+        for (int b = 0; b < 3; ++b) F[b] = -p->G * CS2 * pc * S[b];
+        collide3(p, (uint32_t)SITE3(x, y, z, p), (uint32_t)t, g, F, out + 19 * (size_t)k);
+    }
+    return 0;
+}
+
 int or3_step(or3_lattice *h, int nsteps) {
     for (int s = 0; s < nsteps; ++s) step3(h);
     return 0;

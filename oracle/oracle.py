@@ -104,6 +104,9 @@ def lib():
         L.or3_force_field.argtypes = [C.c_void_p, _D]
         L.or3_moment_basis.argtypes = [_D, _D]
         L.or3_normals.argtypes = [C.POINTER(Or3Params), C.c_uint32, C.c_uint32, _D]
+        L.or3_step_sites.argtypes = [C.POINTER(Or3Params), C.c_longlong, _D, C.c_int, _I, _I, _I,
+                                     _D]
+        L.or3_step_sites.restype = C.c_int
         L.or_box_muller_ring.argtypes = [C.c_uint32, C.c_uint32, _D]
         L.or_threads.restype = C.c_int
         _lib = L
@@ -281,6 +284,21 @@ def normals3(nx, ny, nz, seed, replica, site, t):
     z = np.zeros(15)
     lib().or3_normals(C.byref(p), site, t, z)
     return z
+
+
+def step_sites3(nx, ny, nz, G, tau, kT, seed, t, f_full, xs, ys, zs, replica=0, psi_kind=0,
+                psi_p1=0.0, psi_p2=0.0):
+    """One oracle D3Q19 step evaluated at the sites (xs[i], ys[i], zs[i]) of a
+    full-lattice input state f_full ([19][nz][ny][nx], full populations) at
+    step t.  Returns [n][19]."""
+    p = Or3Params(nx, ny, nz, G, tau, kT, 0.0, seed, replica, psi_kind, psi_p1, psi_p2)
+    xs, ys, zs = (np.ascontiguousarray(a, np.int32) for a in (xs, ys, zs))
+    out = np.zeros(19 * len(xs))
+    rc = lib().or3_step_sites(C.byref(p), int(t), np.ascontiguousarray(f_full, np.float64).ravel(),
+                              len(xs), xs, ys, zs, out)
+    if rc != 0:
+        raise ValueError("oracle: site out of range")
+    return out.reshape(len(xs), 19)
 
 
 class OracleLattice3:

@@ -51,3 +51,37 @@ def test_fullsize_4096_one_step_sampled_sites():
     d_got = got.sum(1) - LN2
     d_ref = ref.sum(1) - LN2
     assert np.abs(d_got - d_ref).max() < 1e-4 * np.sqrt((d_ref ** 2).mean())
+
+
+def test_fullsize_d3q19_256_one_step_sampled_sites():
+    """The D3Q19 step at the 3D benchmark's size (256^3 FP32, G = -5.0,
+    rho0 = ln 2, kT = 1e-6, tau = 1: the unit-relaxation path, strip of 16
+    planes as timed) against the oracle evaluated site by site on the same
+    input state: random sites plus tile, strip and wrap boundaries."""
+    from paper_2212_07848_gb300.lattice3 import Lattice3
+    n = 256
+    G, tau, kT, seed = -5.0, 1.0, 1e-6, 100
+    g = Lattice3(n, n, n, G, tau, kT)
+    g.set_strip(16)
+    g.init(LN2, seed, 0.01)
+    c0 = g.conserved()
+    g.step(3)
+    f_in = g.populations()
+    g.step(1)
+    f_out = g.populations()
+    c1 = g.conserved()
+    g.close()
+    assert abs(c1[0] - c0[0]) / c0[0] < 1e-6
+    assert np.abs(c1[1:] - c0[1:]).max() < 1e-6 * c0[0]
+    rng = np.random.default_rng(2)
+    xs, ys, zs = (list(rng.integers(0, n, 1500)) for _ in range(3))
+    for ex in (0, 1, 31, 32, 33, 255):
+        for ey in (0, 7, 8, 9, 255):
+            for ez in (0, 15, 16, 17, 255):
+                xs.append(ex)
+                ys.append(ey)
+                zs.append(ez)
+    ref = O.step_sites3(n, n, n, G, tau, kT, seed, 3, f_in, xs, ys, zs)
+    got = f_out[:, zs, ys, xs].T
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() < 1e-5, rel.max()

@@ -209,3 +209,18 @@ def test_force_continuum_limit(axis, kind):
         others = [b for b in range(3) if b != axis]
         assert np.abs(F[others]).max() < 1e-15
     assert errs[1] < errs[0] / 3.5 and errs[1] < 1e-2, errs
+
+
+def test_step_sites_equals_full_step():
+    """The site-by-site step (for checking large lattices) reproduces the
+    full-lattice step at every site of a small noisy lattice, bit for bit."""
+    nx, ny, nz, G, tau, kT, seed = 6, 5, 4, -4.2, 0.9, 1e-4, 7
+    o = O.OracleLattice3(nx, ny, nz, G, tau, kT)
+    o.init(LN2, seed, 0.02)
+    o.step(2)
+    f_in = o.populations().copy()
+    o.step(1)
+    ref = o.populations()
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    got = O.step_sites3(nx, ny, nz, G, tau, kT, seed, 2, f_in, xx.ravel(), yy.ravel(), zz.ravel())
+    assert np.array_equal(got.T.reshape(19, nz, ny, nx), ref)
