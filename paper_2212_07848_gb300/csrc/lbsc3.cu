@@ -100,7 +100,28 @@ template <typename T> struct K3 {
     T rho0, force_pref, psi_c, psi_b, psi0, gamma, hsrc;
     T amp[19];     // modes 4..18 used
     uint32_t rk[20];
+    const float2 *ring;   // (cos, sin) of the 1024 ring angles 2 pi (a + 1/2) / 1024
 };
+
+constexpr int kRing3 = 1024;
+
+// One ring Box-Muller pair folded with sqrt(rho): rad = sqrt(-2 rho ln u1),
+// (c, s) = (cos, sin) of angle a.  FP32 reads the angle's cosine and sine from
+// the table (correctly rounded from FP64) instead of evaluating them; FP64
+// evaluates them.
+__device__ __forceinline__ void ring_pair3(float u1, uint32_t a, float rho,
+                                           const float2 *__restrict__ ring, float &rad, float &c,
+                                           float &s) {
+    const float x = (-1.3862943611198906f * rho) * __log2f(u1);   // -2 rho ln u1 > 0
+    rad = x * rsqrtf(fmaxf(x, 1e-30f));
+    const float2 cs = ring[a];
+    c = cs.x;
+    s = cs.y;
+}
+__device__ __forceinline__ void ring_pair3(double u1, uint32_t a, double rho, const float2 *,
+                                           double &rad, double &c, double &s) {
+    box_ring_polar(u1, a, rho, rad, c, s);
+}
 
 // Pull of one site from precomputed wrapped offsets: xo[1 + d] = x + d,
 // yo[1 + d] = (y + d) nx and zo[1 + d] = (z + d) nx ny for d = -1, 0, 1.
@@ -136,7 +157,7 @@ __device__ __forceinline__ double inv3(double rho) { return 1.0 / rho; }
 // that of the general path with gamma = 0.
 template <typename T, bool UNIT = false>
 __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const K3<T> &p,
-                                         uint32_t site, T f[19]) {
+                                         uint32_t site, const float2 *ring, T f[19]) {
     // pair sums and differences: pair q = velocities 2q+1 (c) and 2q+2 (-c)
     T s[10], d[10];
     s[0] = g[0];
@@ -195,7 +216,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         const uint4 r2 = philox4x32_10(make_uint4(site, p.step, p.replica, 2u), p.rk);
         T c, sn, rad;
 #define NOISE_PAIR(R, WORD, SHIFT, KA, KB)                                                 \
-    box_ring_polar(uniform01<T>(R.WORD), (R.w >> SHIFT) & 1023u, rho, rad, c, sn);       \
+    ring_pair3(uniform01<T>(R.WORD), (R.w >> SHIFT) & 1023u, rho, ring, rad, c, sn);     \
     ms[KA] = fma(p.amp[KA] * rad, c, ms[KA]);                                             \
     ms[KB] = fma(p.amp[KB] * rad, sn, ms[KB]);
         NOISE_PAIR(r0, x, 0, 4, 5)
@@ -207,7 +228,7 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         NOISE_PAIR(r2, x, 0, 16, 17)
 #undef NOISE_PAIR
         // mode 18: the cosine of the pair (r2.y, bits 10-19 of r2.w)
-        box_ring_polar(uniform01<T>(r2.y), (r2.w >> 10) & 1023u, rho, rad, c, sn);
+        ring_pair3(uniform01<T>(r2.y), (r2.w >> 10) & 1023u, rho, ring, rad, c, sn);
         ms[18] = fma(p.amp[18] * rad, c, ms[18]);
     }
     // inverse: delta f_i = w_i sum_k e_ki m*_k / b_k, assembled per pair as
@@ -263,6 +284,9 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
 template <typename T, bool SAMPLE, bool UNIT = false>
 __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
     __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
+    __shared__ float2 s_ring[kRing3];    // noise angles (FP32 path; read after the first barrier)
+    if (std::is_same<T, float>::value && p.noise)
+        for (int i = threadIdx.x; i < kRing3; i += blockDim.x) s_ring[i] = p.ring[i];
     const int tx = threadIdx.x % kBX3, ty = threadIdx.x / kBX3;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const uint32_t plane = (uint32_t)nx * ny * nz;
@@ -318,7 +342,7 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
             const uint32_t site = ((uint32_t)zc * ny + y) * nx + x;
             T g[19], f[19];
             pull3(p.src, plane, xo, yo, zprev, g);
-            collide3<T, UNIT>(g, Fx, Fy, Fz, p, site, f);
+            collide3<T, UNIT>(g, Fx, Fy, Fz, p, site, s_ring, f);
 #pragma unroll
             for (int i = 0; i < 19; ++i) p.dst[(uint32_t)i * plane + site] = f[i];
             if (SAMPLE) p.drho_out[site] = sum19(g);
@@ -517,6 +541,7 @@ struct lb3_ctx {
     double *d_prof = nullptr;      // [nz][nx] + [nz][ny] + [nz] plane profiles
     double *d_acc = nullptr;       // axis S(k) sums [nx/2 + ny/2 + nz/2]
     double *d_io = nullptr;        // n doubles for read-outs
+    float2 *d_ring = nullptr;      // [1024] (cos, sin) of the noise ring angles
     int sk_every = 0;
     long long sk_start = 0, sk_count = 0, t = 0;
     uint64_t seed = 0;
@@ -567,6 +592,7 @@ K3<T> params3(const lb3_ctx *h, bool sample) {
     const double mu = h->kT * 3.0;
     for (int kk = 4; kk < 19; ++kk) k.amp[kk] = (T)sqrt(mu * norm3(kk) * (1.0 - gam * gam));
     philox_round_keys(h->seed, k.rk);
+    k.ring = h->d_ring;
     return k;
 }
 
@@ -628,6 +654,7 @@ void free3(lb3_ctx *h) {
     cudaFree(h->d_prof);
     cudaFree(h->d_acc);
     cudaFree(h->d_io);
+    cudaFree(h->d_ring);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -673,6 +700,15 @@ int lb3_create(lb3_ctx **out, int nx, int ny, int nz, double G, double tau, doub
     if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_part, 4 * h->nred * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_ring, kRing3 * sizeof(float2));
+    if (e == cudaSuccess) {
+        float2 tab[kRing3];
+        for (int a = 0; a < kRing3; ++a) {
+            const double th = M_PI * (2.0 * a + 1.0) / kRing3;   // 2 pi (a + 1/2) / 1024
+            tab[a] = make_float2((float)cos(th), (float)sin(th));
+        }
+        e = cudaMemcpy(h->d_ring, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         free3(h);
         delete h;
