@@ -63,3 +63,26 @@ def test_reference_arm_rank1_does_no_work(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(capsys):
+    """`bench.py --impl reference` at N = 1: one JSON line with the keys of the
+    benchmark contract, the oracle as the timed program."""
+    import argparse
+    import json
+
+    import bench
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1)
+    bench.run_reference(args, rank=0, world=1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["metric"] == bench.METRIC and d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
