@@ -306,11 +306,13 @@ def d3q19_leg(n=256, steps=40, strips=(16, 32, 64)):
             "achieved_gbs": gbs, "hbm_frac": gbs / peak, "peak_kind": kind}
 
 
-def l2_assisted_leg(n=1024, steps=2000):
+def l2_assisted_leg(n=1024, steps=2000, strips=(8, 9, 12, 16, 32)):
     """The 1024^2 lattice of the metastable density sweep (FP32, E4, G = -4.5,
     rho0 = 0.33 on the gas branch between coexistence and spinodal, kT =
     1e-6): its 75 MB of populations fit the 129 MB L2, so its rate is
-    L2-assisted and is reported apart from the HBM-bound headline."""
+    L2-assisted and is reported apart from the HBM-bound headline; the
+    fastest of a few strip heights (a 1024^2 lattice fills only about one
+    wave of CTAs, so the strip height decides the halo share and the tail)."""
     import torch
 
     from paper_2212_07848_gb300.lattice import Lattice
@@ -320,14 +322,21 @@ def l2_assisted_leg(n=1024, steps=2000):
     lat.sync()
     st = torch.cuda.ExternalStream(lat.stream())
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    lat.step(steps)
-    b.record(st)
-    b.synchronize()
-    ms = a.elapsed_time(b) / steps
+    best = None
+    for strip in strips:
+        lat.set_strip_height(strip)
+        lat.step(50)
+        a.record(st)
+        lat.step(steps)
+        b.record(st)
+        b.synchronize()
+        t = a.elapsed_time(b) / steps
+        if best is None or t < best[1]:
+            best = (strip, t)
     lat.close()
+    ms = best[1]
     sites = n * n
-    return {"lattice": f"{n}^2 FP32 E4, G=-4.5, rho0=0.33", "ms_per_step": ms,
+    return {"lattice": f"{n}^2 FP32 E4, G=-4.5, rho0=0.33", "strip_h": best[0], "ms_per_step": ms,
             "mlups": sites / (ms * 1e-3) / 1e6,
             "equivalent_gbs": BYTES_PER_SITE * sites / (ms * 1e-3) / 1e9,
             "note": "populations (75 MB) resident in L2; not an HBM figure"}

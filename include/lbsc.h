@@ -379,8 +379,9 @@ int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int 
  * dbias [cout] (may be NULL): dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n].
  * The sum is split over chunks of 128-pixel tiles whose partial sums go to the
  * caller's device workspace (16-byte aligned, at least
- * lb_nn_wgrad_workspace(...) bytes) and are then added in a fixed order, so
- * dw is deterministic.  Requires h * w % 128 == 0 and channel counts
+ * lb_nn_wgrad_workspace(...) bytes, which also holds the bias partials) and
+ * are then added in a fixed order, so dw and dbias are deterministic (the same
+ * inputs give the same bits).  Requires h * w % 128 == 0 and channel counts
  * multiples of 16 (LB_ERR_ARG otherwise, or for a missing/short workspace). */
 size_t lb_nn_wgrad_workspace(int nb, int h, int w_, int cin, int cout);
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,

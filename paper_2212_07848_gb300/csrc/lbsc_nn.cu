@@ -308,15 +308,36 @@ WgPlan wgrad_plan(int nb, int h, int w, int cin, int cout) {
 #define GRID_STRIDE(i, n) \
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
 
-__global__ void bias_grad_kernel(const bf16 *__restrict__ dy, float *__restrict__ db, size_t P, int C) {
-    // one block per channel group of 32; threads stride over pixels
-    const int c = blockIdx.y * 32 + (threadIdx.x & 31);
-    if (c >= C) return;
+// Bias gradient db[c] += sum_p dy[p][c] in a fixed order: block (b, g) sums
+// channel group g over its grid-stride share of pixels (each warp a strided
+// subset, then the warps in order) into part[b][c]; bias_reduce_kernel adds
+// the kBiasBlocks partials of each channel in order.
+constexpr int kBiasBlocks = 256;
+__global__ void __launch_bounds__(256) bias_grad_kernel(const bf16 *__restrict__ dy,
+                                                        float *__restrict__ part, size_t P, int C) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.y * 32 + lane;
     float s = 0.f;
-    for (size_t p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; p < P;
-         p += (size_t)gridDim.x * (blockDim.x / 32))
-        s += __bfloat162float(dy[p * C + c]);
-    atomicAdd(&db[c], s);
+    if (c < C)
+        for (size_t p = blockIdx.x * (blockDim.x / 32) + warp; p < P;
+             p += (size_t)gridDim.x * (blockDim.x / 32))
+            s += __bfloat162float(dy[p * C + c]);
+    __shared__ float red[8][32];
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && c < C) {
+        float a = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w][lane];
+        part[(size_t)blockIdx.x * C + c] = a;
+    }
+}
+__global__ void bias_reduce_kernel(const float *__restrict__ part, float *__restrict__ db, int C,
+                                   int nblocks) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float a = 0.f;
+    for (int b = 0; b < nblocks; ++b) a += part[(size_t)b * C + c];
+    db[c] += a;
 }
 
 __global__ void relu_mask_kernel(const bf16 *__restrict__ dy, const bf16 *__restrict__ y,
@@ -688,7 +709,8 @@ size_t lb_nn_wgrad_workspace(int nb, int h, int wd, int cin, int cout) {
         ((size_t)h * wd) % kWgTile)
         return 0;
     const WgPlan p = wgrad_plan(nb, h, wd, cin, cout);
-    return (size_t)p.nchunk * 9 * cout * cin * sizeof(float);
+    // chunk partials of dw, then the bias partials [kBiasBlocks][cout]
+    return ((size_t)p.nchunk * 9 * cout * cin + (size_t)kBiasBlocks * cout) * sizeof(float);
 }
 
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
@@ -716,8 +738,11 @@ int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, 
     wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, n, p.nchunk);
     if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
     if (dbias) {
-        dim3 gb(256, (cout + 31) / 32);
-        bias_grad_kernel<<<gb, 256, 0, s>>>(db, dbias, (size_t)nb * h * wd, cout);
+        float *bpart = part + (size_t)p.nchunk * n;
+        dim3 gb(kBiasBlocks, (cout + 31) / 32);
+        bias_grad_kernel<<<gb, 256, 0, s>>>(db, bpart, (size_t)nb * h * wd, cout);
+        if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+        bias_reduce_kernel<<<(cout + 127) / 128, 128, 0, s>>>(bpart, dbias, cout, kBiasBlocks);
     }
     NN_RET();
 }

@@ -111,13 +111,16 @@ def test_conv_weight_gradient(nb, h, w, cin, cout):
     first = dw.clone()
     _close(dw.cpu().numpy(), 2 * R.conv3x3_wgrad(_np(x), _np(dy)), 1e-3)
     _close(db.cpu().numpy(), 2 * _np(dy).sum(axis=(0, 1, 2)), 1e-3)
-    # deterministic: the same inputs give the same bits
+    # deterministic: the same inputs give the same bits (weights and biases)
+    first_b = db.clone()
     dw.zero_()
+    db.zero_()
     for _ in range(2):
-        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), None, nb, h, w, cin, cout, _p(ws),
+        assert L.lb_nn_conv3x3_wgrad(_p(x), _p(dy), _p(dw), _p(db), nb, h, w, cin, cout, _p(ws),
                                      nbytes, None) == 0
     torch.cuda.synchronize()
     assert torch.equal(dw, first)
+    assert torch.equal(db, first_b)
 
 
 def test_pool_up_relu_adam():

@@ -151,3 +151,18 @@ def test_guarded_rollout_hands_back_to_the_solver(trained):
     fields, n = S.guarded_rollout(net, frames[k, f0].clone(), float(Gs[k]), 6, frames[k, f0 - 1],
                                   mass_tol=0.0, bound=1e-9)
     assert n == 0 and fields.shape[0] == 0
+
+
+def test_training_is_reproducible():
+    """Two trainings from the same seed on the same frames give the same
+    weights bit for bit (every gradient sum runs in a fixed order)."""
+    from paper_2212_07848_gb300 import surrogate as S
+    frames, Gs, _ = S.generate(3, 128, 800, 200, seed0=3000)
+    ws = []
+    for _ in range(2):
+        net = S.SurrogateNet(32, 4, seed=5)
+        S.train(net, frames, Gs, [0, 1, 2], 40, lr=1e-3, seed=2, pushforward=0.5)
+        torch.cuda.synchronize()
+        ws.append([w.clone() for w in net.w] + [b.clone() for b in net.b])
+    for a, b in zip(*ws):
+        assert torch.equal(a, b)
