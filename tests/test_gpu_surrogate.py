@@ -157,10 +157,10 @@ def test_training_is_reproducible():
     """Two trainings from the same seed on the same frames give the same
     weights bit for bit (every gradient sum runs in a fixed order)."""
     from paper_2212_07848_gb300 import surrogate as S
-    frames, Gs, _ = S.generate(3, 128, 800, 200, seed0=3000)
+    frames, Gs, _ = S.generate(3, 256, 800, 200, seed0=3000)
     ws = []
     for _ in range(2):
-        net = S.SurrogateNet(32, 4, seed=5)
+        net = S.SurrogateNet(64, 4, seed=5)
         S.train(net, frames, Gs, [0, 1, 2], 40, lr=1e-3, seed=2, pushforward=0.5)
         torch.cuda.synchronize()
         ws.append([w.clone() for w in net.w] + [b.clone() for b in net.b])
