@@ -218,7 +218,9 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
     coarse-grained 4x every `stride` steps; the network is trained (Adam,
     cosine learning rate, pushforward trick) on all but `ntest`, which score
     it: one-stride MSE against persistence, and rollouts judged by the solver
-    on the ensemble-mean L(t) and radial S(k, t).  The speedup is the solver's
+    on the ensemble-mean L(t) and radial S(k, t), next to the same metrics for
+    the solver itself continued on an independent noise stream (the floor of
+    any predictor of a stochastic run).  The speedup is the solver's
     time for `stride` steps at size^2 over the surrogate's time for one stride
     at (size/4)^2."""
     import torch
@@ -239,6 +241,16 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
     for f0, nroll in ((5, 10), (10, 20)):
         ev = S.evaluate_rollouts(net, frames, Gs, test_ids, f0, nroll)
         rollouts[f"t={f0 * stride}..{(f0 + nroll) * stride}"] = {
+            "L_mean_max_rel_err": ev["L_mean_max_rel_err"],
+            "L_traj_max_rel_err": ev["L_traj_max_rel_err"],
+            "Sk_peak_max_rel_err": ev["Sk_peak_max_rel_err"],
+            "Sk_l1_rel_err": ev["Sk_l1_rel_err"]}
+    # the floor: the solver itself continued from the same states on an
+    # independent noise stream, judged by the same ensemble metrics
+    floor = {}
+    for f0, nroll in ((5, 10), (10, 20)):
+        ev = S.solver_reseeded(frames, Gs, test_ids, f0, nroll, size, stride, seed * 1000)
+        floor[f"t={f0 * stride}..{(f0 + nroll) * stride}"] = {
             "L_mean_max_rel_err": ev["L_mean_max_rel_err"],
             "L_traj_max_rel_err": ev["L_traj_max_rel_err"],
             "Sk_peak_max_rel_err": ev["Sk_peak_max_rel_err"],
@@ -268,7 +280,7 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
             "trajectories": ntraj, "test_trajectories": ntest, "train_iters": iters,
             "batch": batch, "generate_s": gen_s, "train_s": train_s,
             "heldout_mse": mse, "persistence_mse": persist, "mse_ratio": mse / persist,
-            "rollouts": rollouts,
+            "rollouts": rollouts, "solver_reseeded": floor,
             "surrogate_ms_per_stride": sur_ms, "solver_ms_per_stride": lb_ms,
             "speedup": lb_ms / sur_ms}
 

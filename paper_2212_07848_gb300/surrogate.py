@@ -454,6 +454,63 @@ def guarded_rollout(net, frame0, G, strides, prev0=None, mass_tol=1e-3, bound=No
     return out[:n], n
 
 
+def compare_ensembles(out, ref):
+    """The ensemble metrics of evaluate_rollouts for rollouts `out` and solver
+    frames `ref` (lists over trajectories of [nroll][m][m] arrays)."""
+    Ls, Lr, Ss, Sr, per = [], [], [], [], []
+    for o, r in zip(out, ref):
+        a = [radial_sk(f) for f in o]
+        b = [radial_sk(f) for f in r]
+        Ls.append([v[1] for v in a])
+        Lr.append([v[1] for v in b])
+        Ss.append([v[0] for v in a])
+        Sr.append([v[0] for v in b])
+        per.append(np.max(np.abs(np.array(Ls[-1]) - np.array(Lr[-1])) / np.array(Lr[-1])))
+    Ls, Lr = np.mean(Ls, axis=0), np.mean(Lr, axis=0)
+    Ss, Sr = np.mean(Ss, axis=0), np.mean(Sr, axis=0)
+    s_peak, s_l1 = 0.0, 0.0
+    for t in range(len(Ls)):
+        sel = Sr[t] >= 0.25 * Sr[t].max()
+        s_peak = max(s_peak, float(np.max(np.abs(Ss[t][sel] - Sr[t][sel]) / Sr[t][sel])))
+        s_l1 = max(s_l1, float(np.abs(Ss[t] - Sr[t]).sum() / Sr[t].sum()))
+    return {"L_surrogate": Ls.tolist(), "L_solver": Lr.tolist(),
+            "L_mean_max_rel_err": float(np.max(np.abs(Ls - Lr) / Lr)),
+            "L_traj_max_rel_err": float(np.max(per)), "Sk_peak_max_rel_err": s_peak,
+            "Sk_l1_rel_err": s_l1, "Sk_surrogate": Ss, "Sk_solver": Sr}
+
+
+def solver_reseeded(frames, Gs, ids, f0, nroll, size, stride, seed0, coarse=4, kT=1e-6,
+                    rho0=math.log(2.0), stencil=4):
+    """The floor of any predictor of S(k, t): each trajectory of `ids` is
+    re-run by the solver to frame f0 (the same fine state as in `generate`
+    with the same seed0), then continued on an independent noise stream
+    (replica counter 1) for `nroll` strides and compared with its own frames
+    by the metrics of evaluate_rollouts."""
+    import torch
+
+    from .lattice import Lattice
+    L = abi.load()
+    m = size // coarse
+    outs, refs = [], []
+    buf = torch.empty((nroll, m, m), dtype=torch.float32, device="cuda")
+    for k in ids:
+        lat = Lattice(size, size, float(Gs[k]), 1.0, kT, stencil=stencil)
+        lat.init(rho0, seed0 + k, 0.0)
+        lat.step(f0 * stride)
+        lat.set_replica(1)
+        df = C.c_void_p(lat.device_ptr(abi.LB_PTR_POPULATIONS))
+        for s in range(nroll):
+            lat.step(stride)
+            _check(L.lb_nn_coarse_grain(df, size, size, coarse, 1.0, _p(buf[s]),
+                                        C.c_void_p(lat.stream())), "coarse")
+        lat.sync()
+        lat.close()
+        outs.append(buf.cpu().numpy().copy())
+        ref = frames[k, f0 + 1:f0 + 1 + nroll]
+        refs.append((ref[:, 0] if frames.dim() == 5 else ref).cpu().numpy())
+    return compare_ensembles(outs, refs)
+
+
 def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
     """Judge the surrogate against the solver: from frame f0 of each trajectory
     in `ids` (with frame f0 - 1 for the increment input) roll out `nroll`
@@ -463,30 +520,13 @@ def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
     radial S(k, t) gap, each the worst over the rollout: the largest relative
     gap over the peak shells (solver S at least a quarter of its maximum) and
     the L1 gap sum |S_sur - S_sol| / sum S_sol over all shells."""
-    Ls, Lr, Ss, Sr, per = [], [], [], [], []
+    outs, refs = [], []
     for k in ids:
-        out = rollout(net, frames[k, f0].clone(), float(Gs[k]), nroll,
-                      frames[k, f0 - 1] if f0 > 0 else None).cpu().numpy()
+        outs.append(rollout(net, frames[k, f0].clone(), float(Gs[k]), nroll,
+                            frames[k, f0 - 1] if f0 > 0 else None).cpu().numpy())
         ref = frames[k, f0 + 1:f0 + 1 + nroll]
-        ref = (ref[:, 0] if frames.dim() == 5 else ref).cpu().numpy()
-        a = [radial_sk(f) for f in out]
-        b = [radial_sk(f) for f in ref]
-        Ls.append([v[1] for v in a])
-        Lr.append([v[1] for v in b])
-        Ss.append([v[0] for v in a])
-        Sr.append([v[0] for v in b])
-        per.append(np.max(np.abs(np.array(Ls[-1]) - np.array(Lr[-1])) / np.array(Lr[-1])))
-    Ls, Lr = np.mean(Ls, axis=0), np.mean(Lr, axis=0)
-    Ss, Sr = np.mean(Ss, axis=0), np.mean(Sr, axis=0)
-    s_peak, s_l1 = 0.0, 0.0
-    for t in range(nroll):
-        sel = Sr[t] >= 0.25 * Sr[t].max()
-        s_peak = max(s_peak, float(np.max(np.abs(Ss[t][sel] - Sr[t][sel]) / Sr[t][sel])))
-        s_l1 = max(s_l1, float(np.abs(Ss[t] - Sr[t]).sum() / Sr[t].sum()))
-    return {"L_surrogate": Ls.tolist(), "L_solver": Lr.tolist(),
-            "L_mean_max_rel_err": float(np.max(np.abs(Ls - Lr) / Lr)),
-            "L_traj_max_rel_err": float(np.max(per)), "Sk_peak_max_rel_err": s_peak,
-            "Sk_l1_rel_err": s_l1, "Sk_surrogate": Ss, "Sk_solver": Sr}
+        refs.append((ref[:, 0] if frames.dim() == 5 else ref).cpu().numpy())
+    return compare_ensembles(outs, refs)
 
 
 def radial_sk(field):
