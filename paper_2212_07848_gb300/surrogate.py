@@ -279,14 +279,16 @@ def advance(net, state, x, npx, mean=None):
 
 
 def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=1, lr_end=None,
-          pushforward=0.0):
+          pushforward=0.0, pf_depth=1):
     """Adam on random (trajectory, time) pairs of consecutive frames, the frame
     before each pair giving the last-increment input; the learning rate decays
     from `lr` to `lr_end` on a cosine (constant without `lr_end`).  With
     probability `pushforward` an iteration first advances the batch one stride
     with the network itself (no gradient) and trains on that prediction as the
     input (the pushforward trick: the network learns to correct its own
-    rollout errors).  Returns the losses logged every `log_every` iterations."""
+    rollout errors); with pf_depth > 1 that advance is 1 .. pf_depth strides
+    (uniform), so it also learns from errors compounded over several strides.
+    Returns the losses logged every `log_every` iterations."""
     import torch
     L = net.L
     if net.nb != net.batch:
@@ -306,16 +308,17 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
     losses = []
     for it in range(iters):
         pf = pushforward > 0.0 and rng.random() < pushforward
+        depth = (int(rng.integers(1, pf_depth + 1)) if pf_depth > 1 else 1) if pf else 0
         for j in range(nb):
             k = int(rng.choice(train_ids))
-            f = int(rng.integers(max(t_min, 2) if pf else t_min, nf - 1))
-            src = f - 1 if pf else f
+            f = int(rng.integers(max(t_min, depth + 1) if pf else t_min, nf - 1))
+            src = f - depth
             bview(j).copy_(frames[k, src])
             tview(j).copy_(frames[k, f + 1])
             expand_state(L, frames[k, src], Gs[k], x[j], frames[k, src - 1] if src > 0 else None,
                          net.s)
-        if pf:
-            # one stride by the network itself: base becomes its prediction of
+        for _ in range(depth):
+            # strides by the network itself: base becomes its prediction of
             # frame f, x the matching input (with the increments just applied)
             net.forward(x)
             advance(net, base, x, nb * m * m)
