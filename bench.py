@@ -216,7 +216,7 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
     """Learned surrogate against the solver it stands in for: quench
     trajectories at size^2 (G ~ U[-5.2, -4.4], rho0 = ln2, kT = 1e-6)
     coarse-grained 4x every `stride` steps; the network is trained (Adam,
-    cosine learning rate, pushforward trick) on all but `ntest`, which score
+    cosine learning rate, pushforward over one or two strides) on all but `ntest`, which score
     it: one-stride MSE against persistence, and rollouts judged by the solver
     on the ensemble-mean L(t) and radial S(k, t), next to the same metrics for
     the solver itself continued on an independent noise stream (the floor of
@@ -233,7 +233,8 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
     train_ids, test_ids = list(range(ntraj - ntest)), list(range(ntraj - ntest, ntraj))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S.train(net, frames, Gs, train_ids, iters, lr=2e-3, lr_end=1e-5, seed=seed, pushforward=0.5)
+    S.train(net, frames, Gs, train_ids, iters, lr=2e-3, lr_end=1e-5, seed=seed, pushforward=0.5,
+            pf_depth=2)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     mse, persist = S.one_step_mse(net, frames, Gs, test_ids)
