@@ -354,6 +354,25 @@ int lb3_conserved(lb3_ctx *h, double out[4]);
 int lb3_sk_config(lb3_ctx *h, int every, long long start);
 int lb3_sk_reset(lb3_ctx *h);
 int lb3_structure_factor_axes(lb3_ctx *h, double *host_out, long long *nsamples_out);
+/* The full S(k) in 3D (the structure factor defined after Eq. (12) on every
+ * wave vector of the box): with enable != 0 each sampling step of
+ * lb3_sk_config also transforms the density sample in three dimensions
+ * (FFTs along x, y, z) and adds |delta rho(k)|^2 / N to FP64 sums over the
+ * half spectrum (device memory about nz ny (nx/2+1) x 16 bytes, allocated on
+ * the first call).  Call after lb3_sk_config(every > 0) (LB_ERR_STATE
+ * otherwise); nx, ny, nz must be powers of two (LB_ERR_UNSUPPORTED
+ * otherwise).  The sums are cleared by lb3_sk_reset and lb3_init. */
+int lb3_sk_full(lb3_ctx *h, int enable);
+/* Radial means of the full S(k) over the samples: host_bins[b], b = 0 ..
+ * nbins-1, is the mean over the modes with round(|q|) = b, q_a = m_a max(n) /
+ * n_a (m_a the folded wave-number index on axis a), k = 0 excluded; 0 for
+ * empty shells.  *nsamples_out (may be NULL) = number of samples.
+ * Synchronises.  LB_ERR_STATE without lb3_sk_full. */
+int lb3_structure_factor(lb3_ctx *h, double *host_bins, int nbins, long long *nsamples_out);
+/* First moments of the mean full S(k): out[0] = sum_k S(k), out[1] =
+ * sum_k |k| S(k) over all k != 0 (|k| = 2 pi |(m_x/nx, m_y/ny, m_z/nz)|), so
+ * the domain size is L = 2 pi out[0] / out[1].  Synchronises. */
+int lb3_sk_moments(lb3_ctx *h, double *host_out2);
 
 /* ---- learned surrogate building blocks ---------------------------------------
  * A small convolutional operator advances the 4x coarse-grained density of a

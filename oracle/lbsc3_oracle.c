@@ -206,6 +206,7 @@ typedef struct or3_lattice {
     int sk_every;
     long long sk_start, sk_count;
     double *sk_acc;   /* [nx/2 + ny/2 + nz/2]: x-axis modes, then y, then z */
+    double *sk_full;  /* NULL, or [nz][ny][nx] sums of |delta rho(k)|^2 / N over every k */
 } or3_lattice;
 
 or3_lattice *or3_create(const or3_params *p) {
@@ -227,7 +228,7 @@ or3_lattice *or3_create(const or3_params *p) {
 
 void or3_destroy(or3_lattice *h) {
     if (!h) return;
-    free(h->f); free(h->g); free(h->psi); free(h->sk_acc); free(h);
+    free(h->f); free(h->g); free(h->psi); free(h->sk_acc); free(h->sk_full); free(h);
 }
 
 void or3_init(or3_lattice *h, double rho0, uint64_t seed, double amp) {
@@ -309,8 +310,77 @@ static void sk_sample3(or3_lattice *h) {
         }
         off += L / 2;
     }
+    if (h->sk_full) {
+        /* every wave vector: the 3D DFT of delta rho by three separable passes
+         * (x, then y, then z), each the plain sum of its definition */
+        int nx = p->nx, ny = p->ny, nz = p->nz;
+        double *ar = (double *)calloc(n, sizeof(double)), *ai = (double *)calloc(n, sizeof(double));
+        double *br = (double *)calloc(n, sizeof(double)), *bi = (double *)calloc(n, sizeof(double));
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int k = 0; k < nx; ++k) {
+                    double re = 0.0, im = 0.0;
+                    for (int x = 0; x < nx; ++x) {
+                        double ph = 2.0 * M_PI * (double)(((long long)k * x) % nx) / nx;
+                        double d = rho[SITE3(x, y, z, p)] - mean;
+                        re += d * cos(ph);
+                        im -= d * sin(ph);
+                    }
+                    ar[SITE3(k, y, z, p)] = re;
+                    ai[SITE3(k, y, z, p)] = im;
+                }
+        for (int z = 0; z < nz; ++z)
+            for (int k = 0; k < ny; ++k)
+                for (int x = 0; x < nx; ++x) {
+                    double re = 0.0, im = 0.0;
+                    for (int y = 0; y < ny; ++y) {
+                        double ph = 2.0 * M_PI * (double)(((long long)k * y) % ny) / ny;
+                        double c = cos(ph), sn = sin(ph);
+                        double vr = ar[SITE3(x, y, z, p)], vi = ai[SITE3(x, y, z, p)];
+                        re += vr * c + vi * sn;
+                        im += vi * c - vr * sn;
+                    }
+                    br[SITE3(x, k, z, p)] = re;
+                    bi[SITE3(x, k, z, p)] = im;
+                }
+        for (int k = 0; k < nz; ++k)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    double re = 0.0, im = 0.0;
+                    for (int z = 0; z < nz; ++z) {
+                        double ph = 2.0 * M_PI * (double)(((long long)k * z) % nz) / nz;
+                        double c = cos(ph), sn = sin(ph);
+                        double vr = br[SITE3(x, y, z, p)], vi = bi[SITE3(x, y, z, p)];
+                        re += vr * c + vi * sn;
+                        im += vi * c - vr * sn;
+                    }
+                    h->sk_full[SITE3(x, y, k, p)] += (re * re + im * im) / (double)n;
+                }
+        free(ar); free(ai); free(br); free(bi);
+    }
     h->sk_count += 1;
     free(rho);
+}
+
+/* Full 3D S(k) on the sampling steps (every wave vector; cleared here). */
+int or3_sk_full(or3_lattice *h, int enable) {
+    const or3_params *p = &h->p;
+    free(h->sk_full);
+    h->sk_full = NULL;
+    if (enable) {
+        h->sk_full = (double *)calloc((size_t)p->nx * p->ny * p->nz, sizeof(double));
+        if (!h->sk_full) return -1;
+    }
+    return 0;
+}
+/* Mean over the samples of the full S(k), out [nz][ny][nx] (k = 0 included as
+ * sampled: zero, since the mean is removed). */
+long long or3_sk_full_get(const or3_lattice *h, double *out) {
+    const or3_params *p = &h->p;
+    size_t n = (size_t)p->nx * p->ny * p->nz;
+    for (size_t s = 0; s < n; ++s)
+        out[s] = (h->sk_full && h->sk_count) ? h->sk_full[s] / (double)h->sk_count : 0.0;
+    return h->sk_count;
 }
 
 void or3_sk_config(or3_lattice *h, int every, long long start) {

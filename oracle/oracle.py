@@ -99,6 +99,10 @@ def lib():
         L.or3_sk_config.argtypes = [C.c_void_p, C.c_int, C.c_longlong]
         L.or3_sk_get.argtypes = [C.c_void_p, _D]
         L.or3_sk_get.restype = C.c_longlong
+        L.or3_sk_full.argtypes = [C.c_void_p, C.c_int]
+        L.or3_sk_full.restype = C.c_int
+        L.or3_sk_full_get.argtypes = [C.c_void_p, _D]
+        L.or3_sk_full_get.restype = C.c_longlong
         L.or3_step.argtypes = [C.c_void_p, C.c_int]
         L.or3_lattice_constants.argtypes = [_I, _D]
         L.or3_force_field.argtypes = [C.c_void_p, _D]
@@ -364,3 +368,32 @@ class OracleLattice3:
         out = np.zeros(self.nx // 2 + self.ny // 2 + self.nz // 2)
         n = lib().or3_sk_get(self._h, out)
         return out, n
+
+    def sk_full(self, enable=True):
+        """Accumulate S(k) on every wave vector on the sampling steps."""
+        if lib().or3_sk_full(self._h, 1 if enable else 0) != 0:
+            raise MemoryError("oracle: full S(k)")
+
+    def structure_factor_full(self):
+        """(mean S(k) [nz][ny][nx] over every wave vector, nsamples)."""
+        out = np.zeros(self.nx * self.ny * self.nz)
+        n = lib().or3_sk_full_get(self._h, out)
+        return out.reshape(self.nz, self.ny, self.nx), n
+
+
+def radial_bins3(S):
+    """Radial means of a full S(k) cube [nz][ny][nx]: shell b holds the modes
+    with round(|q|) = b, q_a = m_a max(n) / n_a (m_a the folded index on axis
+    a); k = 0 excluded; empty shells 0.  Returns an array over b = 0 .. the
+    largest shell."""
+    nz, ny, nx = S.shape
+    Lm = max(nx, ny, nz)
+    fold = lambda n: np.where(np.arange(n) <= n // 2, np.arange(n), np.arange(n) - n)
+    qz, qy, qx = np.meshgrid(fold(nz) * (Lm / nz), fold(ny) * (Lm / ny), fold(nx) * (Lm / nx),
+                             indexing="ij")
+    b = np.rint(np.sqrt(qx ** 2 + qy ** 2 + qz ** 2)).astype(int)
+    keep = b > 0
+    keep[0, 0, 0] = False
+    sums = np.bincount(b[keep], S[keep])
+    cnt = np.bincount(b[keep])
+    return np.where(cnt > 0, sums / np.maximum(cnt, 1), 0.0)

@@ -45,6 +45,7 @@ EXPORTED = [
     "lb3_create", "lb3_destroy", "lb3_init", "lb3_set_psi", "lb3_set_replica", "lb3_set_strip", "lb3_step",
     "lb3_sync", "lb3_get_step", "lb3_density", "lb3_populations", "lb3_set_populations",
     "lb3_conserved", "lb3_sk_config", "lb3_sk_reset", "lb3_structure_factor_axes",
+    "lb3_sk_full", "lb3_structure_factor", "lb3_sk_moments",
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
     "lb_nn_to_bf16", "lb_nn_flux_div", "lb_nn_coarse_momentum", "lb_nn_expand_channel",
@@ -143,6 +144,9 @@ def bind(L):
         "lb3_destroy": (None, [P]),
         "lb3_init": (C.c_int, [P, C.c_double, C.c_uint64, C.c_double]),
         "lb3_set_psi": (C.c_int, [P, C.c_int, C.c_double, C.c_double]),
+        "lb3_sk_full": (C.c_int, [P, C.c_int]),
+        "lb3_structure_factor": (C.c_int, [P, _D, C.c_int, C.POINTER(C.c_longlong)]),
+        "lb3_sk_moments": (C.c_int, [P, _D]),
         "lb3_set_replica": (C.c_int, [P, C.c_uint32]),
         "lb3_set_strip": (C.c_int, [P, C.c_int]),
         "lb3_step": (C.c_int, [P, C.c_int]),

@@ -27,6 +27,7 @@
 
 #include "lbsc.h"
 #include "lbsc_device.cuh"
+#include "lbsc_fft.cuh"
 #include "lbsc_internal.cuh"
 
 namespace lbsc {
@@ -519,6 +520,128 @@ int grid_for(size_t n) {
     return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
 
+// ---------------------------------------------------------------------------
+// Full 3D structure factor: the density sample [nz][ny][nx] is transformed
+// along x (two real rows per complex transform, half spectrum [nz][ny][ldx]),
+// then along y and z in place by fft_lines_kernel, whose last pass adds
+// |X(k)|^2 / N to the FP64 sums.  Power-of-two sizes.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void sk3_rows_kernel(const T *__restrict__ drho, typename C2<T>::t *__restrict__ spec,
+                                const typename C2<T>::t *__restrict__ tw, int nx, int log2nx,
+                                int ldx) {
+    sk_rows_block<T>(drho, spec, tw, nx, log2nx, ldx, blockIdx.x);
+}
+
+// Length-n transforms of `cpb` neighbouring lines of plane blockIdx.y (line c
+// holds data[c + j stride], j < n; lines c0 .. c0 + cpb - 1 of the nlines of
+// the plane).  Without acc the result is written back; with acc, |X|^2 inv_n
+// is added at the same index for the lines of a real half spectrum
+// (c % ldx < hx).
+template <typename T>
+__global__ void fft_lines_kernel(typename C2<T>::t *__restrict__ data, int n, int log2n,
+                                 size_t stride, size_t nlines, size_t plane, int cpb,
+                                 const typename C2<T>::t *__restrict__ tw,
+                                 double *__restrict__ acc, double inv_n, int ldx, int hx) {
+    using CT = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT *s = reinterpret_cast<CT *>(smem_raw);
+    data += (size_t)blockIdx.y * plane;
+    const size_t c0 = (size_t)blockIdx.x * cpb;
+    const int total = cpb * n;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e % cpb, j = e / cpb;
+        CT v;
+        if (c0 + c < nlines) {
+            v = data[c0 + c + (size_t)j * stride];
+        } else {
+            v.x = T(0);
+            v.y = T(0);
+        }
+        s[c * n + (__brev((unsigned)j) >> (32 - log2n))] = v;
+    }
+    __syncthreads();
+    fft_smem<CT>(s, n, log2n, cpb, tw);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e % cpb, k = e / cpb;
+        if (c0 + c >= nlines) continue;
+        const size_t idx = c0 + c + (size_t)k * stride;
+        const CT v = s[c * n + k];
+        if (acc) {
+            if ((int)((c0 + c) % ldx) < hx) {
+                const double re = (double)v.x, im = (double)v.y;
+                acc[(size_t)blockIdx.y * plane + idx] += (re * re + im * im) * inv_n;
+            }
+        } else {
+            data[idx] = v;
+        }
+    }
+}
+
+// Radial bins over the full k cube from the half spectrum: b = round(|q|),
+// q_a = (wave number index on axis a) x max(n) / n_a; a kx column with
+// 0 < kx < nx/2 stands for two modes (k and -k).  k = 0 excluded.
+__global__ void sk3_bins_kernel(const double *__restrict__ acc, double inv_count,
+                                double *__restrict__ bins, double *__restrict__ counts, int nbins,
+                                int nx, int ny, int nz, int ldx) {
+    const int hx = nx / 2 + 1;
+    const size_t total = (size_t)hx * ny * nz;
+    const double L = (double)max(nx, max(ny, nz));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e % hx);
+        const size_t r = e / hx;
+        const int ky = (int)(r % ny), kz = (int)(r / ny);
+        if (kx == 0 && ky == 0 && kz == 0) continue;
+        const int my = ky <= ny / 2 ? ky : ky - ny, mz = kz <= nz / 2 ? kz : kz - nz;
+        const double qx = (double)kx * (L / nx), qy = (double)my * (L / ny),
+                     qz = (double)mz * (L / nz);
+        const int b = (int)rint(sqrt(qx * qx + qy * qy + qz * qz));
+        if (b >= nbins) continue;
+        const double w = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
+        atomicAdd(&bins[b], w * acc[((size_t)kz * ny + ky) * ldx + kx] * inv_count);
+        atomicAdd(&counts[b], w);
+    }
+}
+
+// (sum_k S(k), sum_k |k| S(k)) over the full k cube, k = 0 excluded, |k| =
+// 2 pi sqrt((kx/nx)^2 + (ky/ny)^2 + (kz/nz)^2) with folded indices.  One
+// block, fixed summation order.
+__global__ void __launch_bounds__(256)
+sk3_moments_kernel(const double *__restrict__ acc, double inv_count, int nx, int ny, int nz,
+                   int ldx, double *__restrict__ out) {
+    const int hx = nx / 2 + 1;
+    const size_t total = (size_t)hx * ny * nz;
+    double s0 = 0.0, s1 = 0.0;
+    for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int kx = (int)(e % hx);
+        const size_t r = e / hx;
+        const int ky = (int)(r % ny), kz = (int)(r / ny);
+        if (kx == 0 && ky == 0 && kz == 0) continue;
+        const int my = ky <= ny / 2 ? ky : ky - ny, mz = kz <= nz / 2 ? kz : kz - nz;
+        const double w = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
+        const double S = acc[((size_t)kz * ny + ky) * ldx + kx] * inv_count;
+        const double qx = (double)kx / nx, qy = (double)my / ny, qz = (double)mz / nz;
+        s0 += w * S;
+        s1 += w * S * 6.283185307179586 * sqrt(qx * qx + qy * qy + qz * qz);
+    }
+    __shared__ double sh0[256], sh1[256];
+    sh0[threadIdx.x] = s0;
+    sh1[threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh0[threadIdx.x] += sh0[threadIdx.x + o];
+            sh1[threadIdx.x] += sh1[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh0[0];
+        out[1] = sh1[0];
+    }
+}
+
 }  // namespace
 }  // namespace lbsc
 
@@ -542,6 +665,13 @@ struct lb3_ctx {
     double *d_acc = nullptr;       // axis S(k) sums [nx/2 + ny/2 + nz/2]
     double *d_io = nullptr;        // n doubles for read-outs
     float2 *d_ring = nullptr;      // [1024] (cos, sin) of the noise ring angles
+    bool sk_full = false;          // full 3D S(k) on sampling steps
+    int ldx3 = 0;                  // padded half-spectrum row (nx / 2 + 1 -> multiple of 4)
+    void *d_spec = nullptr;        // complex [nz][ny][ldx3] (storage precision)
+    double *d_acc3 = nullptr;      // FP64 sums of |X|^2 / N, [nz][ny][ldx3]
+    void *d_tw = nullptr;          // twiddles for nx, ny, nz (nx/2 + ny/2 + nz/2 complex)
+    double *d_bins = nullptr;      // read-out scratch: bins, counts (2 nbins_cap) + 2 moments
+    int nbins_cap = 0;
     int sk_every = 0;
     long long sk_start = 0, sk_count = 0, t = 0;
     uint64_t seed = 0;
@@ -618,6 +748,47 @@ int step3_once(lb3_ctx *h, bool sample) {
     return LB_OK;
 }
 
+// Lines per block of a length-n transform: as many as fit 128 KB (at most 64).
+int lines_per_block(int n, size_t csize) {
+    int cpb = 64;
+    while (cpb > 1 && (size_t)cpb * n * csize > 128 * 1024) cpb >>= 1;
+    return cpb;
+}
+
+template <typename T>
+int sample_full3(lb3_ctx *h) {
+    using CT = typename C2<T>::t;
+    const int nx = h->nx, ny = h->ny, nz = h->nz, ldx = h->ldx3, hx = nx / 2 + 1;
+    const CT *twx = (const CT *)h->d_tw, *twy = twx + nx / 2, *twz = twy + ny / 2;
+    CT *spec = (CT *)h->d_spec;
+    // x: two real rows per block over the nz ny rows
+    const size_t row_smem = (size_t)nx * sizeof(CT);
+    L3_CHECK(cudaFuncSetAttribute(sk3_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)row_smem));
+    const int rthreads = nx / 2 < 512 ? (nx / 2 < 32 ? 32 : nx / 2) : 512;
+    sk3_rows_kernel<T><<<nz * ny / 2, rthreads, row_smem, h->stream>>>(
+        (const T *)h->drho, spec, twx, nx, ilog2(nx), ldx);
+    L3_CHECK(cudaGetLastError());
+    L3_CHECK(cudaFuncSetAttribute(fft_lines_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  128 * 1024));
+    // y: in place, the hx columns of each z plane
+    int cpb = lines_per_block(ny, sizeof(CT));
+    dim3 gy((hx + cpb - 1) / cpb, nz);
+    fft_lines_kernel<T><<<gy, 512, (size_t)cpb * ny * sizeof(CT), h->stream>>>(
+        spec, ny, ilog2(ny), (size_t)ldx, (size_t)hx, (size_t)ny * ldx, cpb, twy, nullptr, 0.0,
+        ldx, hx);
+    L3_CHECK(cudaGetLastError());
+    // z: over all (y, kx) lines, adding |X|^2 / N
+    cpb = lines_per_block(nz, sizeof(CT));
+    const size_t nl = (size_t)ny * ldx;
+    dim3 gz((unsigned)((nl + cpb - 1) / cpb), 1);
+    fft_lines_kernel<T><<<gz, 512, (size_t)cpb * nz * sizeof(CT), h->stream>>>(
+        spec, nz, ilog2(nz), nl, nl, 0, cpb, twz, h->d_acc3, 1.0 / ((double)nx * ny * nz), ldx,
+        hx);
+    L3_CHECK(cudaGetLastError());
+    return LB_OK;
+}
+
 int sample3(lb3_ctx *h) {
     double *px = h->d_prof, *py = px + (size_t)h->nz * h->nx, *pz = py + (size_t)h->nz * h->ny;
     if (h->precision == LB_FP32)
@@ -630,6 +801,10 @@ int sample3(lb3_ctx *h) {
     axis_dft3_kernel<<<1, 512, (size_t)(h->nx + h->ny + h->nz) * sizeof(double), h->stream>>>(
         px, py, pz, h->nx, h->ny, h->nz, h->d_acc);
     L3_CHECK(cudaGetLastError());
+    if (h->sk_full) {
+        const int rc = h->precision == LB_FP32 ? sample_full3<float>(h) : sample_full3<double>(h);
+        if (rc) return rc;
+    }
     h->sk_count += 1;
     return LB_OK;
 }
@@ -655,6 +830,10 @@ void free3(lb3_ctx *h) {
     cudaFree(h->d_acc);
     cudaFree(h->d_io);
     cudaFree(h->d_ring);
+    cudaFree(h->d_spec);
+    cudaFree(h->d_acc3);
+    cudaFree(h->d_tw);
+    cudaFree(h->d_bins);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -747,6 +926,9 @@ int lb3_init(lb3_ctx *h, double rho0, uint64_t seed, double init_amp) {
                                  h->stream));
         h->sk_count = 0;
     }
+    if (h->d_acc3)
+        L3_CHECK(cudaMemsetAsync(h->d_acc3, 0, (size_t)h->nz * h->ny * h->ldx3 * sizeof(double),
+                                 h->stream));
     h->inited = true;
     return LB_OK;
 }
@@ -913,8 +1095,105 @@ int lb3_sk_reset(lb3_ctx *h) {
         L3_CHECK(cudaMemsetAsync(h->d_acc, 0, (h->nx / 2 + h->ny / 2 + h->nz / 2) * sizeof(double),
                                  h->stream));
     }
+    if (h->d_acc3)
+        L3_CHECK(cudaMemsetAsync(h->d_acc3, 0, (size_t)h->nz * h->ny * h->ldx3 * sizeof(double),
+                                 h->stream));
     h->sk_count = 0;
     return LB_OK;
+}
+
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int lb3_sk_full(lb3_ctx *h, int enable) {
+    if (!h) return LB_ERR_ARG;
+    if (!enable) {
+        h->sk_full = false;
+        return LB_OK;
+    }
+    if (!pow2(h->nx) || !pow2(h->ny) || !pow2(h->nz) || h->nx > 16384 || h->ny > 16384 ||
+        h->nz > 16384)
+        return LB_ERR_UNSUPPORTED;
+    if (!h->d_acc) return LB_ERR_STATE;      // lb3_sk_config first
+    L3_CHECK(cudaSetDevice(h->dev));
+    if (!h->d_acc3) {
+        const size_t cs = h->precision == LB_FP32 ? sizeof(float2) : sizeof(double2);
+        h->ldx3 = ((h->nx / 2 + 1) + 3) / 4 * 4;
+        const size_t ne = (size_t)h->nz * h->ny * h->ldx3;
+        cudaError_t e = cudaMalloc(&h->d_spec, ne * cs);
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_acc3, ne * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_tw, (size_t)(h->nx + h->ny + h->nz) / 2 * cs);
+        if (e != cudaSuccess) {
+            cudaFree(h->d_spec);
+            cudaFree(h->d_acc3);
+            cudaFree(h->d_tw);
+            h->d_spec = h->d_tw = nullptr;
+            h->d_acc3 = nullptr;
+            return e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA;
+        }
+        L3_CHECK(cudaMemsetAsync(h->d_spec, 0, ne * cs, h->stream));
+        L3_CHECK(cudaMemsetAsync(h->d_acc3, 0, ne * sizeof(double), h->stream));
+        const int prec = h->precision == LB_FP32 ? 0 : 1;
+        char *tw = (char *)h->d_tw;
+        L3_CHECK(launch_twiddles(prec, tw, h->nx, h->stream));
+        L3_CHECK(launch_twiddles(prec, tw + (size_t)h->nx / 2 * cs, h->ny, h->stream));
+        L3_CHECK(launch_twiddles(prec, tw + (size_t)(h->nx + h->ny) / 2 * cs, h->nz, h->stream));
+    }
+    h->sk_full = true;
+    return LB_OK;
+}
+
+static int bins_scratch3(lb3_ctx *h, int nbins) {
+    if (h->d_bins && h->nbins_cap >= nbins) return LB_OK;
+    cudaFree(h->d_bins);
+    h->d_bins = nullptr;
+    h->nbins_cap = 0;
+    if (cudaMalloc(&h->d_bins, (2 * (size_t)nbins + 2) * sizeof(double)) != cudaSuccess)
+        return LB_ERR_NOMEM;
+    h->nbins_cap = nbins;
+    return LB_OK;
+}
+
+int lb3_structure_factor(lb3_ctx *h, double *host_bins, int nbins, long long *nsamples_out) {
+    if (!h || !host_bins || nbins < 1) return LB_ERR_ARG;
+    if (!h->d_acc3) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    int rc = bins_scratch3(h, nbins);
+    if (rc) return rc;
+    double *bins = h->d_bins, *counts = bins + nbins;
+    L3_CHECK(cudaMemsetAsync(bins, 0, 2 * (size_t)nbins * sizeof(double), h->stream));
+    const double inv = h->sk_count ? 1.0 / (double)h->sk_count : 0.0;
+    const size_t total = (size_t)(h->nx / 2 + 1) * h->ny * h->nz;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    sk3_bins_kernel<<<blocks, 256, 0, h->stream>>>(h->d_acc3, inv, bins, counts, nbins, h->nx,
+                                                   h->ny, h->nz, h->ldx3);
+    L3_CHECK(cudaGetLastError());
+    double *tmp = new (std::nothrow) double[2 * (size_t)nbins];
+    if (!tmp) return LB_ERR_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(tmp, bins, 2 * (size_t)nbins * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    rc = e == cudaSuccess ? sync3(h) : LB_ERR_CUDA;
+    if (rc == LB_OK)
+        for (int b = 0; b < nbins; ++b)
+            host_bins[b] = tmp[nbins + b] > 0.0 ? tmp[b] / tmp[nbins + b] : 0.0;
+    delete[] tmp;
+    if (rc) return rc;
+    if (nsamples_out) *nsamples_out = h->sk_count;
+    return LB_OK;
+}
+
+int lb3_sk_moments(lb3_ctx *h, double *host_out2) {
+    if (!h || !host_out2) return LB_ERR_ARG;
+    if (!h->d_acc3) return LB_ERR_STATE;
+    L3_CHECK(cudaSetDevice(h->dev));
+    int rc = bins_scratch3(h, 1);
+    if (rc) return rc;
+    double *m = h->d_bins + 2 * (size_t)h->nbins_cap;
+    const double inv = h->sk_count ? 1.0 / (double)h->sk_count : 0.0;
+    sk3_moments_kernel<<<1, 256, 0, h->stream>>>(h->d_acc3, inv, h->nx, h->ny, h->nz, h->ldx3, m);
+    L3_CHECK(cudaGetLastError());
+    L3_CHECK(cudaMemcpyAsync(host_out2, m, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return sync3(h);
 }
 
 int lb3_structure_factor_axes(lb3_ctx *h, double *host_out, long long *nsamples_out) {

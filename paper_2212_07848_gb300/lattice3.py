@@ -93,3 +93,27 @@ class Lattice3:
         self._ck(abi.load().lb3_structure_factor_axes(self._h, out, C.byref(n)),
                  "lb3_structure_factor_axes")
         return out, n.value
+
+    def sk_full(self, enable=True):
+        """Accumulate the full 3D S(k) on the sampling steps of sk_config
+        (power-of-two sizes)."""
+        self._ck(abi.load().lb3_sk_full(self._h, 1 if enable else 0), "lb3_sk_full")
+
+    def structure_factor(self, nbins):
+        """(radial means of the full S(k) [nbins], nsamples)."""
+        out = np.empty(nbins)
+        n = C.c_longlong(0)
+        self._ck(abi.load().lb3_structure_factor(self._h, out, int(nbins), C.byref(n)),
+                 "lb3_structure_factor")
+        return out, n.value
+
+    def sk_moments(self):
+        """(sum_k S, sum_k |k| S) of the mean full S(k), k != 0."""
+        out = np.empty(2)
+        self._ck(abi.load().lb3_sk_moments(self._h, out), "lb3_sk_moments")
+        return out
+
+    def domain_size(self):
+        """L = 2 pi sum_k S / sum_k |k| S of the mean full S(k)."""
+        m = self.sk_moments()
+        return float(2.0 * np.pi * m[0] / m[1]) if m[1] > 0 else float("nan")

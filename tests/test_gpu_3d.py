@@ -113,3 +113,53 @@ def test_fp32_replicas_match_eq16_on_axes():
     sel = m >= 2
     dev = np.abs(mean - th)
     assert ((dev <= 0.03 * th) | (dev <= 4 * sem))[sel].all(), np.round(mean / th - 1, 3)
+
+
+def test_full_structure_factor_matches_oracle():
+    """The full 3D S(k) (FFTs along x, y, z on the device) in FP64 against the
+    oracle's separable DFT on the same noise: radial shells and the first
+    moments behind L = 2 pi sum S / sum |k| S."""
+    nx, ny, nz = 32, 8, 8
+    g, o = _pair(nx, ny, nz, -3.6, 1.0, 1e-4, "fp64", LN2, 5, 0.0)
+    g.sk_config(1, 20)
+    g.sk_full()
+    o.sk_config(1, 20)
+    o.sk_full()
+    g.step(60)
+    o.step(60)
+    So, no = o.structure_factor_full()
+    ref = O.radial_bins3(So)
+    got, ng = g.structure_factor(len(ref))
+    assert ng == no == 41
+    assert np.abs(got - ref).max() < 1e-9 * ref.max()
+    fold = lambda n: np.where(np.arange(n) <= n // 2, np.arange(n), np.arange(n) - n)
+    kz, ky, kx = np.meshgrid(fold(nz) / nz, fold(ny) / ny, fold(nx) / nx, indexing="ij")
+    kabs = 2 * np.pi * np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    m = g.sk_moments()
+    assert abs(m[0] - So.sum()) < 1e-9 * So.sum()
+    assert abs(m[1] - (kabs * So).sum()) < 1e-9 * (kabs * So).sum()
+
+
+def test_full_structure_factor_fp32_one_sample_matches_fft():
+    """FP32, 64^3: one sample of the device S(k) against numpy's FFT of the
+    lattice's own density at that step (radial shells, domain size)."""
+    from paper_2212_07848_gb300.lattice3 import Lattice3
+    n, T = 64, 200
+    g = Lattice3(n, n, n, -3.6, 1.0, 1e-5)
+    g.init(LN2, 11, 0.01)
+    g.sk_config(1, T)
+    g.sk_full()
+    g.step(T)
+    rho = g.density()
+    S = np.abs(np.fft.fftn(rho - rho.mean())) ** 2 / rho.size
+    ref = O.radial_bins3(S)
+    got, ns = g.structure_factor(len(ref))
+    assert ns == 1
+    rel = np.abs(got[1:] - ref[1:]) / ref[1:]
+    assert rel.max() < 1e-3, rel.max()
+    fold = np.where(np.arange(n) <= n // 2, np.arange(n), np.arange(n) - n) / n
+    kz, ky, kx = np.meshgrid(fold, fold, fold, indexing="ij")
+    kabs = 2 * np.pi * np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    L_ref = 2 * np.pi * S.sum() / (kabs * S).sum()
+    assert abs(g.domain_size() / L_ref - 1.0) < 1e-4
+    g.close()

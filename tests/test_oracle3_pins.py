@@ -224,3 +224,41 @@ def test_step_sites_equals_full_step():
     zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     got = O.step_sites3(nx, ny, nz, G, tau, kT, seed, 2, f_in, xx.ravel(), yy.ravel(), zz.ravel())
     assert np.array_equal(got.T.reshape(19, nz, ny, nx), ref)
+
+
+def test_full_structure_factor_matches_fft_and_axes():
+    """The oracle's full 3D S(k) (three separable direct DFT passes): one
+    sample equals |FFT(delta rho)|^2 / N of the sampled density, and its axis
+    entries equal the oracle's axis S(k) over several samples."""
+    nx, ny, nz = 8, 6, 4
+    o = O.OracleLattice3(nx, ny, nz, -3.6, 1.0, 1e-4)
+    o.init(LN2, 9, 0.01)
+    o.sk_full()
+    o.sk_config(1, 5)
+    o.step(5)                                   # one sample, of the state after step 5
+    S, n = o.structure_factor_full()
+    assert n == 1
+    rho = o.density()
+    ref = np.abs(np.fft.fftn(rho - rho.mean())) ** 2 / rho.size
+    assert np.abs(S - ref).max() < 1e-12 * ref.max()
+    o.step(20)
+    S, n = o.structure_factor_full()
+    Sa, na = o.structure_factor_axes()
+    assert n == na == 21
+    axes = np.concatenate([S[0, 0, 1:nx // 2 + 1], S[0, 1:ny // 2 + 1, 0], S[1:nz // 2 + 1, 0, 0]])
+    assert np.abs(axes - Sa).max() < 1e-12 * Sa.max()
+
+
+def test_ideal_gas_full_structure_factor_is_flat():
+    """G = 0: every radial shell of the full S(k) approaches rho0 kT / c_s^2."""
+    L, kT, rho0 = 8, 1e-4, 1.0
+    o = O.OracleLattice3(L, L, L, 0.0, 1.0, kT)
+    o.init(rho0, 4)
+    o.sk_full()
+    o.sk_config(1, 200)
+    o.step(1200)
+    S, n = o.structure_factor_full()
+    bins = O.radial_bins3(S)[1:]
+    ref = rho0 * kT * 3.0
+    assert abs(bins.mean() / ref - 1.0) < 0.04, bins / ref
+    assert np.abs(bins / ref - 1.0).max() < 0.1
