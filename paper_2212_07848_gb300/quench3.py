@@ -92,22 +92,42 @@ def classify_topology3(rho, threshold=None, min_contrast=0.2):
 
 
 def run_quench3(n, G, rho0, kT=1e-7, steps=20000, seed=100, tau=1.0, psi_kind=0, psi_p1=0.0,
-                psi_p2=0.0, init_amp=1e-3, precision="fp32"):
+                psi_p2=0.0, init_amp=1e-3, precision="fp32", every=0, nbins=None):
     """Quench an n^3 lattice from rho0 (plus a density kick of amplitude
     init_amp) and return the final density, its topology, the liquid
-    fraction and the mass drift."""
+    fraction and the mass drift; with `every` > 0 (n a power of two) also the
+    instantaneous radial S(k, t) and the domain size L(t) = 2 pi sum S /
+    sum |k| S of the full 3D S(k) every `every` steps."""
     lat = Lattice3(n, n, n, G, tau, kT, precision=precision, psi_kind=psi_kind, psi_p1=psi_p1,
                    psi_p2=psi_p2)
     lat.init(rho0, seed, init_amp)
     m0 = lat.conserved()[0]
-    lat.step(steps)
+    times, L, S = [], [], []
+    if every > 0:
+        nbins = nbins or int(np.ceil(np.sqrt(3.0) * n / 2)) + 1
+        lat.sk_config(every, every)
+        lat.sk_full()
+        done = 0
+        while done < steps:
+            lat.step(every)
+            done += every
+            bins, _ = lat.structure_factor(nbins)
+            times.append(done)
+            S.append(bins)
+            L.append(lat.domain_size())
+            lat.sk_reset()
+    else:
+        lat.step(steps)
     lat.sync()
     rho = lat.density()
     m1 = lat.conserved()[0]
     lat.close()
     topo, phi, comps = classify_topology3(rho)
-    return {"density": rho, "topology": topo, "liquid_fraction": phi, "components": comps,
-            "mass_drift": abs(m1 - m0) / m0}
+    out = {"density": rho, "topology": topo, "liquid_fraction": phi, "components": comps,
+           "mass_drift": abs(m1 - m0) / m0}
+    if every > 0:
+        out.update(t=np.array(times), L=np.array(L), S=np.array(S))
+    return out
 
 
 # Eq. (5) at T_hat = 0.8: with the lattice temperature c_s^2 = 1/3 and G = -3
@@ -140,6 +160,20 @@ def topology_sweep(densities, seeds, n=64, steps=10000, kT=1e-6, init_amp=1e-3):
     return table
 
 
+def growth_run(n_hat, n=128, steps=20000, every=500, seed=1, kT=1e-6, init_amp=1e-3):
+    """L(t) of one Eq. (5) quench at T_hat = 0.8 from the full 3D S(k); the
+    growth exponent is the log-log slope over the last decade of t."""
+    r = run_quench3(n, EQ5_G, n_hat * EQ5_NC, kT=kT, steps=steps, seed=seed, psi_kind=1,
+                    psi_p1=EQ5_TC, psi_p2=EQ5_NC, init_amp=init_amp, every=every)
+    t, L = r["t"], r["L"]
+    sel = t >= t[-1] / 10
+    slope = float(np.polyfit(np.log(t[sel]), np.log(L[sel]), 1)[0])
+    return {"n_hat": n_hat, "n": n, "seed": seed, "topology": r["topology"],
+            "L": {str(int(tt)): float(LL) for tt, LL in zip(t, L)
+                  if int(tt) in (500, 1000, 2000, 5000, 10000, 20000)},
+            "exponent_last_decade": slope, "mass_drift": r["mass_drift"]}
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -149,8 +183,17 @@ if __name__ == "__main__":
     ap.add_argument("--seeds", type=int, default=6)
     ap.add_argument("--densities", default="0.65,0.7,0.75,0.8,0.85,0.9,0.95,1.0,1.15,1.3,1.45,"
                                            "1.5,1.55,1.6,1.62,1.64,1.66")
+    ap.add_argument("--growth", action="store_true",
+                    help="L(t) from the full 3D S(k) instead of the topology sweep")
+    ap.add_argument("--every", type=int, default=500)
     a = ap.parse_args()
     dens = [float(x) for x in a.densities.split(",")]
-    res = topology_sweep(dens, range(1, a.seeds + 1), n=a.n, steps=a.steps)
-    for nh, r in res.items():
-        print(json.dumps({"n_hat": nh, **r}), flush=True)
+    if a.growth:
+        for nh in dens:
+            for s in range(1, a.seeds + 1):
+                print(json.dumps(growth_run(nh, n=a.n, steps=a.steps, every=a.every, seed=s)),
+                      flush=True)
+    else:
+        res = topology_sweep(dens, range(1, a.seeds + 1), n=a.n, steps=a.steps)
+        for nh, r in res.items():
+            print(json.dumps({"n_hat": nh, **r}), flush=True)
