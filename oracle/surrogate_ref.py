@@ -107,9 +107,10 @@ def net_loss(y, base, target, flux=False, jweight=None):
     return float(np.mean(d[0] ** 2) + jweight * (np.mean(d[1] ** 2) + np.mean(d[2] ** 2))), d
 
 
-def net_backward(x, w, acts, d, flux=False, jweight=None):
+def net_backward(x, w, acts, d, flux=False, jweight=None, want_dx=False):
     """Parameter gradients of net_loss by reverse-mode differentiation of
-    net_forward (chain rule layer by layer).  Returns (dw list, db list)."""
+    net_forward (chain rule layer by layer).  Returns (dw list, db list), and
+    with want_dx also the gradient with respect to the input x."""
     d0 = d[0] if jweight is not None else d
     if flux:
         dy = flux_div_backward(2.0 * d0 / d0.size, w[4].shape[1])
@@ -119,6 +120,12 @@ def net_backward(x, w, acts, d, flux=False, jweight=None):
     if jweight is not None:
         for a in (1, 2):
             dy[..., a + 1] += 2.0 * jweight * d[a] / d[a].size
+    return backward_from_dy(x, w, acts, dy, want_dx)
+
+
+def backward_from_dy(x, w, acts, dy, want_dx=False):
+    """Parameter gradients (and optionally the input gradient) of the network
+    for a given output gradient dy."""
     dw, db = [None] * 5, [None] * 5
     ins = [x, acts["p1"], acts["p2"], acts["u3"], acts["u4"]]
 
@@ -139,4 +146,41 @@ def net_backward(x, w, acts, d, flux=False, jweight=None):
     da1 = pool2_backward(conv3x3_dgrad(dz2, w[1]))
     dz1 = da1 * (acts["a1"] > 0)
     layer(0, dz1)
+    if want_dx:
+        return dw, db, conv3x3_dgrad(dz1, w[0])
     return dw, db
+
+
+def two_stride_loss(x0, w, b, base0, t1, t2):
+    """The loss of two surrogate strides in a row (plain increments): the
+    first prediction s1 = base0 + y0[..., 0] becomes the next input (channel
+    0 the field, channel 2 its increment, the other channels as in x0), and
+    L = mean((s1 - t1)^2) + mean((s1 + y1[..., 0] - t2)^2).  Returns
+    (L, intermediates for two_stride_backward)."""
+    y0, a0 = net_forward(x0, w, b)
+    inc0 = y0[..., 0]
+    s1 = base0 + inc0
+    x1 = np.array(x0, dtype=np.float64)
+    x1[..., 0] = s1
+    x1[..., 2] = inc0
+    y1, a1 = net_forward(x1, w, b)
+    p2 = s1 + y1[..., 0]
+    L = float(np.mean((s1 - t1) ** 2) + np.mean((p2 - t2) ** 2))
+    return L, dict(a0=a0, a1=a1, x1=x1, s1=s1, p2=p2)
+
+
+def two_stride_backward(x0, w, b, t1, t2, mid):
+    """Parameter gradients of two_stride_loss: the second stride's output
+    gradient, then through its input (channels 0 and 2) and its base (s1) into
+    the first stride's increment."""
+    s1, p2 = mid["s1"], mid["p2"]
+    n = s1.size
+    d2 = 2.0 * (p2 - t2) / n
+    dy1 = np.zeros(s1.shape + (w[4].shape[1],))
+    dy1[..., 0] = d2
+    dw1, db1, dx1 = backward_from_dy(mid["x1"], w, mid["a1"], dy1, want_dx=True)
+    dinc0 = 2.0 * (s1 - t1) / n + d2 + dx1[..., 0] + dx1[..., 2]
+    dy0 = np.zeros(s1.shape + (w[4].shape[1],))
+    dy0[..., 0] = dinc0
+    dw0, db0 = backward_from_dy(x0, w, mid["a0"], dy0)
+    return [a + c for a, c in zip(dw0, dw1)], [a + c for a, c in zip(db0, db1)]

@@ -106,3 +106,48 @@ def test_flux_divergence_definition_conservation_and_adjoint():
     lhs = np.sum(inc * d)
     rhs = np.sum(y * R.flux_div_backward(d, 4))
     assert abs(lhs - rhs) < 1e-12
+
+
+def test_input_gradient_and_two_stride_backward_match_finite_differences():
+    """The network's input gradient, and the gradient of the two-stride loss
+    (the first prediction fed back as the next input), against central
+    finite differences."""
+    x, w, b, base, tgt = _net(50)
+    t2 = _rand(tgt.shape, 53)
+    y, acts = R.net_forward(x, w, b)
+    _, d = R.net_loss(y, base, tgt)
+    _, _, dx = R.net_backward(x, w, acts, d, want_dx=True)
+    rng = np.random.default_rng(3)
+    h = 1e-5
+    for _ in range(6):
+        idx = tuple(int(rng.integers(s)) for s in x.shape)
+        old = x[idx]
+        x[idx] = old + h
+        lp, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        x[idx] = old - h
+        lm, _ = R.net_loss(R.net_forward(x, w, b)[0], base, tgt)
+        x[idx] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - dx[idx]) <= 1e-4 * abs(fd) + 1e-9, (idx, fd, dx[idx])
+    L, mid = R.two_stride_loss(x, w, b, base, tgt, t2)
+    dw, db = R.two_stride_backward(x, w, b, tgt, t2, mid)
+    for i in range(5):
+        for _ in range(3):
+            idx = tuple(int(rng.integers(s)) for s in w[i].shape)
+            old = w[i][idx]
+            w[i][idx] = old + h
+            lp, _ = R.two_stride_loss(x, w, b, base, tgt, t2)
+            w[i][idx] = old - h
+            lm, _ = R.two_stride_loss(x, w, b, base, tgt, t2)
+            w[i][idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - dw[i][idx]) <= 1e-4 * abs(fd) + 1e-9, (i, idx, fd, dw[i][idx])
+        j = int(rng.integers(b[i].size))
+        old = b[i][j]
+        b[i][j] = old + h
+        lp, _ = R.two_stride_loss(x, w, b, base, tgt, t2)
+        b[i][j] = old - h
+        lm, _ = R.two_stride_loss(x, w, b, base, tgt, t2)
+        b[i][j] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - db[i][j]) <= 1e-4 * abs(fd) + 1e-9, (i, j, fd, db[i][j])
