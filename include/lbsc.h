@@ -431,6 +431,10 @@ int lb_nn_coarse_momentum(const float *df, int nx, int ny, int f, double scale, 
  * channels are untouched.  LB_ERR_ARG unless ch (and ch + 2 with prev) < c. */
 int lb_nn_expand_channel(const float *src, const float *prev, void *out, int c, int ch, size_t n,
                          void *stream);
+/* dst[.][dch] += src[.][sch] for BF16 buffers dst [n][dc] and src [n][sc]
+ * (gradients gathered from several paths).  LB_ERR_ARG for a bad channel. */
+int lb_nn_add_channel(void *dst, int dc, int dch, const void *src, int sc, int sch, size_t n,
+                      void *stream);
 /* Block MSE of the residual d = base + y[.][0] - target over images
  * [nb][h][w]: *loss += weight * mean over block x block tiles of (tile mean
  * of d)^2, a measure of the error at wavelengths longer than the tile; dy

@@ -49,7 +49,7 @@ EXPORTED = [
     "lb_nn_conv3x3", "lb_nn_conv3x3_wgrad", "lb_nn_relu_mask", "lb_nn_pool2", "lb_nn_up2",
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
     "lb_nn_to_bf16", "lb_nn_flux_div", "lb_nn_coarse_momentum", "lb_nn_expand_channel",
-    "lb_nn_mse_channel", "lb_nn_mse_blocks", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
+    "lb_nn_mse_channel", "lb_nn_mse_blocks", "lb_nn_add_channel", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
     "lb_nn_status",
 ]
 
@@ -173,6 +173,7 @@ def bind(L):
         "lb_nn_wgrad_workspace": (C.c_size_t, [C.c_int] * 5),
         "lb_nn_flux_div": (C.c_int, [P, P] + [C.c_int] * 5 + [P]),
         "lb_nn_mse_blocks": (C.c_int, [P, C.c_int, P, P] + [C.c_int] * 4 + [C.c_double, P, P, P]),
+        "lb_nn_add_channel": (C.c_int, [P, C.c_int, C.c_int, P, C.c_int, C.c_int, C.c_size_t, P]),
         "lb_nn_coarse_momentum": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P, P]),
         "lb_nn_expand_channel": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_size_t, P]),
         "lb_nn_mse_channel": (C.c_int, [P, C.c_int, C.c_int, P, P, C.c_size_t, C.c_double, P, P,

@@ -424,6 +424,13 @@ __global__ void coarse_kernel(const float *__restrict__ df, int nx, int ny, int 
     }
 }
 
+// dst[.][dch] += src[.][sch] (BF16 channels of two [n][C] buffers).
+__global__ void add_channel_kernel(bf16 *__restrict__ dst, int dc, int dch,
+                                   const bf16 *__restrict__ src, int sc, int sch, size_t n) {
+    GRID_STRIDE(i, n) dst[i * dc + dch] = __float2bfloat16(__bfloat162float(dst[i * dc + dch]) +
+                                                            __bfloat162float(src[i * sc + sch]));
+}
+
 // Block MSE: the residual d = base + y[.][0] - target averaged over each
 // B x B block of each image [nb][h][w]; loss += weight * mean over blocks of
 // (block mean)^2 and dy[.][0] += its gradient, 2 weight mean_b / (nblocks B^2),
@@ -783,6 +790,14 @@ int lb_nn_coarse_grain(const float *df, int nx, int ny, int f, double scale, flo
     if (!df || !out || f < 1 || nx % f || ny % f || !(scale != 0.0)) return LB_ERR_ARG;
     coarse_kernel<<<blocks_for((size_t)(nx / f) * (ny / f)), 256, 0, (cudaStream_t)stream>>>(
         df, nx, ny, f, (float)scale, out);
+    NN_RET();
+}
+
+int lb_nn_add_channel(void *dst, int dc, int dch, const void *src, int sc, int sch, size_t n,
+                      void *stream) {
+    if (!dst || !src || dch < 0 || dch >= dc || sch < 0 || sch >= sc) return LB_ERR_ARG;
+    add_channel_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(
+        (bf16 *)dst, dc, dch, (const bf16 *)src, sc, sch, n);
     NN_RET();
 }
 

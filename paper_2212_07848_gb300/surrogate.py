@@ -136,8 +136,52 @@ class SurrogateNet:
     def out_c(self):
         return 1 if self.flux else 16
 
-    def backward(self, x):
-        """Accumulate parameter gradients from self.dy (dL/dy)."""
+    def twin(self):
+        """A second set of activation buffers on the same parameters (the
+        weights, their BF16 copies, biases and gradient sums are shared), for
+        training through two strides."""
+        t = object.__new__(SurrogateNet)
+        t.__dict__.update({k: v for k, v in self.__dict__.items()
+                           if k not in ("_stride_graph",)})
+        t._alloc(self.nb)
+        return t
+
+    def two_stride_loss_and_grad(self, x, base, t1, t2):
+        """Gradients of the two-stride loss mean((s1 - t1)^2) + mean((s1 +
+        inc1 - t2)^2), s1 = base + inc0, where the second stride's input is
+        the first prediction (channel 0 = s1, channel 2 = inc0): forward both
+        strides, backward the second (with its input gradient), gather the
+        gradient of inc0 (its own loss, the second loss through s1, and input
+        channels 0 and 2), backward the first.  Plain increments only.
+        Accumulates into the shared parameter gradients; returns the loss."""
+        if self.flux or self.momentum:
+            raise ValueError("two-stride training is for plain increments")
+        t = self.torch
+        if getattr(self, "_tw", None) is None or self._tw.nb != self.nb:
+            self._tw = self.twin()
+            self._x1 = t.empty_like(x)
+            self._dx1 = t.empty_like(x)
+            self._s1 = t.empty_like(base)
+        tw, x1, dx1, s1 = self._tw, self._x1, self._dx1, self._s1
+        L, npx = self.L, base.numel()
+        self.forward(x)
+        s1.copy_(base)
+        x1.copy_(x)
+        _check(L.lb_nn_residual(_p(s1), _p(self.y), 16, _p(x1), CIN, npx, None, self.s),
+               "residual")
+        tw.forward(x1)
+        loss = self.loss_and_grad(x, t1, base)
+        loss += tw.loss_and_grad(x1, t2, s1)
+        tw.backward(x1, dx=dx1)
+        for src, ch in ((tw.dy, 0), (dx1, 0), (dx1, 2)):
+            _check(L.lb_nn_add_channel(_p(self.dy), 16, 0, _p(src), 16, ch, npx, self.s),
+                   "add channel")
+        self.backward(x)
+        return loss
+
+    def backward(self, x, dx=None):
+        """Accumulate parameter gradients from self.dy (dL/dy); with `dx` (a
+        BF16 [nb][n][n][16] buffer) also write dL/dx, the input gradient."""
         n, L, nb, s = self.n, self.L, self.nb, self.s
         wg = lambda inp, dz, i, h: _check(L.lb_nn_conv3x3_wgrad(
             _p(inp), _p(dz), _p(self.dw[i]), _p(self.db[i]), nb, h, h, LAYERS[i][0], LAYERS[i][1],
@@ -162,6 +206,8 @@ class SurrogateNet:
         _check(L.lb_nn_pool2(_p(self.dp1), _p(self.da1), nb, n, n, 32, 1, s), "poolb")
         _check(L.lb_nn_relu_mask(_p(self.da1), _p(self.a1), _p(self.dz1), self.dz1.numel(), s), "relu")
         wg(x, self.dz1, 0, n)
+        if dx is not None:
+            dg(self.dz1, 0, dx, n)
 
     def zero_grad(self):
         for t in self.dw + self.db:
@@ -279,7 +325,7 @@ def advance(net, state, x, npx, mean=None):
 
 
 def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min=1, lr_end=None,
-          pushforward=0.0, pf_depth=1):
+          pushforward=0.0, pf_depth=1, two_stride=0.0):
     """Adam on random (trajectory, time) pairs of consecutive frames, the frame
     before each pair giving the last-increment input; the learning rate decays
     from `lr` to `lr_end` on a cosine (constant without `lr_end`).  With
@@ -288,6 +334,8 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
     input (the pushforward trick: the network learns to correct its own
     rollout errors); with pf_depth > 1 that advance is 1 .. pf_depth strides
     (uniform), so it also learns from errors compounded over several strides.
+    With probability `two_stride` an iteration instead trains through two
+    strides with gradients (two_stride_loss_and_grad; plain increments).
     Returns the losses logged every `log_every` iterations."""
     import torch
     L = net.L
@@ -306,7 +354,23 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
     rng = np.random.default_rng(seed)
     nf = frames.shape[1]
     losses = []
+    t2 = torch.empty((nb, m, m), dtype=torch.float32, device="cuda") if two_stride > 0 else None
     for it in range(iters):
+        if two_stride > 0.0 and rng.random() < two_stride:
+            for j in range(nb):
+                k = int(rng.choice(train_ids))
+                f = int(rng.integers(t_min, nf - 2))
+                base[j].copy_(frames[k, f])
+                tgt[j].copy_(frames[k, f + 1])
+                t2[j].copy_(frames[k, f + 2])
+                expand_state(L, frames[k, f], Gs[k], x[j], frames[k, f - 1] if f > 0 else None,
+                             net.s)
+            net.zero_grad()
+            loss = net.two_stride_loss_and_grad(x, base, tgt, t2)
+            _adam_step(net, it, iters, lr, lr_end)
+            if log_every and it % log_every == 0:
+                losses.append(float(loss.item()))
+            continue
         pf = pushforward > 0.0 and rng.random() < pushforward
         depth = (int(rng.integers(1, pf_depth + 1)) if pf_depth > 1 else 1) if pf else 0
         for j in range(nb):
@@ -326,13 +390,17 @@ def train(net, frames, Gs, train_ids, iters, lr=1e-3, seed=0, log_every=0, t_min
         net.forward(x)
         loss = net.loss_and_grad(x, tgt, base)
         net.backward(x)
-        if lr_end is None:
-            net.adam(lr)
-        else:
-            net.adam(lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(iters - 1, 1))))
+        _adam_step(net, it, iters, lr, lr_end)
         if log_every and it % log_every == 0:
             losses.append(float(loss.item()))
     return losses
+
+
+def _adam_step(net, it, iters, lr, lr_end):
+    if lr_end is None:
+        net.adam(lr)
+    else:
+        net.adam(lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(iters - 1, 1))))
 
 
 def one_step_mse(net, frames, Gs, ids, t_min=1):

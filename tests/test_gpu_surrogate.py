@@ -166,3 +166,35 @@ def test_training_is_reproducible():
         ws.append([w.clone() for w in net.w] + [b.clone() for b in net.b])
     for a, b in zip(*ws):
         assert torch.equal(a, b)
+
+
+def test_two_stride_gradients_match_reference():
+    """Training through two strides: the gradients of the two-stride loss
+    (the first prediction fed back as the second input) against the FP64
+    CPU reference."""
+    from paper_2212_07848_gb300.surrogate import LAYERS, SurrogateNet
+    n, nb = 64, 2
+    net = SurrogateNet(n, nb, seed=7)
+    g = torch.Generator(device="cpu").manual_seed(8)
+    for i in range(len(LAYERS)):
+        net.w[i].copy_(torch.randn(net.w[i].shape, generator=g).cuda()
+                       * math.sqrt(2.0 / (9 * LAYERS[i][0])) * (0.3 if i == 4 else 1.0))
+        net.wb[i].copy_(net.w[i].to(torch.bfloat16))
+        net.b[i].copy_(0.1 * torch.randn(net.b[i].shape, generator=g).cuda())
+    x = torch.randn((nb, n, n, 16), generator=g).to(torch.bfloat16).cuda()
+    base = x[..., 0].float().contiguous()
+    t1 = base + 0.3 * torch.randn((nb, n, n), generator=g).cuda()
+    t2 = t1 + 0.3 * torch.randn((nb, n, n), generator=g).cuda()
+    net.zero_grad()
+    loss = net.two_stride_loss_and_grad(x, base, t1, t2)
+    torch.cuda.synchronize()
+    w = [t.float().cpu().numpy().astype(np.float64) for t in net.wb]
+    b = [t.cpu().numpy().astype(np.float64) for t in net.b]
+    xr = x.float().cpu().numpy().astype(np.float64)
+    ref_loss, mid = R.two_stride_loss(xr, w, b, base.cpu().numpy(), t1.cpu().numpy(),
+                                      t2.cpu().numpy())
+    dw, db = R.two_stride_backward(xr, w, b, t1.cpu().numpy(), t2.cpu().numpy(), mid)
+    assert abs(float(loss.item()) - ref_loss) < 2e-2 * ref_loss
+    for i in range(len(LAYERS)):
+        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < 8e-2, i
+        assert _rel(net.db[i].cpu().numpy(), db[i]) < 8e-2, i
