@@ -262,3 +262,26 @@ def test_ideal_gas_full_structure_factor_is_flat():
     ref = rho0 * kT * 3.0
     assert abs(bins.mean() / ref - 1.0) < 0.04, bins / ref
     assert np.abs(bins / ref - 1.0).max() < 0.1
+
+
+def test_radial_bins3_on_a_known_cube():
+    """radial_bins3 of S = |q|^2 (q_a = folded index x max(n) / n_a) gives in
+    each shell the mean of |q|^2 over the modes with round(|q|) = b, counted by
+    brute force; k = 0 is left out."""
+    nx, ny, nz = 8, 4, 4
+    Lm = 8
+    S = np.zeros((nz, ny, nx))
+    shells = {}
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                q = np.array([(x if x <= nx // 2 else x - nx) * Lm / nx,
+                              (y if y <= ny // 2 else y - ny) * Lm / ny,
+                              (z if z <= nz // 2 else z - nz) * Lm / nz])
+                S[z, y, x] = q @ q
+                if (x, y, z) != (0, 0, 0):
+                    shells.setdefault(int(np.rint(np.sqrt(q @ q))), []).append(q @ q)
+    bins = O.radial_bins3(S)
+    for b, vals in shells.items():
+        assert abs(bins[b] - np.mean(vals)) < 1e-12, b
+    assert bins[0] == 0.0
