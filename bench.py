@@ -217,7 +217,7 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
     trajectories at size^2 (G ~ U[-5.2, -4.4], rho0 = ln2, kT = 1e-6)
     coarse-grained 4x every `stride` steps; the network is trained (Adam,
     cosine learning rate, pushforward over one or two strides) on all but `ntest`, which score
-    it: one-stride MSE against persistence, and rollouts judged by the solver
+    it: one-stride MSE against persistence, and rollouts scored by the solver
     on the ensemble-mean L(t) and radial S(k, t), next to the same metrics for
     the solver itself continued on an independent noise stream (the floor of
     any predictor of a stochastic run).  The speedup is the solver's
@@ -247,7 +247,7 @@ def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=90
             "Sk_peak_max_rel_err": ev["Sk_peak_max_rel_err"],
             "Sk_l1_rel_err": ev["Sk_l1_rel_err"]}
     # the floor: the solver itself continued from the same states on an
-    # independent noise stream, judged by the same ensemble metrics
+    # independent noise stream, scored by the same ensemble metrics
     floor = {}
     for f0, nroll in ((5, 10), (10, 20)):
         ev = S.solver_reseeded(frames, Gs, test_ids, f0, nroll, size, stride, seed * 1000)

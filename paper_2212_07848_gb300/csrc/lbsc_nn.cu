@@ -4,7 +4,7 @@
 // operator (pooling, upsampling, skip sums, ReLU mask, coarse-graining of the
 // lattice density, MSE loss, Adam).  The surrogate advances the coarse
 // density of a quench by a fixed stride; the plain lattice Boltzmann step
-// stays the reference it is judged against.
+// stays the reference it is scored against.
 //
 // The forward convolution runs on tcgen05 (lbsc_nn_tc.cu) for its output
 // channel counts; the mma.sync kernels here serve the input gradient, the

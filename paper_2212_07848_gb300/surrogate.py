@@ -583,7 +583,7 @@ def solver_reseeded(frames, Gs, ids, f0, nroll, size, stride, seed0, coarse=4, k
 
 
 def evaluate_rollouts(net, frames, Gs, ids, f0, nroll):
-    """Judge the surrogate against the solver: from frame f0 of each trajectory
+    """Score the surrogate against the solver: from frame f0 of each trajectory
     in `ids` (with frame f0 - 1 for the increment input) roll out `nroll`
     strides and compare with the solver's frames f0+1 .. f0+nroll.  Returns
     the ensemble-mean domain size L(t) of both, their largest relative gap,
