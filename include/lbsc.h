@@ -52,7 +52,7 @@ extern "C" {
 #define LB_ERR_CUDA (-2)         /* a CUDA runtime call or launch failed    */
 #define LB_ERR_NONFINITE (-3)    /* the step produced NaN or Inf            */
 #define LB_ERR_TIMEOUT (-4)      /* a bounded device wait ran out           */
-#define LB_ERR_UNSUPPORTED (-5)  /* valid request this build cannot serve   */
+#define LB_ERR_UNSUPPORTED (-5)  /* valid request this library cannot serve */
 #define LB_ERR_IO (-6)           /* file open/read/write failed             */
 #define LB_ERR_NOMEM (-7)        /* host or device allocation failed        */
 #define LB_ERR_STATE (-8)        /* call out of order (e.g. step before init)*/

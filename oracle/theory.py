@@ -199,7 +199,7 @@ def stencil_vectors(order):
 
 # --------------------------------------------------------------------------
 # Static structure factor.  Eq. (15)-(16) in the paper's convention, and the
-# same on lattice axes in this build's convention for any stencil.
+# same on lattice axes in this library's convention for any stencil.
 # --------------------------------------------------------------------------
 def sk_exact_paper(k, n0, T, psi0, dpsi0, kT):
     """Eq. (16) verbatim (paper convention: c_s0^2 = dp/dn with p of Eq. (2),
@@ -218,7 +218,7 @@ def sk_axis(k, rho0, G, kT, order=4, kind=0, p1=0.0, p2=0.0):
     """S(k) for a wave vector along a lattice axis:
         S = rho0 kT / (c_s^2 [1 + G psi0 psi0' s(k) / (2 tan(k/2))]).
     For E4, s(k) = sin k and s/(2 tan(k/2)) = (1 + cos k)/2, which is Eq. (16)
-    mapped to this build's convention.  For E6/E8 this is the reading used
+    mapped to this library's convention.  For E6/E8 this is the reading used
     for the longer-range one-dimensional projection."""
     k = np.asarray(k, dtype=np.float64)
     pp = psi(rho0, kind, p1, p2) * dpsi(rho0, kind, p1, p2)
