@@ -227,7 +227,7 @@ def sk_axis(k, rho0, G, kT, order=4, kind=0, p1=0.0, p2=0.0):
 
 
 def pn_lattice(rho_line, G, kind=0, p1=0.0, p2=0.0):
-    """Normal pressure across a flat interface, Eq. (14), in this build's
+    """Normal pressure across a flat interface, Eq. (14), in this library's
     convention (nearest-neighbour 1D projection of E4):
         P_N(x) = rho c_s^2 + (G c_s^2 / 4) psi(x) [psi(x+1) + psi(x-1)]."""
     ps = psi(rho_line, kind, p1, p2)
