@@ -26,11 +26,11 @@
  *     1/12 (diagonals), normalised to sum_a w_a e_ax^2 = 1 (fourth-order
  *     isotropic), so p = rho c_s^2 + (G c_s^2 / 2) psi^2 as in 2D;
  *   - random numbers: Philox4x32-10, counter (site, step, replica, block),
- *     site = x + nx (y + ny z); blocks 0, 1, 2 give the 15 normals by the ring
- *     Box-Muller (radius words r0, r1, r2; angle indices bits 0-9, 10-19,
- *     20-29 of r3): block 0 -> modes 4..9, block 1 -> modes 10..15, block 2 ->
- *     modes 16, 17 (pair 1) and 18 (cosine of pair 2); block 3 of step 0 drives
- *     the optional initial density kick (plain Box-Muller pair (r0, r1));
+ *     site = x + nx (y + ny z); blocks 0 and 1 give the 15 normals by the ring
+ *     Box-Muller, one pair per 32-bit word (radius from the high 22 bits, angle
+ *     index from the low 10): block 0 -> modes 4..11, block 1 -> modes 12..17
+ *     and 18 (cosine of its last pair); block 3 of step 0 drives the optional
+ *     initial density kick (plain Box-Muller pair (r0, r1));
  *   - S(k) on the three lattice axes: S(k e_a) = |sum_x drho(x) e^{-i k x_a}|^2 / N
  *     with drho = rho - mean(rho), k = 2 pi m / n_a, m = 1 .. n_a/2.
  */
@@ -132,28 +132,28 @@ static void draw3(const or3_params *p, uint32_t site, uint32_t step, uint32_t bl
 
 static double unif(uint32_t r) { return ((double)r + 0.5) * (1.0 / 4294967296.0); }
 
-static void ring_pair(uint32_t ra, uint32_t a, double *z0, double *z1) {
-    double rad = sqrt(-2.0 * log(unif(ra)));
-    double th = 2.0 * M_PI * ((double)(a & 1023u) + 0.5) / 1024.0;
+/* One ring pair from a single word: the radius from its high 22 bits,
+ * u = ((w >> 10) + 1/2) 2^-22, the angle index from its low 10 bits. */
+static void ring_pair22(uint32_t w, double *z0, double *z1) {
+    double u = ((double)(w >> 10) + 0.5) * (1.0 / 4194304.0);
+    double rad = sqrt(-2.0 * log(u));
+    double th = 2.0 * M_PI * ((double)(w & 1023u) + 0.5) / 1024.0;
     *z0 = rad * cos(th);
     *z1 = rad * sin(th);
 }
 
-/* The 15 thermal normals of a site and step: z[k - 4] for modes k = 4..18. */
+/* The 15 thermal normals of a site and step: z[k - 4] for modes k = 4..18,
+ * one ring pair per Philox word: block 0 words 0..3 -> modes (4,5), (6,7),
+ * (8,9), (10,11); block 1 words 0..2 -> (12,13), (14,15), (16,17), word 3 ->
+ * mode 18 (the cosine of its pair). */
 static void site_normals3(const or3_params *p, uint32_t site, uint32_t t, double z[15]) {
     uint32_t r[4];
     double s;
     draw3(p, site, t, 0, r);
-    ring_pair(r[0], r[3], &z[0], &z[1]);
-    ring_pair(r[1], r[3] >> 10, &z[2], &z[3]);
-    ring_pair(r[2], r[3] >> 20, &z[4], &z[5]);
+    for (int j = 0; j < 4; ++j) ring_pair22(r[j], &z[2 * j], &z[2 * j + 1]);
     draw3(p, site, t, 1, r);
-    ring_pair(r[0], r[3], &z[6], &z[7]);
-    ring_pair(r[1], r[3] >> 10, &z[8], &z[9]);
-    ring_pair(r[2], r[3] >> 20, &z[10], &z[11]);
-    draw3(p, site, t, 2, r);
-    ring_pair(r[0], r[3], &z[12], &z[13]);
-    ring_pair(r[1], r[3] >> 10, &z[14], &s);
+    for (int j = 0; j < 3; ++j) ring_pair22(r[j], &z[8 + 2 * j], &z[9 + 2 * j]);
+    ring_pair22(r[3], &z[14], &s);
 }
 
 static inline int wrap3(int a, int n) {

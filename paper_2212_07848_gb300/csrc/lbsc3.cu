@@ -15,7 +15,7 @@
 // mass and momentum conserved (momentum + F), the six stress modes relaxed
 // to rho u u with the Guo source, the nine ghost modes relaxed to zero, and
 // noise sqrt(mu rho b_k (1 - gamma^2)) z_k on the fifteen modes 4..18 from
-// three Philox4x32-10 calls (ring Box-Muller).
+// two Philox4x32-10 calls (ring Box-Muller, one pair per word).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -105,6 +105,16 @@ template <typename T> struct K3 {
 };
 
 constexpr int kRing3 = 1024;
+
+// Uniform in (0, 1) from the high 22 bits of a word: ((w >> 10) + 1/2) 2^-22
+// (exact in FP32 and FP64).
+template <typename T> __device__ __forceinline__ T uniform22(uint32_t w);
+template <> __device__ __forceinline__ float uniform22<float>(uint32_t w) {
+    return __fmaf_rn(__uint2float_rn(w >> 10), 2.384185791015625e-07f, 1.1920928955078125e-07f);
+}
+template <> __device__ __forceinline__ double uniform22<double>(uint32_t w) {
+    return ((double)(w >> 10) + 0.5) * 2.384185791015625e-07;
+}
 
 // One ring Box-Muller pair folded with sqrt(rho): rad = sqrt(-2 rho ln u1),
 // (c, s) = (cos, sin) of angle a.  FP32 reads the angle's cosine and sine from
@@ -212,24 +222,25 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         for (int k = 10; k < 19; ++k) ms[k] = g_ * m[k];
     }
     if (p.noise) {
+        // two Philox calls, one ring pair per word (radius from the high 22
+        // bits, angle index from the low 10): block 0 -> modes 4..11, block 1
+        // -> modes 12..17 and 18 (the cosine of its last pair)
         const uint4 r0 = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), p.rk);
         const uint4 r1 = philox4x32_10(make_uint4(site, p.step, p.replica, 1u), p.rk);
-        const uint4 r2 = philox4x32_10(make_uint4(site, p.step, p.replica, 2u), p.rk);
         T c, sn, rad;
-#define NOISE_PAIR(R, WORD, SHIFT, KA, KB)                                                 \
-    ring_pair3(uniform01<T>(R.WORD), (R.w >> SHIFT) & 1023u, rho, ring, rad, c, sn);     \
-    ms[KA] = fma(p.amp[KA] * rad, c, ms[KA]);                                             \
+#define NOISE_PAIR(W, KA, KB)                                                \
+    ring_pair3(uniform22<T>(W), (W) & 1023u, rho, ring, rad, c, sn);      \
+    ms[KA] = fma(p.amp[KA] * rad, c, ms[KA]);                              \
     ms[KB] = fma(p.amp[KB] * rad, sn, ms[KB]);
-        NOISE_PAIR(r0, x, 0, 4, 5)
-        NOISE_PAIR(r0, y, 10, 6, 7)
-        NOISE_PAIR(r0, z, 20, 8, 9)
-        NOISE_PAIR(r1, x, 0, 10, 11)
-        NOISE_PAIR(r1, y, 10, 12, 13)
-        NOISE_PAIR(r1, z, 20, 14, 15)
-        NOISE_PAIR(r2, x, 0, 16, 17)
+        NOISE_PAIR(r0.x, 4, 5)
+        NOISE_PAIR(r0.y, 6, 7)
+        NOISE_PAIR(r0.z, 8, 9)
+        NOISE_PAIR(r0.w, 10, 11)
+        NOISE_PAIR(r1.x, 12, 13)
+        NOISE_PAIR(r1.y, 14, 15)
+        NOISE_PAIR(r1.z, 16, 17)
 #undef NOISE_PAIR
-        // mode 18: the cosine of the pair (r2.y, bits 10-19 of r2.w)
-        ring_pair3(uniform01<T>(r2.y), (r2.w >> 10) & 1023u, rho, ring, rad, c, sn);
+        ring_pair3(uniform22<T>(r1.w), r1.w & 1023u, rho, ring, rad, c, sn);
         ms[18] = fma(p.amp[18] * rad, c, ms[18]);
     }
     // inverse: delta f_i = w_i sum_k e_ki m*_k / b_k, assembled per pair as
