@@ -523,6 +523,9 @@ void or3_moment_basis(double m[361], double b[19]) {
         for (int i = 0; i < 19; ++i) m[19 * k + i] = E3[k][i];
     }
 }
+/* One ring pair from a single word (the 3D mapping: 22-bit radius, 10-bit angle). */
+void or3_ring_pair22(uint32_t w, double z[2]) { ring_pair22(w, &z[0], &z[1]); }
+
 void or3_normals(const or3_params *p, uint32_t site, uint32_t t, double z[15]) {
     site_normals3(p, site, t, z);
 }

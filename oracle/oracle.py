@@ -111,6 +111,7 @@ def lib():
         L.or3_step_sites.argtypes = [C.POINTER(Or3Params), C.c_longlong, _D, C.c_int, _I, _I, _I,
                                      _D]
         L.or3_step_sites.restype = C.c_int
+        L.or3_ring_pair22.argtypes = [C.c_uint32, _D]
         L.or_box_muller_ring.argtypes = [C.c_uint32, C.c_uint32, _D]
         L.or_threads.restype = C.c_int
         _lib = L
@@ -303,6 +304,14 @@ def step_sites3(nx, ny, nz, G, tau, kT, seed, t, f_full, xs, ys, zs, replica=0, 
     if rc != 0:
         raise ValueError("oracle: site out of range")
     return out.reshape(len(xs), 19)
+
+
+def ring_pair22(word):
+    """The 3D noise pair of one Philox word: radius from its high 22 bits,
+    angle index from its low 10 bits."""
+    z = np.zeros(2)
+    lib().or3_ring_pair22(int(word), z)
+    return z
 
 
 class OracleLattice3:

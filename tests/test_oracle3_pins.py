@@ -285,3 +285,23 @@ def test_radial_bins3_on_a_known_cube():
     for b, vals in shells.items():
         assert abs(bins[b] - np.mean(vals)) < 1e-12, b
     assert bins[0] == 0.0
+
+
+def test_ring_pair22_moments_exact():
+    """The 3D mapping of one word to a pair: for a fixed high 22 bits (u =
+    (h + 1/2) 2^-22, R^2 = -2 ln u) the 1024 low-bit angle indices reproduce the
+    isotropic moments of a normal pair exactly (as the 2D ring does)."""
+    for high in (0, 4321, 2 ** 21, 2 ** 22 - 1):
+        R2 = -2.0 * np.log((high + 0.5) / 2.0 ** 22)
+        z = np.array([O.ring_pair22((high << 10) | a) for a in range(1024)])
+        z0, z1 = z[:, 0], z[:, 1]
+        assert np.allclose(np.hypot(z0, z1), np.sqrt(R2), rtol=1e-14)
+        tol = 1e-13 * max(R2, 1.0) ** 2
+        for m in (z0.mean(), z1.mean(), (z0 * z1).mean(), (z0 ** 3).mean(), (z0 * z1 ** 2).mean()):
+            assert abs(m) < tol
+        assert abs((z0 ** 2).mean() - R2 / 2) < tol and abs((z1 ** 2).mean() - R2 / 2) < tol
+        assert abs((z0 ** 4).mean() - 3 * R2 ** 2 / 8) < tol
+        assert abs((z0 ** 2 * z1 ** 2).mean() - R2 ** 2 / 8) < tol
+    # over all 2^22 radius values the radius moment E R^2 = 2 up to the 22-bit midpoint rule
+    h = np.arange(2 ** 22, dtype=np.float64)
+    assert abs(np.mean(-2.0 * np.log((h + 0.5) / 2.0 ** 22)) - 2.0) < 1e-6
