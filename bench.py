@@ -131,11 +131,24 @@ def cpu_baseline():
     o.step(steps)
     o.sk_sample_now()
     dt = time.perf_counter() - t0
-    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": O.threads(),
+    cores = O.threads()
+    # one core: a quarter of the sample (the site loops are the same code)
+    O.set_threads(1)
+    try:
+        o1 = O.OracleLattice(nx // 2, ny // 2, G, TAU, KT)
+        o1.init(RHO0, SEED, 0.0)
+        t1 = time.perf_counter()
+        o1.step(steps)
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
             "kind": "oracle",
+            "single_core_mlups": (nx // 2) * (ny // 2) * steps / dt1 / 1e6,
             "sample": f"{nx}x{ny} lattice, {steps} steps of the same physics (G=-5.0, "
                       f"rho0=ln2, kT=1e-6, E4, FP64) plus one direct-DFT S(k) sample; "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s on {cores} threads; one thread: {nx // 2}x{ny // 2}, "
+                      f"{steps} steps, {dt1:.1f} s"}
 
 
 def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):

@@ -692,3 +692,12 @@ int or_threads(void) {
     return 1;
 #endif
 }
+/* Set the threads of the site loops (timing on one core or all; ignored
+ * without OpenMP). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

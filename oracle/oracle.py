@@ -114,6 +114,7 @@ def lib():
         L.or3_ring_pair22.argtypes = [C.c_uint32, _D]
         L.or_box_muller_ring.argtypes = [C.c_uint32, C.c_uint32, _D]
         L.or_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -121,6 +122,11 @@ def lib():
 def threads():
     """Host threads the oracle's site loops use."""
     return int(lib().or_threads())
+
+
+def set_threads(n):
+    """Threads for the oracle's site loops (for timing on one core)."""
+    lib().or_set_threads(int(n))
 
 
 def philox4x32(ctr, key):
