@@ -36,3 +36,19 @@ def test_component_wrapping_in_both_directions():
     two[2:4, 2:4] = True
     two[10:12, 10:12] = True
     assert sorted(c[0] for c in _components(two)) == [4, 4]
+
+
+def test_growth_exponent_and_block_mean():
+    """The driver's helpers: the log-log slope of an exact power law over the
+    chosen window, and block means of a field."""
+    import numpy as np
+
+    from paper_2212_07848_gb300.quench import block_mean, growth_exponent
+    t = np.arange(500, 50001, 500)
+    L = 2.5 * t ** 0.45
+    L[t < 5000] *= 3.0                       # a different early regime, outside the window
+    assert abs(growth_exponent(t, L, 5000) - 0.45) < 1e-12
+    f = np.arange(64.0).reshape(8, 8)
+    b = block_mean(f, 4)
+    assert b.shape == (2, 2)
+    assert b[0, 0] == f[:4, :4].mean() and b[1, 1] == f[4:, 4:].mean()
