@@ -315,9 +315,9 @@ def test_flat_interface_normal_pressure_is_constant(tau):
     P_N = rho c_s^2 + (G c_s^2 / 4) psi(x) [psi(x+1) + psi(x-1)] must be
     constant across a converged slab (G = -5, T_hat = 0.8; odd side, no k = pi
     mode), and the two bulk phases sit at equal EoS pressure.  The spread is
-    taken at its minimum: at tau = 0.8 a slowly growing mode of the discrete
-    scheme about the slab (about x3.5 per 10^4 steps, the same in 2D) lifts it
-    again after about 3 10^4 steps, so the bound there is 5e-13."""
+    taken at its minimum: at tau = 0.8 a slowly growing translation of the slab
+    (a counterflow, about x3.5 per 10^4 steps, the same in 2D) lifts it again
+    after about 3 10^4 steps, so the bound there is 5e-13."""
     from oracle import theory as T
     from paper_2212_07848_gb300 import inputs
     G = -5.0

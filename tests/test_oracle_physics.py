@@ -38,8 +38,8 @@ def test_flat_interface_normal_pressure_is_constant(tau):
     so the lattice carries no k = pi momentum mode (with an even side that
     undamped checkerboard mode can survive the transient and add O(u^2)
     terms).  The spread is taken at its minimum: at tau = 0.8 a slowly growing
-    mode of the discrete scheme about the slab (about x3.4 per 10^4 steps)
-    lifts it again after about 3 10^4 steps."""
+    translation of the slab (a counterflow, about x3.4 per 10^4 steps) lifts
+    it again after about 3 10^4 steps."""
     G = -5.0
     nx, ny = 65, 4
     rg, rl = T.coexistence(G, eps=0.0)
