@@ -412,3 +412,65 @@ def radial_bins3(S):
     sums = np.bincount(b[keep], S[keep])
     cnt = np.bincount(b[keep])
     return np.where(cnt > 0, sums / np.maximum(cnt, 1), 0.0)
+
+
+def full_plane(S_half, nx, ny):
+    """The full spectrum [ny][nx] of a real field's S(k), rebuilt from its half
+    plane [ny][nx/2+1] by S(-k) = S(k) (the density is real, so
+    |dn(-k)|^2 = |dn(k)|^2)."""
+    S_half = np.asarray(S_half, dtype=np.float64)
+    full = np.zeros((ny, nx))
+    for my in range(ny):
+        for mx in range(nx):
+            if mx <= nx // 2:
+                full[my, mx] = S_half[my, mx]
+            else:
+                full[my, mx] = S_half[(-my) % ny, nx - mx]
+    return full
+
+
+def _folded(m, n):
+    return m if m <= n // 2 else m - n
+
+
+def radial_bins(S_half, nx, ny, nbins):
+    """Radial read-out of a 2D S(k) (defined after Eq. (12)), binned as the
+    paper bins its S(k) curves against |k| (Fig. 2): every wave vector of the
+    full plane except k = 0, with q = (m_x max(n)/n_x, m_y max(n)/n_y) from
+    the folded indices m, falls in bin b = round(|q|) (bin width
+    dk = 2 pi / max(n_x, n_y)); bins at or above nbins are dropped.  Returns
+    (mean of S over each bin, NaN where empty; number of modes per bin)."""
+    full = full_plane(S_half, nx, ny)
+    Lm = max(nx, ny)
+    sums = np.zeros(nbins)
+    counts = np.zeros(nbins, dtype=np.int64)
+    for my in range(ny):
+        for mx in range(nx):
+            if mx == 0 and my == 0:
+                continue
+            qx = _folded(mx, nx) * (Lm / nx)
+            qy = _folded(my, ny) * (Lm / ny)
+            b = int(np.rint(np.sqrt(qx * qx + qy * qy)))
+            if b < nbins:
+                sums[b] += full[my, mx]
+                counts[b] += 1
+    with np.errstate(invalid="ignore", divide="ignore"):
+        means = np.where(counts > 0, sums / np.maximum(counts, 1), np.nan)
+    return means, counts
+
+
+def sk_first_moments(S_half, nx, ny):
+    """(sum_k S(k), sum_k |k| S(k)) over every wave vector of the full plane
+    except k = 0, |k| = 2 pi sqrt((m_x/n_x)^2 + (m_y/n_y)^2) with folded
+    indices.  Their ratio gives the domain size L = 2 pi sum S / sum |k| S
+    (the library's definition of L(t); the paper defines none)."""
+    full = full_plane(S_half, nx, ny)
+    s0 = s1 = 0.0
+    for my in range(ny):
+        for mx in range(nx):
+            if mx == 0 and my == 0:
+                continue
+            k = 2.0 * np.pi * np.hypot(_folded(mx, nx) / nx, _folded(my, ny) / ny)
+            s0 += full[my, mx]
+            s1 += k * full[my, mx]
+    return s0, s1

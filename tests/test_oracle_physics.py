@@ -137,6 +137,9 @@ SK_CASES = [
     # the paper's critical-scaled psi, Eq. (5), with G = -1/c_s^2 so p is
     # Eq. (6) at T = 1/3; T_c chosen for T_hat = 0.8, metastable liquid
     (-3.0, 1.9, 1e-6, 4, 1, 1.0 / 3.0 / 0.8, 1.0),
+    # a exp(-b/n) (the form before Eq. (3)) with a = 1.3, b = 0.8, at its
+    # critical density n = b and T_hat = 1.11: G = 0.9 G_c, G_c = -b e^2 / a^2
+    (-0.9 * 0.8 * np.e ** 2 / 1.3 ** 2, 0.8, 1e-5, 4, 2, 1.3, 0.8),
 ]
 
 

@@ -239,21 +239,47 @@ def test_guo_forcing_moments(stencil, tau):
         assert np.abs(post - (e + gam * (pre - e) + s * sr)).max() < 1e-14
 
 
+# psi kinds: 0 = 1 - exp(-rho); 1 = Eq. (5) with (T_c, n_c); 2 = a exp(-b/n),
+# the form introduced before Eq. (3), here with (a, b) away from the
+# critical-point constants of Eq. (4) so that it is not kind 1 in disguise.
+PSI_KINDS = [(0, 0.0, 0.0), (1, 0.5, 0.9), (2, 1.3, 0.8)]
+
+
+@pytest.mark.parametrize("kind,p1,p2", PSI_KINDS)
 @pytest.mark.parametrize("stencil", [4, 6, 8])
-def test_force_sums_to_zero_and_continuum_limit(stencil):
+def test_force_sums_to_zero_and_continuum_limit(stencil, kind, p1, p2):
     """Sum of F over the lattice vanishes (pair antisymmetry of Eq. (1)), and
     for a long-wave density F -> -G c_s^2 psi grad psi (the continuum limit of
-    Eq. (1) with sum_a w_a e_a e_a = I)."""
+    Eq. (1) with sum_a w_a e_a e_a = I), for each pseudopotential form.  The
+    expected psi and psi' are written here from the paper's formulas, and
+    psi' is checked against a central difference of psi."""
+    def psi_ref(r):
+        if kind == 0:
+            return 1.0 - np.exp(-r)
+        if kind == 1:
+            return np.sqrt(p1 * p2) * np.exp(1.0 - p2 / r)
+        return p1 * np.exp(-p2 / r)
+
+    def dpsi_ref(r):
+        if kind == 0:
+            return np.exp(-r)
+        return psi_ref(r) * p2 / r ** 2
+
+    r = np.linspace(0.3, 2.0, 7)
+    fd = (psi_ref(r + 1e-6) - psi_ref(r - 1e-6)) / 2e-6
+    assert np.allclose(dpsi_ref(r), fd, rtol=1e-8)
+    kw = dict(psi_kind=kind, psi_p1=p1, psi_p2=p2)
     nx, ny = 24, 20
-    o = O.OracleLattice(nx, ny, G=-4.2, tau=1.0, kT=0.0, stencil=stencil)
+    o = O.OracleLattice(nx, ny, G=-4.2, tau=1.0, kT=0.0, stencil=stencil, **kw)
     o.init(LN2)
     o.set_density(inputs.perturbed_density(nx, ny, LN2, 0.1, seed=5))
     Fx, Fy = o.force()
     assert abs(Fx.sum()) < 1e-14 and abs(Fy.sum()) < 1e-14
+    assert np.abs(Fx).max() > 1e-3                # the force is not trivially zero
     for mx, my in [(1, 0), (0, 1), (1, 1)]:
         errs = []
         for L in (128, 256):
-            o = O.OracleLattice(L, L, G=-4.2, tau=1.0, kT=0.0, stencil=stencil)
+            o = O.OracleLattice(L, L, G=-4.2, tau=1.0, kT=0.0, stencil=stencil, **kw)
             o.init(LN2)
             rho = inputs.sinusoid_density(L, L, LN2, 0.02, mx, my)
             o.set_density(rho)
@@ -262,13 +288,37 @@ def test_force_sums_to_zero_and_continuum_limit(stencil):
             ph = 2 * np.pi * (mx * x / L + my * y / L)
             grx = 0.02 * np.cos(ph) * 2 * np.pi * mx / L
             gry = 0.02 * np.cos(ph) * 2 * np.pi * my / L
-            ps, dps = T.psi(rho), T.dpsi(rho)
+            ps, dps = psi_ref(rho), dpsi_ref(rho)
             ex_x = 4.2 / 3.0 * ps * dps * grx
             ex_y = 4.2 / 3.0 * ps * dps * gry
             scale = np.abs(np.hypot(ex_x, ex_y)).max()
             errs.append(max(np.abs(Fx - ex_x).max(), np.abs(Fy - ex_y).max()) / scale)
         assert errs[1] < 5e-4
         assert errs[1] < errs[0] / 3.0           # second-order convergence in k
+
+
+def test_psi_kind2_at_critical_constants_is_eq5():
+    """Eq. (4): with a = e sqrt(T_c n_c) and b = n_c the form a exp(-b/n)
+    becomes Eq. (5).  The oracle run with kind 2 at those constants must
+    reproduce the kind-1 run (same noisy state, same Philox stream) up to
+    rounding, and or_psi must agree pointwise."""
+    Tc, nc = 0.41, 1.1
+    a, b = np.e * np.sqrt(Tc * nc), nc
+    p1 = O.make_params(8, 8, -3.0, 1.0, 0.0, psi_kind=1, psi_p1=Tc, psi_p2=nc)
+    p2 = O.make_params(8, 8, -3.0, 1.0, 0.0, psi_kind=2, psi_p1=a, psi_p2=b)
+    for r in (0.2, 0.7, 1.1, 2.3):
+        v1 = O.lib().or_psi(p1, r)
+        v2 = O.lib().or_psi(p2, r)
+        assert abs(v2 / v1 - 1.0) < 1e-14
+    runs = []
+    for kind, q1, q2 in [(1, Tc, nc), (2, a, b)]:
+        o = O.OracleLattice(32, 24, G=-3.0, tau=0.9, kT=1e-5, stencil=4,
+                            psi_kind=kind, psi_p1=q1, psi_p2=q2)
+        o.init(1.3, seed=3, init_amp=0.02)
+        o.step(40)
+        runs.append(o.populations())
+    assert np.max(np.abs(runs[1] - runs[0]) / np.abs(runs[0])) < 1e-12
+    assert np.max(np.abs(runs[0] - runs[0][:, :1, :1])) > 1e-4   # the state is not flat
 
 
 def test_flat_equilibrium_stays_flat():
@@ -354,3 +404,63 @@ def test_step_sites_equals_lattice_step():
     f1 = o.populations()
     for s in range(len(xs)):
         assert np.array_equal(out[s], f1[:, ys[s], xs[s]])
+
+
+# --------------------------------------------------------------------------
+# Radial read-out of S(k) and its first moments
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 6), (6, 10)])
+def test_full_plane_rebuild_matches_numpy_fft(nx, ny):
+    """The half plane of |FFT|^2 of a real field, rebuilt by full_plane, equals
+    numpy's full |FFT|^2 (S(-k) = S(k) for a real density)."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((ny, nx))
+    P = np.abs(np.fft.fft2(x)) ** 2
+    assert np.allclose(O.full_plane(P[:, : nx // 2 + 1], nx, ny), P, rtol=1e-13)
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 8), (8, 24)])
+def test_radial_bins_on_a_known_plane(nx, ny):
+    """radial_bins of S = |q|^2 + 1 gives in every bin the mean of that value
+    over the integer wave vectors with round(|q|) = b, enumerated here from
+    numpy's fftfreq; the counts over all bins add up to nx ny - 1 (every mode
+    but k = 0)."""
+    Lm = max(nx, ny)
+    fy = np.fft.fftfreq(ny) * ny * (Lm / ny)
+    fx = np.fft.fftfreq(nx) * nx * (Lm / nx)
+    if nx % 2 == 0:
+        fx[nx // 2] = abs(fx[nx // 2])
+    QY, QX = np.meshgrid(fy, fx, indexing="ij")
+    val = QX ** 2 + QY ** 2 + 1.0
+    half = val[:, : nx // 2 + 1]
+    nb = int(np.ceil(np.hypot(nx, ny))) + 2
+    means, counts = O.radial_bins(half, nx, ny, nb)
+    assert counts.sum() == nx * ny - 1
+    expected = {}
+    for qy, qx, v in zip(QY.ravel(), QX.ravel(), val.ravel()):
+        if qx == 0 and qy == 0:
+            continue
+        expected.setdefault(int(np.rint(np.hypot(qx, qy))), []).append(v)
+    for b in range(nb):
+        if b in expected:
+            assert counts[b] == len(expected[b])
+            assert abs(means[b] - np.mean(expected[b])) < 1e-12 * means[b]
+        else:
+            assert counts[b] == 0 and np.isnan(means[b])
+    # bins past nbins are dropped, the rest unchanged
+    m2, c2 = O.radial_bins(half, nx, ny, 3)
+    assert np.array_equal(c2, counts[:3])
+
+
+def test_first_moments_of_a_single_wave():
+    """A density cos(2 pi (3x/nx + 2y/ny)) has S(k) only at k = +-(3, 2), so
+    the first moments give L = 2 pi sum S / sum |k| S = 1 / |(3/nx, 2/ny)|,
+    and sum S = N/2 (Parseval with the N^{-1/2} transform)."""
+    nx, ny = 32, 16
+    y, x = np.mgrid[0:ny, 0:nx]
+    rho = np.cos(2 * np.pi * (3 * x / nx + 2 * y / ny))
+    S = np.abs(np.fft.rfft2(rho)) ** 2 / (nx * ny)
+    s0, s1 = O.sk_first_moments(S, nx, ny)
+    assert abs(s0 - nx * ny / 2) < 1e-9
+    L = 2 * np.pi * s0 / s1
+    assert abs(L - 1.0 / np.hypot(3 / nx, 2 / ny)) < 1e-12
