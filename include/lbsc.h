@@ -73,6 +73,9 @@ extern "C" {
 #define LB_KERNEL_PLAIN 1   /* pulls with coalesced global loads                  */
 #define LB_KERNEL_TMA 2     /* rows staged in shared memory by cp.async.bulk.tensor
                                (FP32 and nx a multiple of 128 only)               */
+#define LB_KERNEL_OVERLAP 3 /* coalesced global loads; strips of 128 - 2H columns
+                               whose halo columns are pulled by the CTA's own
+                               threads (no separate halo warp)                    */
 
 /* ---- lb_device_ptr selectors -------------------------------------------- */
 #define LB_PTR_POPULATIONS 0   /* current deviations [9][ny][nx] (T)        */
@@ -144,6 +147,17 @@ int lb_set_strip_height(lb_ctx *h, int rows);
  * lb_get_kernel returns the kernel lb_step uses. */
 int lb_set_kernel(lb_ctx *h, int mode);
 int lb_get_kernel(const lb_ctx *h);
+
+/* Bound, in nanoseconds of the device's global timer, on each mbarrier wait
+ * of the staged kernel (LB_KERNEL_TMA) for a row copy to land (failure
+ * detection).  ns < 0 restores the default of 2 s; ns = 0 makes a wait give
+ * up at the first check that finds its copy in flight.  On a timeout every
+ * thread of the CTA leaves through the same barrier, the CTA waits (with the
+ * default bound) for the copies it issued, and lb_sync returns
+ * LB_ERR_TIMEOUT; the steps launched since the last good sync are then
+ * incomplete and the state must be restored (lb_init, lb_load or
+ * lb_set_populations) before it is used again.  Errors: LB_ERR_ARG. */
+int lb_set_wait_ns(lb_ctx *h, long long ns);
 
 /* Advance n >= 0 time steps of Eq. (12), asynchronously on the context
  * stream.  Sampling steps (lb_sk_config) also run the S(k) transform and
@@ -246,7 +260,11 @@ void *lb_stream(lb_ctx *h);
  * clearing, but calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The first call on a
  * device looks up the array's device address (make that first call before
- * any stream capture).  Nothing here allocates device or host memory.
+ * any stream capture) and keeps it for the life of the process: after a
+ * cudaDeviceReset, or anything else that destroys the device's primary
+ * context, the kept address is stale and this entry point must not be called
+ * again on that device until the library is reloaded.  Nothing here
+ * allocates device or host memory.
  * Errors: LB_ERR_ARG, LB_ERR_UNSUPPORTED, LB_ERR_CUDA. */
 int lb_conserved_static(const void *d_df, int precision, int nx, int ny, double rho0,
                         double *d_out3, void *stream);
@@ -295,6 +313,16 @@ int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *cho
 #define LB_ENS_PERSISTENT 1
 int lb_ens_set_launch(lb_ens *e, int mode);
 int lb_ens_get_launch(const lb_ens *e);
+/* Bound, in nanoseconds of the device's global timer, on each replica
+ * barrier of the persistent launch (failure detection, the bounded waits of
+ * a persistent kernel).  ns < 0 restores the default of 2 s; ns = 0 makes a
+ * barrier give up at the first check that finds its replica's previous step
+ * unfinished.  On a timeout the waiting CTA records it, every other CTA stops
+ * at its next barrier, the launch ends, and lb_ens_sync returns
+ * LB_ERR_TIMEOUT; the replicas' state is then partly advanced and must be
+ * re-initialised (lb_ens_init) before it is used again.  Synchronises the
+ * ensemble's stream.  Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+int lb_ens_set_wait_ns(lb_ens *e, long long ns);
 /* Advance every replica n steps (asynchronous); windows of steps replay
  * captured CUDA graphs. */
 int lb_ens_step(lb_ens *e, int n);
@@ -477,8 +505,19 @@ int lb_nn_expand(const float *src, const float *prev, double gfeat, void *out, i
 int lb_nn_set_conv_path(int path);
 /* Synchronises the device and reports whether a tensor-core convolution gave
  * up waiting on its mbarrier since the last call: LB_ERR_TIMEOUT (the flag is
- * then cleared) or LB_OK. */
+ * then cleared), LB_ERR_CUDA if tensor memory had to be left allocated (see
+ * lb_nn_set_wait_ns), or LB_OK. */
 int lb_nn_status(void);
+/* Bound, in nanoseconds of the device's global timer, on the tensor-core
+ * convolution's wait for its MMAs (current device, process-wide).  ns < 0
+ * restores the default of 1 s; ns = 0 makes the wait give up at the first
+ * check that finds the MMAs unfinished.  On a timeout the CTA skips its
+ * output tile, records the timeout for lb_nn_status, waits (with the
+ * default bound) for the MMAs it committed, and only then frees its tensor
+ * memory; if even that wait runs out it leaves the tensor memory allocated
+ * and lb_nn_status returns LB_ERR_CUDA (the process should then be
+ * restarted).  Errors: LB_ERR_CUDA. */
+int lb_nn_set_wait_ns(long long ns);
 /* BF16 copy of FP32 values. */
 int lb_nn_to_bf16(const float *a, void *b, size_t n, void *stream);
 /* Increment as the divergence of a predicted flux, so that the surrogate

@@ -25,7 +25,7 @@ LB_ERR_STATE = -8
 LB_PSI_EXP, LB_PSI_CRITICAL, LB_PSI_AEXP = 0, 1, 2
 LB_FP32, LB_FP64 = 0, 1
 LB_PTR_POPULATIONS, LB_PTR_DENSITY_SAMPLE, LB_PTR_SK_ACCUM = 0, 1, 2
-LB_KERNEL_AUTO, LB_KERNEL_PLAIN, LB_KERNEL_TMA = 0, 1, 2
+LB_KERNEL_AUTO, LB_KERNEL_PLAIN, LB_KERNEL_TMA, LB_KERNEL_OVERLAP = 0, 1, 2, 3
 
 # Every function the header declares, for export checks.
 EXPORTED = [
@@ -36,7 +36,7 @@ EXPORTED = [
     "lb_sk_reset", "lb_sk_sample_now", "lb_structure_factor",
     "lb_structure_factor_counts", "lb_conserved", "lb_save", "lb_load",
     "lb_device_ptr", "lb_stream", "lb_strerror", "lb_conserved_static",
-    "lb_set_kernel", "lb_get_kernel",
+    "lb_set_kernel", "lb_get_kernel", "lb_set_wait_ns", "lb_ens_set_wait_ns",
     "lb_ens_create", "lb_ens_destroy", "lb_ens_init", "lb_ens_sk_config",
     "lb_ens_set_strip_height", "lb_ens_autotune", "lb_ens_step", "lb_ens_sync",
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
@@ -50,7 +50,7 @@ EXPORTED = [
     "lb_nn_add", "lb_nn_coarse_grain", "lb_nn_mse", "lb_nn_residual", "lb_nn_adam",
     "lb_nn_to_bf16", "lb_nn_flux_div", "lb_nn_coarse_momentum", "lb_nn_expand_channel",
     "lb_nn_mse_channel", "lb_nn_mse_blocks", "lb_nn_add_channel", "lb_nn_expand", "lb_nn_wgrad_workspace", "lb_nn_set_conv_path",
-    "lb_nn_status",
+    "lb_nn_status", "lb_nn_set_wait_ns",
 ]
 
 
@@ -129,6 +129,9 @@ def bind(L):
         "lb_strerror": (C.c_char_p, [C.c_int]),
         "lb_conserved_static": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_double, P, P]),
         "lb_set_kernel": (C.c_int, [P, C.c_int]),
+        "lb_set_wait_ns": (C.c_int, [P, C.c_longlong]),
+        "lb_ens_set_wait_ns": (C.c_int, [P, C.c_longlong]),
+        "lb_nn_set_wait_ns": (C.c_int, [C.c_longlong]),
         "lb_get_kernel": (C.c_int, [P]),
         "lb_ens_create": (C.c_int, [C.POINTER(P), C.POINTER(lb_replica), C.c_int, C.c_int,
                                     C.c_double, C.c_double, C.c_int, C.c_uint64, P]),
@@ -248,6 +251,10 @@ def lb_set_kernel(h, mode):
 
 def lb_get_kernel(h):
     return load().lb_get_kernel(h)
+
+
+def lb_set_wait_ns(h, ns):
+    _check(load().lb_set_wait_ns(h, int(ns)), "lb_set_wait_ns")
 
 
 def lb_step(h, n=1):
@@ -385,6 +392,14 @@ def lb_ens_set_launch(h, mode):
 
 def lb_ens_get_launch(h):
     return load().lb_ens_get_launch(h)
+
+
+def lb_ens_set_wait_ns(h, ns):
+    _check(load().lb_ens_set_wait_ns(h, int(ns)), "lb_ens_set_wait_ns")
+
+
+def lb_nn_set_wait_ns(ns):
+    _check(load().lb_nn_set_wait_ns(int(ns)), "lb_nn_set_wait_ns")
 
 
 def lb_ens_set_strip_height(h, rows):

@@ -48,6 +48,7 @@ struct lb_ctx {
     int strip_h = 32;
     int kernel_mode = 0;            // LB_KERNEL_*
     TmaMaps maps;                   // tensor maps of df[0], df[1] (FP32 only)
+    long long wait_ns = -1;         // staged kernel's mbarrier bound (< 0: default)
     StepArgs base;
 };
 
@@ -335,9 +336,15 @@ int lb_set_strip_height(lb_ctx *h, int rows) {
 }
 
 int lb_set_kernel(lb_ctx *h, int mode) {
-    if (!h || mode < LB_KERNEL_AUTO || mode > LB_KERNEL_TMA) return LB_ERR_ARG;
+    if (!h || mode < LB_KERNEL_AUTO || mode > LB_KERNEL_OVERLAP) return LB_ERR_ARG;
     if (mode == LB_KERNEL_TMA && !h->maps.ok) return LB_ERR_UNSUPPORTED;
     h->kernel_mode = mode;
+    return LB_OK;
+}
+
+int lb_set_wait_ns(lb_ctx *h, long long ns) {
+    if (!h) return LB_ERR_ARG;
+    h->wait_ns = ns < 0 ? -1 : ns;
     return LB_OK;
 }
 
@@ -347,6 +354,7 @@ int lb_get_kernel(const lb_ctx *h) {
     // staged one for this step (the step is issue-bound, and the staged
     // kernel's per-row mbarrier hand-off costs more than the loads it saves).
     if (h->kernel_mode == LB_KERNEL_TMA && h->maps.ok) return LB_KERNEL_TMA;
+    if (h->kernel_mode == LB_KERNEL_OVERLAP) return LB_KERNEL_OVERLAP;
     return LB_KERNEL_PLAIN;
 }
 
@@ -365,6 +373,8 @@ int lb_step(lb_ctx *h, int n) {
         a.dst = h->df[h->cur ^ 1];
         a.drho_out = sample ? h->drho : nullptr;
         a.step = (uint32_t)h->t;
+        a.wait_ns = h->wait_ns;
+        a.layout = kern == LB_KERNEL_OVERLAP ? 1 : 0;
         if (kern == LB_KERNEL_TMA)
             LB_CHECK(launch_step_tma(h->p.stencil, a, h->maps, h->cur, h->stream));
         else

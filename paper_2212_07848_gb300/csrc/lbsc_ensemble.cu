@@ -149,8 +149,9 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
 struct EnsCtl {
     uint32_t finished;
     int abort;
+    unsigned long long wait_ns;   // bound on a replica barrier (lb_ens_set_wait_ns)
 };
-constexpr uint64_t kEnsWaitNs = 2000000000ull;   // 2 s bound on a replica barrier
+constexpr uint64_t kEnsWaitNs = 2000000000ull;   // default: 2 s
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
@@ -163,13 +164,16 @@ __device__ __forceinline__ uint64_t ens_global_ns() {
     return t;
 }
 // 1: the counter reached target; 0: another CTA aborted; -1: timed out.
-__device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abort) {
+// A limit of 0 gives up at the first check that finds the counter short.
+__device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abort,
+                            uint64_t limit_ns) {
     if (ld_acquire_u32(cnt) >= target) return 1;
+    if (limit_ns == 0) return -1;
     const uint64_t t0 = ens_global_ns();
     for (;;) {
         if (ld_acquire_u32(cnt) >= target) return 1;
         if (*(volatile const int *)abort) return 0;
-        if (ens_global_ns() - t0 > kEnsWaitNs) return -1;
+        if (ens_global_ns() - t0 > limit_ns) return -1;
         __nanosleep(100);
     }
 }
@@ -184,6 +188,7 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
     __shared__ int s_go, s_last;
     const uint32_t t0 = __ldcg(&clk->t);
     const int cur0 = __ldcg(&clk->cur);
+    const uint64_t wait_ns = __ldcg(&ctl->wait_ns);
     bool go = true;
     for (int s = 0; s < nsteps && go; ++s) {
         const bool sample = sample_last && s == nsteps - 1;
@@ -192,7 +197,7 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
             if (threadIdx.x == 0) {
                 int w = 1;
                 if (s > 0) w = wait_replica(&done[tile.r], (uint32_t)s * rep_ntiles[tile.r],
-                                            &ctl->abort);
+                                            &ctl->abort, wait_ns);
                 if (w < 0) {
                     atomicOr(flag, LB_STEP_TIMEOUT);
                     atomicExch(&ctl->abort, 1);
@@ -565,7 +570,10 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
     if (err == cudaSuccess) err = cudaMalloc(&e->d_done, nrep * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMemset(e->d_done, 0, nrep * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl, sizeof(EnsCtl));
-    if (err == cudaSuccess) err = cudaMemset(e->d_ctl, 0, sizeof(EnsCtl));
+    if (err == cudaSuccess) {
+        const EnsCtl c0 = {0u, 0, (unsigned long long)kEnsWaitNs};
+        err = cudaMemcpy(e->d_ctl, &c0, sizeof(EnsCtl), cudaMemcpyHostToDevice);
+    }
     if (err == cudaSuccess) {
         int per_sm = 0, nsm = 0;
         const void *k = stencil == 4   ? (const void *)ens_persist_kernel<4>
@@ -721,6 +729,15 @@ int lb_ens_set_launch(lb_ens *e, int mode) {
 }
 
 int lb_ens_get_launch(const lb_ens *e) { return e ? e->launch_mode : LB_ERR_ARG; }
+
+int lb_ens_set_wait_ns(lb_ens *e, long long ns) {
+    if (!e) return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    const unsigned long long v = ns < 0 ? (unsigned long long)kEnsWaitNs : (unsigned long long)ns;
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    ENS_CHECK(cudaMemcpy(&e->d_ctl->wait_ns, &v, sizeof(v), cudaMemcpyHostToDevice));
+    return LB_OK;
+}
 
 int lb_ens_step(lb_ens *e, int n) {
     if (!e || n < 0) return LB_ERR_ARG;

@@ -47,6 +47,8 @@ struct StepArgs {
     uint32_t step;        // counter word 1: number of completed steps
     uint32_t replica;     // counter word 2
     int noise;            // kT > 0
+    long long wait_ns;    // staged kernel: bound on an mbarrier wait (< 0: default)
+    int layout;           // plain kernel: 0 = halo warp, 1 = overlapped strips
 };
 
 // FFT / structure-factor buffers of one lattice.

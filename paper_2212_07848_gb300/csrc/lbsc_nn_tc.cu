@@ -25,12 +25,14 @@
 namespace lbsc {
 
 int nn_conv_path = 0;   // 0: auto, 1: mma.sync, 2: tcgen05 wherever it has a kernel
-__device__ int g_nn_status;               // bit 0: an mbarrier wait gave up
+__device__ int g_nn_status;               // bit 0: an mbarrier wait gave up;
+                                          // bit 1: tensor memory left allocated
+constexpr unsigned long long kTcWaitNs = 1000000000ull;   // default bound: 1 s
+__device__ unsigned long long g_nn_wait_ns = kTcWaitNs;   // lb_nn_set_wait_ns
 
 namespace {
 
 using bf16 = __nv_bfloat16;
-constexpr uint64_t kTcWaitNs = 1000000000ull;   // 1 s bound on every mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,6 +48,16 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                  : "memory");
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -57,12 +69,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Wait for the completion of the phase with the given parity; false if it has
-// not completed within kTcWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+// not completed within limit_ns (0: give up at the first unfinished check,
+// which does not block).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kTcWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -230,8 +244,9 @@ conv3x3_tc_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
             if (r == 2) tc_commit(&bar);
         }
     }
-    const bool done = mbar_wait(&bar, 0);
+    const bool done = mbar_wait(&bar, 0, g_nn_wait_ns);
     const bool ok = !__syncthreads_or(!done);
+    __shared__ int s_drained;
     if (ok) {
         tc_fence_after();
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
@@ -261,11 +276,15 @@ conv3x3_tc_kernel(const bf16 *__restrict__ x, const bf16 *__restrict__ w,
         }
     } else if (tid == 0) {
         atomicOr(&g_nn_status, 1);
-        mbar_wait(&bar, 0);   // a bounded second chance before the accumulator is freed
+        // the committed MMAs must finish before their accumulator is freed:
+        // wait for them again with the default bound
+        s_drained = mbar_wait(&bar, 0, kTcWaitNs) ? 1 : 0;
+        if (!s_drained) atomicOr(&g_nn_status, 2);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, C::NCOLS);
+    // never free tensor memory under MMAs that may still be in flight
+    if (warp == 0 && (ok || s_drained)) tmem_dealloc(tmem, C::NCOLS);
 }
 
 template <int BN, int CIN>
@@ -340,7 +359,14 @@ extern "C" int lb_nn_status(void) {
         const int zero = 0;
         if (cudaMemcpyToSymbol(lbsc::g_nn_status, &zero, sizeof(int)) != cudaSuccess)
             return LB_ERR_CUDA;
-        return LB_ERR_TIMEOUT;
+        return (v & 2) ? LB_ERR_CUDA : LB_ERR_TIMEOUT;
     }
+    return LB_OK;
+}
+
+extern "C" int lb_nn_set_wait_ns(long long ns) {
+    const unsigned long long v = ns < 0 ? lbsc::kTcWaitNs : (unsigned long long)ns;
+    if (cudaDeviceSynchronize() != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaMemcpyToSymbol(lbsc::g_nn_wait_ns, &v, sizeof(v)) != cudaSuccess) return LB_ERR_CUDA;
     return LB_OK;
 }

@@ -182,7 +182,9 @@ conserved_static_final_kernel(const double *__restrict__ partials, int nblocks, 
 
 namespace {
 // Device address of g_conserved_scratch, looked up once per device with that
-// device current (in host code the symbol names a host-side stand-in).
+// device current (in host code the symbol names a host-side stand-in).  It is
+// kept until the process exits; a reset of the device's primary context makes
+// it stale (the header says so).
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 double *g_scratch_addr[kMaxDevices] = {nullptr};

@@ -13,9 +13,10 @@
 // Columns outside [0, nx) arrive zero-filled (the copy starts at x0 - 4);
 // in the first and last strip the halo warp overwrites them with the
 // periodic images (plain loads) once the copy has landed.  Every wait is
-// bounded in time: on expiry the kernel records LB_STEP_TIMEOUT in the flag,
-// lets every thread leave through the same barrier, and waits (bounded) for
-// its copies in flight before returning.
+// bounded in time (a per-context limit, 2 s by default): on expiry the
+// kernel records LB_STEP_TIMEOUT in the flag, lets every thread leave
+// through the same barrier, and waits (with the default bound) for its
+// copies in flight before returning.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -32,7 +33,7 @@ namespace {
 constexpr int kTX = kStepTX;            // interior columns per CTA (128)
 constexpr int kBox = kTX + 8;           // columns per staged row: x0-4 .. x0+131
 constexpr int kSlot = 1248;             // floats per ring slot: 9 x 136 = 1224 padded to 128 B
-constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s
+constexpr uint64_t kWaitNs = 2000000000ull;   // default bound on a wait: 2 s
 
 template <int H> struct TmaCfg {
     static constexpr int R = (H == 1) ? 6 : 8;            // ring rows (>= lookahead + H + 3)
@@ -63,6 +64,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -74,12 +85,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // Wait for the phase with the given parity; false if it has not completed
-// within kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+// within limit_ns (0: give up at the first unfinished check, which does not
+// block).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 __device__ __forceinline__ void tma_load_row(float *dst, const CUtensorMap *map, int x, int y,
@@ -126,7 +139,8 @@ __device__ __forceinline__ void pull_smem(const float *rm, const float *rc, cons
 template <int ORDER, bool SAMPLE>
 __global__ void __launch_bounds__(kTX + 32)
 step_kernel_tma(const __grid_constant__ CUtensorMap tm_src,
-                const __grid_constant__ CUtensorMap tm_dst, const KParams<float> p) {
+                const __grid_constant__ CUtensorMap tm_dst, const KParams<float> p,
+                const unsigned long long wait_ns) {
     using S = Stencil<ORDER>;
     constexpr int H = S::H;
     using Cfg = TmaCfg<H>;
@@ -210,7 +224,8 @@ step_kernel_tma(const __grid_constant__ CUtensorMap tm_src,
     }
     bool ok = true;
     // rows 0..2 are read in iteration 0 and must be in place (and fixed) first
-    for (int k = 0; k < 3 && k < nrows; ++k) ok = ok && mbar_wait(&bar[k % R], parity_of(k));
+    for (int k = 0; k < 3 && k < nrows; ++k)
+        ok = ok && mbar_wait(&bar[k % R], parity_of(k), wait_ns);
     if (ok)
         for (int k = 0; k < 3 && k < nrows; ++k) fixup(k);
     bool aborted = __syncthreads_or(!ok) != 0;
@@ -219,13 +234,13 @@ step_kernel_tma(const __grid_constant__ CUtensorMap tm_src,
     for (int it = 0; it < it_end && !aborted; ++it) {
         // halo warp: fix the periodic columns of row it+3 (read from iteration it+1 on)
         if (!interior && (edge_l || edge_r) && it + 3 < nrows) {
-            if (mbar_wait(&bar[(it + 3) % R], parity_of(it + 3)))
+            if (mbar_wait(&bar[(it + 3) % R], parity_of(it + 3), wait_ns))
                 fixup(it + 3);
             else
                 ok = false;
         }
         // newest row of this iteration's psi pulls
-        if (!mbar_wait(&bar[(it + 2) % R], parity_of(it + 2))) ok = false;
+        if (!mbar_wait(&bar[(it + 2) % R], parity_of(it + 2), wait_ns)) ok = false;
 
         const int pslot = it & (PR - 1);
         if (interior || halo) {
@@ -289,9 +304,9 @@ step_kernel_tma(const __grid_constant__ CUtensorMap tm_src,
         if (aborted) {
             atomicOr(p.flag, LB_STEP_TIMEOUT);
             // let every copy this CTA issued land before its shared memory is
-            // released (each wait bounded again)
+            // released (each wait bounded again, by the default bound)
             for (int k = max(0, last_issued - R + 1); k <= last_issued; ++k)
-                mbar_wait(&bar[k % R], parity_of(k));
+                mbar_wait(&bar[k % R], parity_of(k), kWaitNs);
         }
     }
 }
@@ -354,17 +369,20 @@ static cudaError_t launch_tma_t(const StepArgs &a, const TmaMaps &m, int src_buf
     const CUtensorMap *stv = reinterpret_cast<const CUtensorMap *>(m.store);
     const size_t smem = tma_smem<H>();
     dim3 grid(a.nx / kTX, (a.ny + a.strip_h - 1) / a.strip_h);
+    const unsigned long long wait_ns = a.wait_ns < 0 ? kWaitNs : (unsigned long long)a.wait_ns;
     cudaError_t e;
     if (a.drho_out) {
         e = cudaFuncSetAttribute(step_kernel_tma<ORDER, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        step_kernel_tma<ORDER, true><<<grid, kTX + 32, smem, s>>>(ld[src_buf], stv[src_buf ^ 1], k);
+        step_kernel_tma<ORDER, true>
+            <<<grid, kTX + 32, smem, s>>>(ld[src_buf], stv[src_buf ^ 1], k, wait_ns);
     } else {
         e = cudaFuncSetAttribute(step_kernel_tma<ORDER, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        step_kernel_tma<ORDER, false><<<grid, kTX + 32, smem, s>>>(ld[src_buf], stv[src_buf ^ 1], k);
+        step_kernel_tma<ORDER, false>
+            <<<grid, kTX + 32, smem, s>>>(ld[src_buf], stv[src_buf ^ 1], k, wait_ns);
     }
     return cudaGetLastError();
 }

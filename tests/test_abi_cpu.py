@@ -61,3 +61,18 @@ def test_null_handles_are_rejected(lib):
     assert lib.lb_sync(None) == abi.LB_ERR_ARG
     assert lib.lb_get_step(None) == -1
     lib.lb_destroy(None)
+
+
+def test_static_conserved_rejects_before_any_device_call(lib):
+    """lb_conserved_static checks its sizes and pointers before it touches the
+    device: a lattice one row past its 4096 x 4096 scratch limit is
+    LB_ERR_UNSUPPORTED, null pointers and bad sizes are LB_ERR_ARG.  The
+    pointers are never dereferenced on these paths (no GPU here)."""
+    fake = C.c_void_p(0x1000)
+    f = lib.lb_conserved_static
+    assert f(fake, abi.LB_FP32, 4096, 4097, 0.7, fake, None) == abi.LB_ERR_UNSUPPORTED
+    assert f(fake, abi.LB_FP64, 8192, 4096, 0.7, fake, None) == abi.LB_ERR_UNSUPPORTED
+    assert f(None, abi.LB_FP32, 4, 4, 0.7, fake, None) == abi.LB_ERR_ARG
+    assert f(fake, abi.LB_FP32, 4, 4, 0.7, None, None) == abi.LB_ERR_ARG
+    assert f(fake, abi.LB_FP32, 0, 4, 0.7, fake, None) == abi.LB_ERR_ARG
+    assert f(fake, 7, 4, 4, 0.7, fake, None) == abi.LB_ERR_ARG

@@ -1,5 +1,5 @@
 """Device structure factor vs the oracle's direct DFT on the same trajectory,
-and the radial read-out vs binning the half plane on the host."""
+and the radial read-out and first moments vs the oracle's binning and sums."""
 import numpy as np
 import pytest
 
@@ -38,29 +38,41 @@ def test_sample_now_matches_oracle():
     assert np.max(np.abs(Sg - So) / (So + So.mean())) < 1e-10
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 64), (128, 32)])
-def test_radial_bins_match_host_binning(nx, ny):
+@pytest.mark.parametrize("nx,ny", [(64, 64), (128, 32), (32, 64)])
+def test_radial_bins_match_oracle_binning(nx, ny):
+    """The device's radial read-out (mean S per bin, modes per bin) equals the
+    oracle's radial binning of the device's own half-plane S(k): counts index
+    exact, means to FP64 rounding of the (atomic) bin sums."""
+    from oracle import oracle as O
     g, _ = make_pair(nx, ny, -3.6, 1.0, 1e-5, precision="fp32", seed=9)
     g.sk_config(2, 2)
     g.step(40)
     S, n = g.structure_factor()
-    nb = max(nx, ny) // 2 + 2
-    bins, nbs = g.structure_factor(nbins=nb)
-    counts = g.structure_factor_counts(nb)
-    assert nbs == n
-    L = max(nx, ny)
-    kx = np.arange(nx // 2 + 1)
-    ky = np.fft.fftfreq(ny) * ny
-    qx, qy = np.meshgrid(kx * (L / nx), ky * (L / ny))
-    b = np.rint(np.sqrt(qx ** 2 + qy ** 2)).astype(int)
-    w = np.where((kx == 0) | (2 * kx == nx), 1, 2)[None, :] * np.ones((ny, 1), int)
-    w[0, 0] = 0
-    ref_c = np.bincount(b.ravel(), weights=w.ravel(), minlength=nb)[:nb]
-    ref_s = np.bincount(b.ravel(), weights=(w * S).ravel(), minlength=nb)[:nb]
-    assert np.array_equal(counts, ref_c.astype(np.int64))
-    ok = ref_c > 0
-    assert np.allclose(bins[ok], ref_s[ok] / ref_c[ok], rtol=1e-12)
-    assert np.all(np.isnan(bins[~ok]))
+    for nb in (max(nx, ny) // 2 + 2, 7):
+        bins, nbs = g.structure_factor(nbins=nb)
+        counts = g.structure_factor_counts(nb)
+        assert nbs == n
+        ref_m, ref_c = O.radial_bins(S, nx, ny, nb)
+        assert np.array_equal(counts, ref_c)
+        ok = ref_c > 0
+        assert np.allclose(bins[ok], ref_m[ok], rtol=1e-12, atol=0.0)
+        assert np.all(np.isnan(bins[~ok]))
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 64), (128, 32)])
+def test_sk_moments_match_oracle(nx, ny):
+    """The device's first moments of S(k) (the domain size L(t) of the quench
+    driver) equal the oracle's sums over the full plane."""
+    from oracle import oracle as O
+    g, _ = make_pair(nx, ny, -5.0, 1.0, 1e-5, precision="fp32", seed=3, amp=0.05)
+    g.sk_config(5, 5)
+    g.step(50)
+    S, _ = g.structure_factor()
+    m = g.sk_moments()
+    s0, s1 = O.sk_first_moments(S, nx, ny)
+    assert abs(m[0] / s0 - 1.0) < 1e-12
+    assert abs(m[1] / s1 - 1.0) < 1e-12
+    assert abs(g.domain_size() / (2 * np.pi * s0 / s1) - 1.0) < 1e-12
 
 
 def test_unsupported_sizes_for_sk():
