@@ -69,8 +69,10 @@ extern "C" {
 #define LB_FP64 1           /* deviations stored in FP64                      */
 
 /* ---- step kernel selection (lb_set_kernel) -------------------------------- */
-#define LB_KERNEL_AUTO 0    /* the faster kernel for this GPU (currently plain)   */
-#define LB_KERNEL_PLAIN 1   /* pulls with coalesced global loads                  */
+#define LB_KERNEL_AUTO 0    /* the fastest kernel for this GPU and lattice: on
+                               GB300 overlap for nx >= 1024, else plain          */
+#define LB_KERNEL_PLAIN 1   /* coalesced global loads; strips of 128 columns and a
+                               fifth warp for the halo columns' pseudopotential   */
 #define LB_KERNEL_TMA 2     /* rows staged in shared memory by cp.async.bulk.tensor
                                (FP32 and nx a multiple of 128 only)               */
 #define LB_KERNEL_OVERLAP 3 /* coalesced global loads; strips of 128 - 2H columns
@@ -323,6 +325,14 @@ int lb_ens_get_launch(const lb_ens *e);
  * re-initialised (lb_ens_init) before it is used again.  Synchronises the
  * ensemble's stream.  Errors: LB_ERR_ARG, LB_ERR_CUDA. */
 int lb_ens_set_wait_ns(lb_ens *e, long long ns);
+/* Strip layout of the ensemble's step kernels, as lb_set_kernel:
+ * LB_KERNEL_PLAIN (128-column strips and a halo warp) or LB_KERNEL_OVERLAP
+ * (strips of 128 - 2H columns whose halo the CTA's own threads pull);
+ * LB_KERNEL_AUTO takes the faster one on this GPU.  Same results either way.
+ * Synchronises the ensemble's stream and rebuilds the tile list.
+ * lb_ens_get_kernel returns the layout in use.  Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+int lb_ens_set_kernel(lb_ens *e, int mode);
+int lb_ens_get_kernel(const lb_ens *e);
 /* Advance every replica n steps (asynchronous); windows of steps replay
  * captured CUDA graphs. */
 int lb_ens_step(lb_ens *e, int n);

@@ -37,6 +37,7 @@ EXPORTED = [
     "lb_structure_factor_counts", "lb_conserved", "lb_save", "lb_load",
     "lb_device_ptr", "lb_stream", "lb_strerror", "lb_conserved_static",
     "lb_set_kernel", "lb_get_kernel", "lb_set_wait_ns", "lb_ens_set_wait_ns",
+    "lb_ens_set_kernel", "lb_ens_get_kernel",
     "lb_ens_create", "lb_ens_destroy", "lb_ens_init", "lb_ens_sk_config",
     "lb_ens_set_strip_height", "lb_ens_autotune", "lb_ens_step", "lb_ens_sync",
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
@@ -131,6 +132,8 @@ def bind(L):
         "lb_set_kernel": (C.c_int, [P, C.c_int]),
         "lb_set_wait_ns": (C.c_int, [P, C.c_longlong]),
         "lb_ens_set_wait_ns": (C.c_int, [P, C.c_longlong]),
+        "lb_ens_set_kernel": (C.c_int, [P, C.c_int]),
+        "lb_ens_get_kernel": (C.c_int, [P]),
         "lb_nn_set_wait_ns": (C.c_int, [C.c_longlong]),
         "lb_get_kernel": (C.c_int, [P]),
         "lb_ens_create": (C.c_int, [C.POINTER(P), C.POINTER(lb_replica), C.c_int, C.c_int,
@@ -392,6 +395,14 @@ def lb_ens_set_launch(h, mode):
 
 def lb_ens_get_launch(h):
     return load().lb_ens_get_launch(h)
+
+
+def lb_ens_set_kernel(h, mode):
+    _check(load().lb_ens_set_kernel(h, int(mode)), "lb_ens_set_kernel")
+
+
+def lb_ens_get_kernel(h):
+    return load().lb_ens_get_kernel(h)
 
 
 def lb_ens_set_wait_ns(h, ns):

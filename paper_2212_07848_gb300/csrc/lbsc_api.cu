@@ -95,7 +95,7 @@ int validate(const lb_params *p) {
 }
 
 int default_strip(int nx, int ny) {
-    const long gx = (nx + kStepTX - 1) / kStepTX;
+    const long gx = nx >= 1024 ? (nx + kStepTX - 3) / (kStepTX - 2) : (nx + kStepTX - 1) / kStepTX;
     long target = (long)ny * gx / (152 * 4);
     int h = 8;
     while (h < 32 && h * 2 <= target) h *= 2;
@@ -350,12 +350,17 @@ int lb_set_wait_ns(lb_ctx *h, long long ns) {
 
 int lb_get_kernel(const lb_ctx *h) {
     if (!h) return LB_ERR_ARG;
-    // AUTO takes the plain-load kernel: on GB300 it measures faster than the
-    // staged one for this step (the step is issue-bound, and the staged
-    // kernel's per-row mbarrier hand-off costs more than the loads it saves).
+    // AUTO: on GB300 the overlapped-strip kernel is the fastest for lattices
+    // at least 1024 columns wide (the step is issue-bound; without a halo warp
+    // every resident warp collides, 8 CTAs of 4 warps per SM instead of 6 of
+    // 5: 73 against 67 GLUPS at 4096^2), while narrower lattices lose more to
+    // its partly filled last strip (a power-of-two width leaves a strip of a
+    // few columns) and take the halo-warp kernel.  The staged kernel's per-row
+    // mbarrier hand-off costs more than the loads it saves.
     if (h->kernel_mode == LB_KERNEL_TMA && h->maps.ok) return LB_KERNEL_TMA;
+    if (h->kernel_mode == LB_KERNEL_PLAIN) return LB_KERNEL_PLAIN;
     if (h->kernel_mode == LB_KERNEL_OVERLAP) return LB_KERNEL_OVERLAP;
-    return LB_KERNEL_PLAIN;
+    return h->p.nx >= 1024 ? LB_KERNEL_OVERLAP : LB_KERNEL_PLAIN;
 }
 
 int lb_step(lb_ctx *h, int n) {

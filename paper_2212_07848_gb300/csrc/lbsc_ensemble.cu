@@ -5,7 +5,9 @@
 // of Figs. 2-3 of arXiv:2212.07848) need many independent realisations; one
 // small lattice cannot fill a GB300 and a launch per replica per step is
 // launch-bound.  Here every step of every replica is one launch over a tile
-// list (replica, 128-column strip, row strip) sorted largest replica first;
+// list (replica, strip of 128 - 2H columns, row strip) sorted largest
+// replica first (the overlapped layout of the single-lattice kernel: 128
+// threads per CTA pull the strip and its halo columns);
 // each CTA copies its replica's parameters into shared memory and runs the
 // same per-strip code as the single-lattice kernel, so a replica evolves
 // bit-identically to a single lattice with the same seed and replica index.
@@ -95,8 +97,11 @@ __device__ __forceinline__ void fill_tile_params(KParams<float> &sp, const EnsRe
     for (int k = 0; k < 6; ++k) sp.amp[k] = R.amp[k];
 }
 
-template <int ORDER>
-__global__ void __launch_bounds__(kStepTX + 32, ORDER == 4 ? 6 : 4)
+// OV: the overlapped layout (kStepTX threads, strips of kStepTX - 2H
+// columns); otherwise strips of kStepTX columns and a halo warp.
+template <int ORDER, bool OV>
+__global__ void __launch_bounds__(OV ? kStepTX : kStepTX + 32, OV ? (ORDER == 4 ? 8 : 5)
+                                                                  : (ORDER == 4 ? 6 : 4))
 ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles, int ntiles,
                 EnsClock *clk, int *flag, const EnsKeys keys, int sk_every, long long sk_start) {
     __shared__ KParams<float> sp;
@@ -117,10 +122,17 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
         s_cur = cur;
     }
     __syncthreads();
-    if (s_sample)
-        step_strip<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
-    else
-        step_strip<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+    if (OV) {
+        if (s_sample)
+            step_strip_ov<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        else
+            step_strip_ov<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+    } else {
+        if (s_sample)
+            step_strip<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        else
+            step_strip<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -178,8 +190,9 @@ __device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abo
     }
 }
 
-template <int ORDER>
-__global__ void __launch_bounds__(kStepTX + 32, ORDER == 4 ? 6 : 4)
+template <int ORDER, bool OV>
+__global__ void __launch_bounds__(OV ? kStepTX : kStepTX + 32, OV ? (ORDER == 4 ? 8 : 5)
+                                                                  : (ORDER == 4 ? 6 : 4))
 ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles,
                    int ntiles, const int *__restrict__ rep_ntiles, uint32_t *done, int nrep,
                    EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys, int nsteps,
@@ -214,10 +227,19 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
                 go = false;
                 break;
             }
-            if (sp.drho_out)
-                step_strip<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
-            else
-                step_strip<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            if (OV) {
+                if (sp.drho_out)
+                    step_strip_ov<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0,
+                                                            tile.y1);
+                else
+                    step_strip_ov<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0,
+                                                             tile.y1);
+            } else {
+                if (sp.drho_out)
+                    step_strip<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+                else
+                    step_strip<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            }
             __syncthreads();   // the tile's stores are done, and sp may be refilled
             if (threadIdx.x == 0) {
                 __threadfence();
@@ -313,6 +335,8 @@ struct lb_ens {
     uint32_t *d_done = nullptr;                // per-replica completion counters
     EnsCtl *d_ctl = nullptr;
     int persist_grid = 0;                      // co-resident CTAs of the persistent kernel
+    int kernel_mode = LB_KERNEL_AUTO;          // LB_KERNEL_PLAIN or _OVERLAP (strip layout)
+    bool ov = false;                           // the layout in use
 };
 
 namespace {
@@ -377,8 +401,9 @@ int build_tiles(lb_ens *e) {
     for (int r : order) {
         const int nx = e->reps[r].nx, ny = e->reps[r].ny;
         const int h = std::min(e->strip_h, ny);
+        const int cols = e->ov ? kStepTX - 2 * (e->stencil == 4 ? 1 : 2) : kStepTX;
         for (int y0 = 0; y0 < ny; y0 += h)
-            for (int x0 = 0; x0 < nx; x0 += kStepTX) {
+            for (int x0 = 0; x0 < nx; x0 += cols) {
                 tiles.push_back({r, x0, y0, std::min(y0 + h, ny)});
                 per_rep[r] += 1;
             }
@@ -399,23 +424,48 @@ int build_tiles(lb_ens *e) {
 // One step of every replica; `sample` also runs the S(k) sample of all
 // replicas (the step kernel then writes delta rho: the device decides from
 // its own step counter, which agrees with the host's).
-template <int ORDER>
+template <int ORDER, bool OV>
 cudaError_t launch_persist_t(lb_ens *e, int nsteps, int sample_last) {
     void *args[] = {&e->d_reps, &e->d_tiles,  &e->ntiles, &e->d_rep_ntiles,
                     &e->d_done, &e->nrep,     &e->d_ctl,  &e->d_clk,
                     &e->d_flag, &e->keys,     &nsteps,    &sample_last};
     const int grid = std::min(e->persist_grid, e->ntiles);
-    return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER>, dim3(grid),
-                                       dim3(kStepTX + 32), args, 0, e->stream);
+    return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER, OV>, dim3(grid),
+                                       dim3(OV ? kStepTX : kStepTX + 32), args, 0, e->stream);
+}
+
+template <int ORDER>
+cudaError_t launch_persist_o(lb_ens *e, int nsteps, int sample_last) {
+    return e->ov ? launch_persist_t<ORDER, true>(e, nsteps, sample_last)
+                 : launch_persist_t<ORDER, false>(e, nsteps, sample_last);
+}
+
+// Co-resident CTAs of the persistent kernel of the ensemble's layout.
+cudaError_t persist_occupancy(lb_ens *e) {
+    int per_sm = 0, nsm = 0;
+    const void *k;
+    if (e->ov)
+        k = e->stencil == 4   ? (const void *)ens_persist_kernel<4, true>
+            : e->stencil == 6 ? (const void *)ens_persist_kernel<6, true>
+                              : (const void *)ens_persist_kernel<8, true>;
+    else
+        k = e->stencil == 4   ? (const void *)ens_persist_kernel<4, false>
+            : e->stencil == 6 ? (const void *)ens_persist_kernel<6, false>
+                              : (const void *)ens_persist_kernel<8, false>;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k, e->ov ? kStepTX : kStepTX + 32, 0);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->dev);
+    e->persist_grid = per_sm * nsm;
+    return err;
 }
 
 // `nsteps` steps of every replica in one persistent launch (the last one
 // sampling if sample_last), then the S(k) sample when sampling.
 cudaError_t launch_ens_persistent(lb_ens *e, int nsteps, bool sample_last) {
     const int sl = sample_last ? 1 : 0;
-    cudaError_t err = e->stencil == 4   ? launch_persist_t<4>(e, nsteps, sl)
-                      : e->stencil == 6 ? launch_persist_t<6>(e, nsteps, sl)
-                                        : launch_persist_t<8>(e, nsteps, sl);
+    cudaError_t err = e->stencil == 4   ? launch_persist_o<4>(e, nsteps, sl)
+                      : e->stencil == 6 ? launch_persist_o<6>(e, nsteps, sl)
+                                        : launch_persist_o<8>(e, nsteps, sl);
     if (err != cudaSuccess || !sample_last) return err;
     ens_rows_kernel<<<e->nrows, 512, (size_t)e->max_nx * sizeof(float2), e->stream>>>(e->d_reps,
                                                                                        e->d_rows);
@@ -428,15 +478,20 @@ cudaError_t launch_ens_persistent(lb_ens *e, int nsteps, bool sample_last) {
 
 cudaError_t launch_ens_step(lb_ens *e, bool sample) {
     const int sk_every = sample ? e->sk_every : 0;
-    if (e->stencil == 4)
-        ens_step_kernel<4><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
-            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
-    else if (e->stencil == 6)
-        ens_step_kernel<6><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
-            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
-    else
-        ens_step_kernel<8><<<e->ntiles, kStepTX + 32, 0, e->stream>>>(
-            e->d_reps, e->d_tiles, e->ntiles, e->d_clk, e->d_flag, e->keys, sk_every, e->sk_start);
+#define ENS_STEP(O, V, B)                                                                     \
+    ens_step_kernel<O, V><<<e->ntiles, B, 0, e->stream>>>(e->d_reps, e->d_tiles, e->ntiles,   \
+                                                          e->d_clk, e->d_flag, e->keys,       \
+                                                          sk_every, e->sk_start)
+    if (e->ov) {
+        if (e->stencil == 4) ENS_STEP(4, true, kStepTX);
+        else if (e->stencil == 6) ENS_STEP(6, true, kStepTX);
+        else ENS_STEP(8, true, kStepTX);
+    } else {
+        if (e->stencil == 4) ENS_STEP(4, false, kStepTX + 32);
+        else if (e->stencil == 6) ENS_STEP(6, false, kStepTX + 32);
+        else ENS_STEP(8, false, kStepTX + 32);
+    }
+#undef ENS_STEP
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !sample) return err;
     ens_rows_kernel<<<e->nrows, 512, (size_t)e->max_nx * sizeof(float2), e->stream>>>(e->d_reps,
@@ -574,16 +629,7 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
         const EnsCtl c0 = {0u, 0, (unsigned long long)kEnsWaitNs};
         err = cudaMemcpy(e->d_ctl, &c0, sizeof(EnsCtl), cudaMemcpyHostToDevice);
     }
-    if (err == cudaSuccess) {
-        int per_sm = 0, nsm = 0;
-        const void *k = stencil == 4   ? (const void *)ens_persist_kernel<4>
-                        : stencil == 6 ? (const void *)ens_persist_kernel<6>
-                                       : (const void *)ens_persist_kernel<8>;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStepTX + 32, 0);
-        if (err == cudaSuccess)
-            err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->dev);
-        e->persist_grid = per_sm * nsm;
-    }
+    if (err == cudaSuccess) err = persist_occupancy(e);
     if (err != cudaSuccess) {
         free_ens(e);
         delete e;
@@ -729,6 +775,25 @@ int lb_ens_set_launch(lb_ens *e, int mode) {
 }
 
 int lb_ens_get_launch(const lb_ens *e) { return e ? e->launch_mode : LB_ERR_ARG; }
+
+int lb_ens_set_kernel(lb_ens *e, int mode) {
+    if (!e || (mode != LB_KERNEL_AUTO && mode != LB_KERNEL_PLAIN && mode != LB_KERNEL_OVERLAP))
+        return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    e->kernel_mode = mode;
+    // AUTO: the halo-warp layout.  Replica widths are powers of two up to a
+    // few hundred columns, where the overlapped layout's last strip holds
+    // only a few columns (256 replicas of {64..512}^2: 61 against 56 GLUPS).
+    e->ov = mode == LB_KERNEL_OVERLAP;
+    ENS_CHECK(persist_occupancy(e));
+    return build_tiles(e);
+}
+
+int lb_ens_get_kernel(const lb_ens *e) {
+    if (!e) return LB_ERR_ARG;
+    return e->ov ? LB_KERNEL_OVERLAP : LB_KERNEL_PLAIN;
+}
 
 int lb_ens_set_wait_ns(lb_ens *e, long long ns) {
     if (!e) return LB_ERR_ARG;

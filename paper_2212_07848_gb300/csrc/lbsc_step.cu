@@ -8,14 +8,17 @@
 // Storing deviations keeps the relative precision of density fluctuations of
 // size sqrt(kT) in FP32.
 //
-// Work decomposition: a CTA owns a strip of kStepTX columns and sweeps
-// strip_h rows downwards.  Each iteration pulls one new row (one thread per
-// column, plus one extra warp for the 2H halo columns), writes the pseudopotential
-// deviation of that row into a shared-memory ring of rows, and collides the
-// row H above it, whose 2H+1 pseudopotential rows are then complete.  The
-// pulled populations of the last H+1 rows stay in registers, so every
-// population is read from DRAM once per step (halo rows and columns are
-// re-read from L2 only at strip boundaries).
+// Work decomposition: a CTA owns a strip of columns and sweeps strip_h rows
+// downwards.  Each iteration pulls one new row (one thread per column),
+// writes the pseudopotential deviation of that row into a shared-memory ring
+// of rows, and collides the row H above it, whose 2H+1 pseudopotential rows
+// are then complete.  The pulled populations of the last H+1 rows stay in
+// registers, so every population is read from DRAM once per step (halo rows
+// and columns are re-read from L2 only at strip boundaries).  Two layouts
+// of the halo columns: step_kernel (128 columns per CTA and a fifth warp
+// that only pulls the 2H halo columns) and step_kernel_ov (128 threads per
+// CTA covering 128 - 2H interior columns plus their halo, so every warp
+// collides and 8 CTAs of 4 warps fit an SM; the faster one on GB300).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,8 +39,35 @@ __global__ void __launch_bounds__(kStepTX + 32) step_kernel(const KParams<T> p) 
 }
 
 
+// Overlapped layout: kStepTX threads per CTA, kStepTX - 2H interior columns,
+// the halo pseudopotentials recomputed by the CTA's own edge threads.
+template <typename T, int ORDER, bool SAMPLE, bool UNIT = false>
+__global__ void __launch_bounds__(kStepTX) step_kernel_ov(const KParams<T> p) {
+    const int y0 = blockIdx.y * p.strip_h;
+    step_strip_ov<T, ORDER, SAMPLE, false, UNIT>(p, p.rk, blockIdx.x * ov_cols<ORDER>(), y0,
+                                                 min(y0 + p.strip_h, p.ny));
+}
+
+template <typename T, int ORDER>
+static cudaError_t launch_ov_t(const StepArgs &a, cudaStream_t s) {
+    KParams<T> k = make_params<T>(a);
+    constexpr int C = ov_cols<ORDER>();
+    dim3 grid((a.nx + C - 1) / C, (a.ny + a.strip_h - 1) / a.strip_h);
+    const bool unit =
+        std::is_same<T, float>::value && a.gamma == 0.0 && a.gamma_b == 0.0 && a.gamma_g == 0.0;
+    if (unit) {
+        if (a.drho_out) step_kernel_ov<T, ORDER, true, true><<<grid, kStepTX, 0, s>>>(k);
+        else step_kernel_ov<T, ORDER, false, true><<<grid, kStepTX, 0, s>>>(k);
+    } else {
+        if (a.drho_out) step_kernel_ov<T, ORDER, true><<<grid, kStepTX, 0, s>>>(k);
+        else step_kernel_ov<T, ORDER, false><<<grid, kStepTX, 0, s>>>(k);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, int ORDER>
 static cudaError_t launch_t(const StepArgs &a, cudaStream_t s) {
+    if (a.layout == 1) return launch_ov_t<T, ORDER>(a, s);
     KParams<T> k = make_params<T>(a);
     dim3 grid((a.nx + kStepTX - 1) / kStepTX, (a.ny + a.strip_h - 1) / a.strip_h);
     // FP32 with every relaxation rate 1 (tau = 1 BGK, the usual setting) takes

@@ -136,4 +136,109 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
     }
 }
 
+// Columns per CTA of the overlapped layout: a CTA of kStepTX threads owns
+// kStepTX - 2H interior columns and recomputes the pseudopotential of the H
+// halo columns on each side itself (each of its threads pulls one column),
+// so no warp is set aside for the halo and every warp does the same work up
+// to the row barrier.
+template <int ORDER> __host__ __device__ constexpr int ov_cols() {
+    return kStepTX - 2 * Stencil<ORDER>::H;
+}
+
+// One CTA's work in the overlapped layout: interior columns [xs, xs + ncol),
+// ncol = min(ov_cols, nx - xs), rows [y0, y1).  Thread t handles column
+// xs - H + t (periodic); threads H .. H + ncol - 1 collide.  Same arithmetic,
+// same bits as step_strip.
+template <typename T, int ORDER, bool SAMPLE, bool CG = false, bool UNIT = false>
+__device__ __forceinline__ void step_strip_ov(const KParams<T> &p,
+                                              const uint32_t *__restrict__ rk, int xs, int y0,
+                                              int y1) {
+    using S = Stencil<ORDER>;
+    constexpr int H = S::H;
+    constexpr int RING = (H == 1) ? 4 : 8;   // >= 2H + 2 rows, power of two
+    __shared__ T s_dpsi[RING][kStepTX];
+
+    const int nx = p.nx, ny = p.ny;
+    const size_t plane = (size_t)nx * ny;
+    const int tx = threadIdx.x;
+    const int ncol = min(ov_cols<ORDER>(), nx - xs);
+    const bool active = tx < ncol + 2 * H;
+    const bool collides = tx >= H && tx < H + ncol;
+    const int x = active ? wrap_once(xs - H + tx, nx) : 0;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+
+    const T rho0 = p.rho0;
+
+    T q[H + 1][9];   // pulled populations of rows yy-H .. yy
+#pragma unroll
+    for (int r = 0; r <= H; ++r)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[r][i] = T(0);
+
+    const int it_end = (y1 - y0) + 2 * H;
+    T gn[9];
+    {
+        const int yc = wrap_once(y0 - H, ny);
+        const int ym = yc == 0 ? ny - 1 : yc - 1;
+        const int yp = yc == ny - 1 ? 0 : yc + 1;
+        if (active) pull<CG>(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+    }
+#pragma unroll 2
+    for (int it = 0; it < it_end; ++it) {
+        const int slot = it & (RING - 1);
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = gn[i];
+        if (it + 1 < it_end && active) {
+            const int yc = wrap_once(y0 - H + it + 1, ny);
+            const int ym = yc == 0 ? ny - 1 : yc - 1;
+            const int yp = yc == ny - 1 ? 0 : yc + 1;
+            pull<CG>(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
+        }
+        const int yy = y0 - H + it;
+        if (active) s_dpsi[slot][tx] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
+#pragma unroll
+        for (int r = 0; r < H; ++r)
+#pragma unroll
+            for (int i = 0; i < 9; ++i) q[r][i] = q[r + 1][i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[H][i] = g[i];
+        __syncthreads();
+        if (it < 2 * H || !collides) continue;
+
+        const int yr = yy - H;
+        const int cslot = (it - H) & (RING - 1);
+        T sx = T(0), sy = T(0);
+#pragma unroll
+        for (int a = 0; a < S::N; ++a) {
+            const HalfVec hv = S::v(a);
+            const T dpl = s_dpsi[(it - H + hv.ey) & (RING - 1)][tx + hv.ex];
+            const T dmi = s_dpsi[(it - H - hv.ey) & (RING - 1)][tx - hv.ex];
+            const T d = T(hv.w) * (dpl - dmi);
+            if (hv.ex != 0) sx += T(hv.ex) * d;
+            if (hv.ey != 0) sy += T(hv.ey) * d;
+        }
+        const T psic = p.psi0 + s_dpsi[cslot][tx];
+        const T Fx = p.force_pref * psic * sx;
+        const T Fy = p.force_pref * psic * sy;
+
+        T f[9];
+        collide<T, UNIT>(q[0], Fx, Fy, p, rk, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
+
+        const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
+        p.dst[o] = f[0];
+        p.dst[o + pl] = f[1];
+        p.dst[o + 2u * pl] = f[2];
+        p.dst[o + 3u * pl] = f[3];
+        p.dst[o + 4u * pl] = f[4];
+        p.dst[o + 5u * pl] = f[5];
+        p.dst[o + 6u * pl] = f[6];
+        p.dst[o + 7u * pl] = f[7];
+        p.dst[o + 8u * pl] = f[8];
+        if (SAMPLE) p.drho_out[o] = sum9(q[0]);
+        if (!isfinite(f[1] + f[5])) atomicOr(p.flag, LB_STEP_NONFINITE);
+    }
+}
+
 }  // namespace lbsc

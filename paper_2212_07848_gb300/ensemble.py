@@ -43,6 +43,14 @@ class Ensemble:
     def launch(self):
         return abi.lb_ens_get_launch(self._h)
 
+    def set_kernel(self, mode):
+        """Strip layout: abi.LB_KERNEL_AUTO / LB_KERNEL_PLAIN / LB_KERNEL_OVERLAP."""
+        abi.lb_ens_set_kernel(self._h, mode)
+
+    @property
+    def kernel(self):
+        return abi.lb_ens_get_kernel(self._h)
+
     def set_strip_height(self, rows):
         abi.lb_ens_set_strip_height(self._h, rows)
 

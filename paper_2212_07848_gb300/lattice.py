@@ -139,7 +139,7 @@ class Lattice:
         abi.lb_set_strip_height(self._h, rows)
 
     def set_kernel(self, mode):
-        """abi.LB_KERNEL_AUTO / LB_KERNEL_PLAIN / LB_KERNEL_TMA."""
+        """abi.LB_KERNEL_AUTO / LB_KERNEL_PLAIN / LB_KERNEL_TMA / LB_KERNEL_OVERLAP."""
         abi.lb_set_kernel(self._h, mode)
 
     @property

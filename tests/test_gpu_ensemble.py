@@ -26,11 +26,14 @@ def _single(r, rep, seed, amp, sk=None):
     return g
 
 
+@pytest.mark.parametrize("kernel", [1, 3])        # strip layouts: halo warp, overlapped
 @pytest.mark.parametrize("launch", [0, 1])        # per-step launches, persistent windows
 @pytest.mark.parametrize("strip", [8, 32])
-def test_replicas_match_single_lattices(strip, launch):
+def test_replicas_match_single_lattices(strip, launch, kernel):
     from paper_2212_07848_gb300.ensemble import Ensemble
     e = Ensemble(REPS, seed=77)
+    e.set_kernel(kernel)
+    assert e.kernel == kernel
     e.set_launch(launch)
     assert e.launch == launch
     e.set_strip_height(strip)
@@ -112,10 +115,12 @@ def test_persistent_launch_many_tiles_per_cta():
             (1024, 256, -4.0, 1.1, 1e-6, 0.68), (256, 256, -4.6, 1.0, 1e-6, LN2)]
     a, b = Ensemble(reps, seed=9), Ensemble(reps, seed=9)
     a.set_launch(abi.LB_ENS_PERSISTENT)
+    b.set_kernel(abi.LB_KERNEL_OVERLAP)         # the other strip layout: the same bits
     for e in (a, b):
         e.set_strip_height(8)
         e.init(0.01)
         e.sk_config(16, 16)
+    assert a.kernel == abi.LB_KERNEL_PLAIN     # automatic layout for power-of-two widths
     assert a.num_tiles > 1000          # above the 6 x 152 resident CTAs
     a.step(3)
     a.step(16 * 4 + 5)      # sampling windows replayed as persistent launches

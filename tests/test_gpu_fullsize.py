@@ -18,7 +18,9 @@ def test_fullsize_4096_one_step_sampled_sites():
     from paper_2212_07848_gb300.lattice import Lattice
     nx = ny = 4096
     G, tau, kT, seed = -5.0, 1.0, 1e-6, 100
+    from paper_2212_07848_gb300 import abi
     g = Lattice(nx, ny, G, tau, kT)
+    assert g.kernel == abi.LB_KERNEL_OVERLAP          # the kernel the benchmark times
     g.init(LN2, seed, 0.01)
     c0 = g.conserved()
     g.step(3)
@@ -32,8 +34,12 @@ def test_fullsize_4096_one_step_sampled_sites():
     rng = np.random.default_rng(1)
     xs = list(rng.integers(0, nx, 3000))
     ys = list(rng.integers(0, ny, 3000))
-    edge_x = [0, 1, 2, nx - 3, nx - 2, nx - 1, 127, 128, 129, 255, 256, 2047, 2048]
-    edge_y = [0, 1, 2, ny - 3, ny - 2, ny - 1, 63, 64, 65, 127, 128, 2047, 2048]
+    # strip boundaries of both layouts: 128-column strips (halo warp) and
+    # 126-column strips (overlapped, the automatic choice; the last strip
+    # starts at 32 x 126 = 4032), and row strips of 32
+    edge_x = [0, 1, 2, nx - 3, nx - 2, nx - 1, 125, 126, 127, 128, 129, 251, 252, 255, 256,
+              2047, 2048, 4031, 4032, 4033]
+    edge_y = [0, 1, 2, ny - 3, ny - 2, ny - 1, 31, 32, 33, 63, 64, 65, 127, 128, 2047, 2048]
     for ex in edge_x:
         for ey in edge_y:
             xs.append(ex)

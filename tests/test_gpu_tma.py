@@ -57,12 +57,17 @@ def test_tma_kernel_matches_oracle():
 def test_kernel_selection():
     from paper_2212_07848_gb300 import abi
     from paper_2212_07848_gb300.lattice import Lattice
-    assert Lattice(256, 64, -3.6).kernel == abi.LB_KERNEL_PLAIN     # auto
+    assert Lattice(256, 64, -3.6).kernel == abi.LB_KERNEL_PLAIN      # auto, narrow
+    assert Lattice(1024, 8, -3.6).kernel == abi.LB_KERNEL_OVERLAP    # auto, wide
     t = Lattice(256, 64, -3.6)
     t.set_kernel(abi.LB_KERNEL_TMA)
     assert t.kernel == abi.LB_KERNEL_TMA
+    t.set_kernel(abi.LB_KERNEL_OVERLAP)
+    assert t.kernel == abi.LB_KERNEL_OVERLAP
+    t.set_kernel(abi.LB_KERNEL_PLAIN)
+    assert t.kernel == abi.LB_KERNEL_PLAIN
     assert Lattice(132, 64, -3.6).kernel == abi.LB_KERNEL_PLAIN
-    assert Lattice(256, 64, -3.6, precision="fp64").kernel == abi.LB_KERNEL_PLAIN
+    assert Lattice(1024, 8, -3.6, precision="fp64").kernel == abi.LB_KERNEL_OVERLAP
     g = Lattice(132, 64, -3.6)
     with pytest.raises(abi.LbError) as e:
         g.set_kernel(abi.LB_KERNEL_TMA)
