@@ -224,6 +224,66 @@ def ensemble_leg(stream_ptr, steps=200, nrep=256, seed=7):
             "sizes": "uniform {64,128,256,512}^2, G~U[-4.8,-3.6], rho0=ln2(1+U[-0.1,0.1])"}
 
 
+def conv_layer_leg(nb=8, h=128, cin=64, cout=128, reps=20):
+    """The surrogate's widest convolution (64 -> 128 channels on 8 images of
+    128^2, BF16 operands, FP32 accumulation, bias + ReLU) on the path the
+    network takes, forward and input gradient: mean time per call over
+    `reps` calls replayed from a captured CUDA graph (no host gaps), TFLOP/s
+    at 2 * 9 * cin * cout FLOP per output pixel, and the fraction of the
+    measured BF16 peak (burst: the layer is timed alone)."""
+    import torch
+
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    p = lambda t: C.c_void_p(t.data_ptr())
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((nb, h, h, cin), generator=g).to(torch.bfloat16).cuda()
+    w = (0.1 * torch.randn((9, cout, cin), generator=g)).to(torch.bfloat16).cuda()
+    b = torch.zeros(cout, device="cuda")
+    y = torch.empty((nb, h, h, cout), dtype=torch.bfloat16, device="cuda")
+    dy = torch.randn((nb, h, h, cout), generator=g).to(torch.bfloat16).cuda()
+    dx = torch.empty_like(x)
+    st = torch.cuda.Stream()
+    fwd = lambda: L.lb_nn_conv3x3(p(x), p(w), p(b), p(y), nb, h, h, cin, cout, 1, 0,
+                                  C.c_void_p(st.cuda_stream))
+    bwd = lambda: L.lb_nn_conv3x3(p(dy), p(w), None, p(dx), nb, h, h, cout, cin, 0, 1,
+                                  C.c_void_p(st.cuda_stream))
+    peak = _bf16_peak()
+    flop = 2.0 * 9 * cin * cout * nb * h * h
+    out = {"layer": f"{nb}x{h}^2 {cin}->{cout}", "peak_tflops": peak[0], "peak_kind": peak[1]}
+    for name, call in (("forward", fwd), ("input_gradient", bwd)):
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                if call() != 0:
+                    raise RuntimeError("lb_nn_conv3x3 failed")
+            st.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=st):
+                for _ in range(reps):
+                    call()
+            graph.replay()
+            st.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            graph.replay()
+            e.record(st)
+            e.synchronize()
+        us = a.elapsed_time(e) * 1e3 / reps
+        out[name] = {"us": us, "tflops": flop / (us * 1e-6) / 1e12,
+                     "frac": flop / (us * 1e-6) / 1e12 / peak[0]}
+    if L.lb_nn_status() != 0:
+        raise RuntimeError("a tensor-core wait gave up")
+    return out
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured burst"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def surrogate_leg(ntraj=64, ntest=8, size=2048, steps=6000, stride=200, iters=9000, batch=8,
                   seed=11):
     """Learned surrogate against the solver it stands in for: quench
@@ -537,6 +597,7 @@ def run_gpu(args, rank, world, local_rank):
     sur = None
     if rank == 0 and world == 1 and not args.no_surrogate:
         sur = surrogate_leg()
+        sur["conv_layer"] = conv_layer_leg()
     d3 = None
     if rank == 0 and world == 1 and not args.no_3d:
         d3 = d3q19_leg()

@@ -425,11 +425,11 @@ int lb3_sk_moments(lb3_ctx *h, double *host_out2);
  *              tap = 3 (dy+1) + (dx+1)), bias [cout] or NULL, act = ReLU if relu;
  *   dgrad = 1: the input gradient dx [..][cout] of a forward layer with
  *              weights w [9][cin][cout] from dy [..][cin] (bias NULL, relu 0).
- * Requires h * w % 128 == 0 and channel counts multiples of 16.  The forward
- * case runs on the tcgen05 tensor cores (accumulator in tensor memory) for
- * w % 128 == 0, cout in {16, 32, 64, 128} and, under the automatic choice,
- * cin in {32, 64} (where it measured faster); otherwise, and for dgrad, on
- * mma.sync. */
+ * Requires h * w % 128 == 0 and channel counts multiples of 16.  For w % 128
+ * == 0 and 16/32/64/128 channels both cases run on the tcgen05 tensor cores
+ * in a persistent kernel (accumulators in tensor memory, weights and input
+ * rows staged by TMA); otherwise on mma.sync (the forward case with 32 or 64
+ * input channels on a per-tile tcgen05 kernel when lb_nn_set_conv_path(2)). */
 int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int nb, int h, int w_,
                   int cin, int cout, int relu, int dgrad, void *stream);
 /* Weight and bias gradients, accumulated (+=) into FP32 dw [9][cout][cin] and
@@ -510,8 +510,11 @@ int lb_nn_adam(float *w, const float *g, float *m, float *v, void *w_bf16, size_
  * BF16(src - prev) (the field's last increment; 0 when prev is NULL), others 0. */
 int lb_nn_expand(const float *src, const float *prev, double gfeat, void *out, int c, size_t n,
                  void *stream);
-/* Process-wide choice of the forward convolution kernel: 0 = automatic
- * (default), 1 = mma.sync always, 2 = tcgen05 wherever it has a kernel. */
+/* Process-wide choice of the convolution kernel: 0 = automatic (default),
+ * 1 = mma.sync always, 2 = the per-tile tcgen05 forward kernel wherever it
+ * has one, 3 = the persistent tcgen05 kernel (forward and input gradient;
+ * weights staged once per CTA, a ring of input rows, double-buffered tensor
+ * memory) wherever it has one. */
 int lb_nn_set_conv_path(int path);
 /* Synchronises the device and reports whether a tensor-core convolution gave
  * up waiting on its mbarrier since the last call: LB_ERR_TIMEOUT (the flag is

@@ -2,10 +2,11 @@
 
     python -m paper_2212_07848_gb300.convbench --nb 8 --h 128 --cin 64 --cout 128 --path 0
 
-Runs the forward convolution (bias + ReLU) `--iters` times on random BF16
-inputs after `--warmup` calls and prints the mean time per call and the
-achieved TFLOP/s (2 * 9 * cin * cout FLOP per output pixel).  `--path`
-selects the kernel (0 automatic, 1 mma.sync, 2 tcgen05) as in
+Runs the forward convolution (bias + ReLU), or with `--dgrad` the input
+gradient of that layer, `--iters` times on random BF16 inputs after
+`--warmup` calls and prints the mean time per call and the achieved TFLOP/s
+(2 * 9 * cin * cout FLOP per output pixel).  `--path` selects the kernel (0
+automatic, 1 mma.sync, 2 tcgen05 per tile, 3 persistent tcgen05) as in
 `lb_nn_set_conv_path`.
 """
 import argparse
@@ -23,6 +24,7 @@ def main():
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--dgrad", action="store_true")
     a = ap.parse_args()
     import torch
     L = abi.load()
@@ -34,8 +36,14 @@ def main():
     y = torch.empty((a.nb, a.h, a.h, a.cout), dtype=torch.bfloat16, device="cuda")
     if L.lb_nn_set_conv_path(a.path) != 0:
         raise SystemExit("bad --path")
-    call = lambda: L.lb_nn_conv3x3(p(x), p(w), p(b), p(y), a.nb, a.h, a.h, a.cin, a.cout, 1, 0,
-                                   None)
+    if a.dgrad:   # dL/dx [..][cin] from dL/dy [..][cout] with the layer's weights
+        dy = torch.randn((a.nb, a.h, a.h, a.cout), generator=g).to(torch.bfloat16).cuda()
+        dx = torch.empty((a.nb, a.h, a.h, a.cin), dtype=torch.bfloat16, device="cuda")
+        call = lambda: L.lb_nn_conv3x3(p(dy), p(w), None, p(dx), a.nb, a.h, a.h, a.cout, a.cin,
+                                       0, 1, None)
+    else:
+        call = lambda: L.lb_nn_conv3x3(p(x), p(w), p(b), p(y), a.nb, a.h, a.h, a.cin, a.cout, 1,
+                                       0, None)
     for _ in range(a.warmup):
         if call() != 0:
             raise SystemExit("lb_nn_conv3x3 failed")
@@ -49,7 +57,8 @@ def main():
         raise SystemExit("a tensor-core wait gave up")
     ms = s.elapsed_time(e) / a.iters
     flop = 2.0 * 9 * a.cin * a.cout * a.nb * a.h * a.h
-    print(f"{a.nb}x{a.h}^2 {a.cin}->{a.cout} path {a.path}: {ms * 1e3:.1f} us, "
+    kind = "dgrad" if a.dgrad else "fwd"
+    print(f"{a.nb}x{a.h}^2 {a.cin}->{a.cout} {kind} path {a.path}: {ms * 1e3:.1f} us, "
           f"{flop / ms / 1e9:.1f} TFLOP/s")
 
 

@@ -26,6 +26,9 @@ namespace lbsc {
 
 // tcgen05 forward convolution (lbsc_nn_tc.cu) and the path selection.
 extern int nn_conv_path;
+cudaError_t launch_conv3x3_tcp(const void *x, const void *w, const float *bias, void *y, int nb,
+                               int h, int wd, int cin, int cout, int relu, int dgrad,
+                               cudaStream_t s);
 cudaError_t launch_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int nb,
                               int h, int wd, int cin, int cout, int relu, cudaStream_t s);
 
@@ -683,7 +686,16 @@ int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int 
         cout % 16 || cin < 16 || cout < 16)
         return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!dgrad && nn_conv_path != 1) {
+    if (dgrad && (bias || relu)) return LB_ERR_ARG;
+    // automatic choice: the persistent tcgen05 kernel wherever it has one
+    // (rows a multiple of 128 pixels), forward and input gradient; it measured
+    // fastest on GB300 for every layer of the surrogate
+    if (nn_conv_path == 0 || nn_conv_path == 3) {
+        const cudaError_t e = launch_conv3x3_tcp(x, w, bias, y, nb, h, wd, cin, cout, relu, dgrad, s);
+        if (e == cudaSuccess) return LB_OK;
+        if (e != cudaErrorNotSupported) return LB_ERR_CUDA;
+    }
+    if (!dgrad && nn_conv_path != 1 && nn_conv_path != 3) {
         const cudaError_t e = launch_conv3x3_tc(x, w, bias, y, nb, h, wd, cin, cout, relu, s);
         if (e == cudaSuccess) return LB_OK;
         if (e != cudaErrorNotSupported) return LB_ERR_CUDA;

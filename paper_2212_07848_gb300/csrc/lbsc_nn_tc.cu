@@ -16,15 +16,20 @@
 // epilogue.
 // The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
 // 32w..32w+31), adds the bias, applies ReLU and stores BF16.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "lbsc.h"
 
 namespace lbsc {
 
-int nn_conv_path = 0;   // 0: auto, 1: mma.sync, 2: tcgen05 wherever it has a kernel
+int nn_conv_path = 0;   // 0: auto, 1: mma.sync, 2: tcgen05 per-tile kernel wherever it
+                        // has one, 3: persistent tcgen05 kernel wherever it has one
 __device__ int g_nn_status;               // bit 0: an mbarrier wait gave up;
                                           // bit 1: tensor memory left allocated
 constexpr unsigned long long kTcWaitNs = 1000000000ull;   // default bound: 1 s
@@ -138,6 +143,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -304,7 +324,457 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised variant.  One CTA per SM (192 threads):
+//   warp 4  producer: stages the nine taps' weights of the CTA's output-channel
+//           block once, then input rows into a ring of R slots (cp.async,
+//           completion tracked on mbarriers), as far ahead as free slots allow;
+//   warp 5  MMA issuer (one thread): for each output row (128 pixels of one
+//           image row) the 9 x CIN/16 tcgen05.mma of its three input rows
+//           into one of two tensor-memory accumulators, then tcgen05.commit
+//           to release the accumulator to the epilogue and the input rows
+//           that no later row needs back to the producer;
+//   warps 0-3 epilogue: tcgen05.ld of the accumulator (warp w owns lanes
+//           32w .. 32w+31 = pixels), bias, ReLU, BF16 stores, then release
+//           the accumulator.
+// A CTA walks runs of consecutive output rows down a 128-pixel column band,
+// so each input row is staged once per run.  DG: the input gradient of a
+// forward layer (weights read transposed, taps mirrored), so the same kernel
+// serves forward and backward.  Every wait is bounded; a timeout stops every
+// role, and tensor memory is freed only after the committed MMAs finished.
+// ---------------------------------------------------------------------------
+template <int BN, int CIN>
+struct PCfg {
+    static constexpr int KC = CIN / 8;
+    // a staged K chunk (8 channels) of one input row holds pixels x0-8 ..
+    // x0+135 at 16-byte pitch; column c = pixel x0-1+c sits at byte 112 + 16c
+    // (the three copies that fill it start on 128-byte boundaries)
+    static constexpr uint32_t LBO_A = 144 * 16;
+    static constexpr uint32_t COL0 = 112;
+    static constexpr int ROW_BYTES = KC * LBO_A;
+    static constexpr int TAP_BYTES = BN * CIN * 2;
+    static constexpr int B_BYTES = 9 * TAP_BYTES;
+    static constexpr int R0 = (220 * 1024 - B_BYTES) / ROW_BYTES;
+    static constexpr int R = R0 < 4 ? 4 : (R0 > 8 ? 8 : R0);   // ring slots
+    static constexpr int A_BYTES = R * ROW_BYTES;
+    static constexpr int SMEM = A_BYTES + B_BYTES;
+    // B per tap: K chunk kc of output channel n at kc * BN * 16 + n * 16
+    static constexpr uint32_t LBO_B = BN * 16;
+    static constexpr uint32_t ROW_TX = (uint32_t)KC * 144 * 16;   // bytes landing per row
+    static constexpr uint32_t NCOLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : 256));
+};
+constexpr int kTcpThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int c0, int c1,
+                                          int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                             const volatile int *abort) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// tm_x: the input as [nb*H][W][CIN] with a box of 8 channels x 128 pixels
+// (tm_xh: 8 channels x 8 pixels, the halo copies); tm_w: the weights as
+// [9][Cout][CIN] with a box of 8 channels x BN output channels (forward only;
+// the input gradient transposes the weights while staging them).
+template <int BN, int CIN, bool DG>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_xh,
+                   const __grid_constant__ CUtensorMap tm_w, const bf16 *__restrict__ w,
+                   const float *__restrict__ bias, bf16 *__restrict__ y, int nb, int H, int W,
+                   int Cout, int relu, int ctas_per_block, int units_per_cta) {
+    using C = PCfg<BN, CIN>;
+    constexpr int R = C::R;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[R], slot_free[R], acc_full[2], acc_empty[2], wfull;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_drained;
+    __shared__ float s_bias[BN];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // 128-byte aligned base (the launch adds 128 bytes of slack)
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + C::A_BYTES;
+    constexpr uint32_t IDESC = idesc_bf16(128, BN);
+    const int bands = W / 128;
+    // this CTA's output-channel block and its share of that block's rows
+    const int n0 = (blockIdx.x / ctas_per_block) * BN;
+    const long units = (long)nb * H * bands;
+    const long u_begin = (long)(blockIdx.x % ctas_per_block) * units_per_cta;
+    const long u_end = min(units, u_begin + units_per_cta);
+    const uint64_t limit = g_nn_wait_ns;
+    volatile int *abort = &s_abort;
+
+    if (warp == 0) tmem_alloc(&s_tmem, C::NCOLS);
+    for (int i = tid; i < BN; i += kTcpThreads) s_bias[i] = bias ? bias[n0 + i] : 0.f;
+    if (DG) {
+        // w holds the forward layer's [9][CIN][Cout]; B[n][c] = w[8 - tap][c][n0 + n],
+        // staged by every thread (16-byte loads of 8 n, scattered 2-byte stores)
+        for (int v = tid; v < 9 * CIN * (BN / 8); v += kTcpThreads) {
+            const int tap = v / (CIN * (BN / 8)), rem = v - tap * (CIN * (BN / 8));
+            const int c = rem / (BN / 8), nc = rem - c * (BN / 8);
+            const uint4 q = *reinterpret_cast<const uint4 *>(
+                w + ((size_t)(8 - tap) * CIN + c) * Cout + n0 + nc * 8);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&q);
+            uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 3) * C::LBO_B + nc * 128 + (c & 7) * 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16 *>(d + j * 16) = e[j];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (tid == kTcpThreads - 1) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&slot_free[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        mbar_init(&wfull, 1);
+        s_abort = 0;
+        s_drained = 1;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // unit u -> (image, band, row); rows vary fastest.  A run: consecutive
+    // rows of one (image, band), at most to the end of the CTA's share.
+    auto run_at = [&](long u, int &b, int &x0, int &row0, int &len) {
+        row0 = (int)(u % H);
+        const long r = u / H;
+        x0 = (int)(r % bands) * 128;
+        b = (int)(r / bands);
+        len = (int)min(u_end - u, (long)(H - row0));
+    };
+
+    if (warp == 4) {
+        // ---------------- producer (one thread issues the bulk copies) ----------------
+        long seq = 0;
+        if (lane == 0) {
+            if (!DG) {
+                mbar_expect_tx(&wfull, (uint32_t)C::B_BYTES);
+                for (int tap = 0; tap < 9; ++tap)
+                    for (int kc = 0; kc < C::KC; ++kc)
+                        tma_load3(sB + tap * C::TAP_BYTES + kc * C::LBO_B, &tm_w, kc * 8, n0, tap,
+                                  &wfull);
+            }
+            for (long u = u_begin; u < u_end && !*abort;) {
+                int b, x0, row0, len;
+                run_at(u, b, x0, row0, len);
+                const int xl = x0 == 0 ? W - 8 : x0 - 8;          // left halo (periodic)
+                const int xr = x0 + 128 == W ? 0 : x0 + 128;      // right halo
+                bool stop = false;
+                for (int j = 0; j < len + 2; ++j, ++seq) {
+                    const int slot = (int)(seq % R);
+                    if (seq >= R &&
+                        !mbar_wait_ab(&slot_free[slot], (uint32_t)((seq / R - 1) & 1), limit, abort)) {
+                        *abort = 1;
+                        stop = true;
+                        break;
+                    }
+                    int ys = row0 - 1 + j;
+                    ys = ys < 0 ? ys + H : (ys >= H ? ys - H : ys);
+                    const int yy = b * H + ys;
+                    uint8_t *dst = sA + slot * C::ROW_BYTES;
+                    mbar_expect_tx(&full[slot], C::ROW_TX);
+                    for (int kc = 0; kc < C::KC; ++kc) {
+                        uint8_t *ch = dst + kc * C::LBO_A;
+                        tma_load3(ch, &tm_xh, kc * 8, xl, yy, &full[slot]);              // x0-8 .. x0-1
+                        tma_load3(ch + 128, &tm_x, kc * 8, x0, yy, &full[slot]);         // x0 .. x0+127
+                        tma_load3(ch + 128 + 2048, &tm_xh, kc * 8, xr, yy, &full[slot]); // x0+128 ..
+                    }
+                }
+                if (stop) break;
+                u += len;
+            }
+            // every copy must land before the CTA exits (the barriers and the
+            // buffers live in its shared memory): wait, with the default
+            // bound, for the weights and the last R rows issued
+            if (!DG) mbar_wait(&wfull, 0, kTcWaitNs);
+            for (long sq = seq > R ? seq - R : 0; sq < seq; ++sq)
+                mbar_wait(&full[sq % R], (uint32_t)((sq / R) & 1), kTcWaitNs);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        // ---------------- MMA issuer ----------------
+        long t = 0, seq0 = 0;
+        bool ok = true;
+        int nfreed[C::R];   // commits issued to each slot_free barrier
+        for (int i = 0; i < R; ++i) nfreed[i] = 0;
+        const uint64_t bdesc0 = smem_desc(smem_u32(sB), C::LBO_B, 128);
+        if (lane == 0) {
+            if (!DG) ok = mbar_wait_ab(&wfull, 0, limit, abort);
+            for (long u = u_begin; u < u_end && ok;) {
+                int b, x0, row0, len;
+                run_at(u, b, x0, row0, len);
+                for (int tt = 0; tt < len && ok; ++tt, ++t) {
+                    // the three input rows of output row tt: sequence numbers
+                    // seq0 + tt .. seq0 + tt + 2 (the first two were waited for
+                    // with the previous row, except at the start of a run)
+                    for (int q = tt == 0 ? 0 : 2; q < 3 && ok; ++q) {
+                        const long sq = seq0 + tt + q;
+                        ok = mbar_wait_ab(&full[sq % R], (uint32_t)((sq / R) & 1), limit, abort);
+                    }
+                    if (ok && t >= 2)
+                        ok = mbar_wait_ab(&acc_empty[t & 1], (uint32_t)(((t - 2) >> 1) & 1), limit,
+                                          abort);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t acc = tmem + (uint32_t)((t & 1) * BN);
+                    // descriptors of the row and tap bases; each MMA adds a
+                    // compile-time offset (in 16-byte units) to them, so the
+                    // issuing thread spends about one add per operand
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const uint64_t arow = smem_desc(
+                            smem_u32(sA + ((seq0 + tt + dy) % R) * C::ROW_BYTES) + C::COL0, C::LBO_A, 128);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                            for (int j = 0; j < CIN / 16; ++j)
+                                tc_mma(acc, arow + (uint64_t)((dx * 16 + 2 * j * C::LBO_A) >> 4),
+                                       bdesc0 + (uint64_t)(((3 * dy + dx) * C::TAP_BYTES + 2 * j * C::LBO_B) >> 4),
+                                       IDESC, (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
+                        }
+                        if (dy == 0) {
+                            // the row above is read by no later output row: hand
+                            // its slot back as soon as these MMAs finish
+                            const int sl = (int)((seq0 + tt) % R);
+                            tc_commit(&slot_free[sl]);
+                            ++nfreed[sl];
+                        }
+                    }
+                    tc_commit(&acc_full[t & 1]);
+                    if (tt + 1 == len) {
+                        // end of the run: its last two input rows are free too
+                        for (int q = 1; q < 3; ++q) {
+                            const int sl = (int)((seq0 + tt + q) % R);
+                            tc_commit(&slot_free[sl]);
+                            ++nfreed[sl];
+                        }
+                    }
+                }
+                seq0 += len + 2;
+                u += len;
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicOr(&g_nn_status, 1);
+            }
+            // drain: every MMA committed must finish before the accumulator
+            // is freed, and every commit's arrival must land before the CTA
+            // exits: wait (default bound) for the last phase of each barrier
+            // this thread committed to
+            bool drained = true;
+            for (long g = t > 2 ? t - 2 : 0; g < t; ++g)
+                drained = mbar_wait(&acc_full[g & 1], (uint32_t)((g >> 1) & 1), kTcWaitNs) && drained;
+            for (int i = 0; i < R; ++i)
+                if (nfreed[i] > 0)
+                    drained = mbar_wait(&slot_free[i], (uint32_t)((nfreed[i] - 1) & 1), kTcWaitNs) &&
+                              drained;
+            if (!drained) {
+                s_drained = 0;
+                atomicOr(&g_nn_status, 2);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-3) ----------------
+        long t = 0;
+        for (long u = u_begin; u < u_end && !*abort;) {
+            int b, x0, row0, len;
+            run_at(u, b, x0, row0, len);
+            for (int tt = 0; tt < len; ++tt, ++t) {
+                if (!mbar_wait_ab(&acc_full[t & 1], (uint32_t)((t >> 1) & 1), limit, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t lane_base =
+                    tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((t & 1) * BN);
+                bf16 *yout = y + (((size_t)b * H + row0 + tt) * W + x0 + warp * 32 + lane) * Cout + n0;
+                constexpr int CH = BN < 32 ? BN : 32;   // columns per tensor-memory load
+#pragma unroll
+                for (int col = 0; col < BN; col += CH) {
+                    uint32_t rr[CH];
+                    if constexpr (CH == 32) tmem_ld32(lane_base + col, rr);
+                    else tmem_ld16(lane_base + col, rr);
+                    uint32_t packed[CH / 2];
+#pragma unroll
+                    for (int q = 0; q < CH / 2; ++q) {
+                        float v0 = __uint_as_float(rr[2 * q]) + s_bias[col + 2 * q];
+                        float v1 = __uint_as_float(rr[2 * q + 1]) + s_bias[col + 2 * q + 1];
+                        if (relu) {
+                            v0 = fmaxf(v0, 0.f);
+                            v1 = fmaxf(v1, 0.f);
+                        }
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                        packed[q] = *reinterpret_cast<uint32_t *>(&h2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(yout + col);
+#pragma unroll
+                    for (int q = 0; q < CH / 8; ++q)
+                        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
+                                            packed[4 * q + 3]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[t & 1]);
+            }
+            if (*abort) break;
+            u += len;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && s_drained) tmem_dealloc(tmem, C::NCOLS);
+}
+
+// Tensor maps of the persistent convolution (cuTensorMapEncodeTiled through
+// the runtime's driver entry point).
+PFN_cuTensorMapEncodeTiled_v12000 tcp_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// A BF16 tensor [d2][d1][d0] (d0 innermost) with a box of b0 x b1 x 1.
+bool tcp_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+             uint32_t b1) {
+    auto fn = tcp_encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+    const cuuint32_t box[3] = {b0, b1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int CIN, bool DG>
+cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, int nb, int h,
+                       int wd, int cout, int relu, cudaStream_t s) {
+    using C = PCfg<BN, CIN>;
+    static_assert(C::SMEM + 128 <= 226 * 1024, "shared-memory plan too large");
+    // at most 512 / NCOLS CTAs may share an SM's 512 tensor-memory columns:
+    // the shared-memory request is padded so that no more fit
+    constexpr int kPerSm = 512 / (int)C::NCOLS;
+    constexpr int kMinSmem = 233472 / (kPerSm + 1) + 1;   // 228 KB of shared memory per SM
+    constexpr int kSmem = C::SMEM + 128 > kMinSmem ? C::SMEM + 128 : kMinSmem;
+    // TMA: 16-byte aligned base addresses
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w)) & 15)
+        return cudaErrorNotSupported;
+    CUtensorMap mx, mxh, mw;
+    if (!tcp_map(&mx, x, CIN, wd, (uint64_t)nb * h, 8, 128) ||
+        !tcp_map(&mxh, x, CIN, wd, (uint64_t)nb * h, 8, 8))
+        return cudaErrorNotSupported;
+    if (!DG) {
+        if (!tcp_map(&mw, w, CIN, cout, 9, 8, BN)) return cudaErrorNotSupported;
+    } else {
+        mw = mx;   // unused by the input gradient
+    }
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv3x3_tcp_kernel<BN, CIN, DG>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) {
+            nsm = 0;
+            return e;
+        }
+    }
+    const int nblk = cout / BN;
+    const long units = (long)nb * h * (wd / 128);
+    int per_blk = std::max(1, nsm / nblk);
+    if (per_blk > units) per_blk = (int)units;
+    const int per = (int)((units + per_blk - 1) / per_blk);
+    conv3x3_tcp_kernel<BN, CIN, DG><<<nblk * per_blk, kTcpThreads, kSmem, s>>>(
+        mx, mxh, mw, w, bias, y, nb, h, wd, cout, relu, per_blk, per);
+    return cudaGetLastError();
+}
+
+// Channel block per CTA: all of cout where the weights and the ring fit,
+// else 32 (128 input channels).
+template <bool DG>
+cudaError_t launch_tcp_shape(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, int nb,
+                             int h, int wd, int cin, int cout, int relu, cudaStream_t s) {
+#define TCP(BN, CIN) return launch_tcp<BN, CIN, DG>(x, w, bias, y, nb, h, wd, cout, relu, s)
+    if (cin == 16) {
+        if (cout == 16) TCP(16, 16);
+        if (cout == 32) TCP(32, 16);
+        if (cout == 64) TCP(64, 16);
+        if (cout == 128) TCP(128, 16);
+    } else if (cin == 32) {
+        if (cout == 16) TCP(16, 32);
+        if (cout == 32) TCP(32, 32);
+        if (cout == 64) TCP(64, 32);
+        if (cout == 128) TCP(128, 32);
+    } else if (cin == 64) {
+        if (cout == 16) TCP(16, 64);
+        if (cout == 32) TCP(32, 64);
+        if (cout == 64) TCP(64, 64);
+        if (cout == 128) TCP(128, 64);
+    } else if (cin == 128) {
+        if (cout == 16) TCP(16, 128);
+        if (cout % 32 == 0) TCP(32, 128);
+    }
+#undef TCP
+    return cudaErrorNotSupported;
+}
+
 }  // namespace
+
+// Persistent tcgen05 convolution (forward, or the input gradient with dgrad)
+// for rows a multiple of 128 pixels and 16/32/64/128 channels;
+// cudaErrorNotSupported otherwise so that the caller takes the mma.sync kernel.
+cudaError_t launch_conv3x3_tcp(const void *x, const void *w, const float *bias, void *y, int nb,
+                               int h, int wd, int cin, int cout, int relu, int dgrad,
+                               cudaStream_t s) {
+    if (wd % 128 || h < 2) return cudaErrorNotSupported;
+    const bf16 *xb = (const bf16 *)x, *wb = (const bf16 *)w;
+    bf16 *yb = (bf16 *)y;
+    return dgrad ? launch_tcp_shape<true>(xb, wb, bias, yb, nb, h, wd, cin, cout, relu, s)
+                 : launch_tcp_shape<false>(xb, wb, bias, yb, nb, h, wd, cin, cout, relu, s);
+}
 
 // Forward convolution on tcgen05 when the path selection and the shape allow
 // (rows a multiple of 128 pixels, 16/32/64/128 channels);
@@ -346,7 +816,7 @@ cudaError_t launch_conv3x3_tc(const void *x, const void *w, const float *bias, v
 }  // namespace lbsc
 
 extern "C" int lb_nn_set_conv_path(int path) {
-    if (path < 0 || path > 2) return LB_ERR_ARG;
+    if (path < 0 || path > 3) return LB_ERR_ARG;
     lbsc::nn_conv_path = path;
     return LB_OK;
 }

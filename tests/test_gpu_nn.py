@@ -59,10 +59,13 @@ def _close_bf16(got, ref, tol=2e-3):
 
 CONV = [(2, 4, 128, 16, 32), (1, 3, 256, 64, 128), (2, 2, 128, 128, 64), (1, 2, 128, 32, 16),
         (2, 16, 16, 64, 32),   # tiles span rows (h w % 128 == 0 only)
-        (1, 6, 128, 32, 128)]  # several 128-pixel tiles, widest tcgen05 N
+        (1, 6, 128, 32, 128),  # several 128-pixel tiles, widest tcgen05 N
+        # more output rows than SMs: persistent CTAs walk runs of rows that
+        # cross bands, images and (128 input channels) channel blocks
+        (2, 96, 256, 128, 64), (3, 80, 128, 64, 128)]
 
 
-@pytest.mark.parametrize("path", [0, 1, 2])    # auto, mma.sync, tcgen05 (TMEM accumulator)
+@pytest.mark.parametrize("path", [0, 1, 2, 3])  # auto, mma.sync, tcgen05 per tile, persistent
 @pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
 def test_conv_forward(nb, h, w, cin, cout, path):
     from paper_2212_07848_gb300 import abi
@@ -81,15 +84,20 @@ def test_conv_forward(nb, h, w, cin, cout, path):
     assert L.lb_nn_set_conv_path(0) == 0
 
 
+@pytest.mark.parametrize("path", [0, 1])        # auto (persistent tcgen05 where it applies), mma.sync
 @pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
-def test_conv_input_gradient(nb, h, w, cin, cout):
+def test_conv_input_gradient(nb, h, w, cin, cout, path):
+    from paper_2212_07848_gb300 import abi
     L = _lib()
+    assert L.lb_nn_set_conv_path(path) == 0
     dy = _bf((nb, h, w, cout), seed=3)
     wt = _bf((9, cout, cin), 0.1, seed=4)
     dx = torch.empty((nb, h, w, cin), dtype=torch.bfloat16, device="cuda")
     assert L.lb_nn_conv3x3(_p(dy), _p(wt), None, _p(dx), nb, h, w, cout, cin, 0, 1, None) == 0
     torch.cuda.synchronize()
     _close_bf16(_np(dx), R.conv3x3_dgrad(_np(dy), _np(wt)))
+    assert L.lb_nn_status() == abi.LB_OK
+    assert L.lb_nn_set_conv_path(0) == 0
 
 
 @pytest.mark.parametrize("nb,h,w,cin,cout", CONV)

@@ -19,11 +19,14 @@ def _rel(got, ref):
     return float(np.sqrt(np.mean((got - ref) ** 2)) / (np.sqrt(np.mean(ref ** 2)) + 1e-30))
 
 
-@pytest.mark.parametrize("flux,mom", [(False, False), (True, False), (True, True)])
-def test_network_gradients_match_reference(flux, mom):
-    """Plain increment, flux form, and flux form with the momentum state."""
+@pytest.mark.parametrize("flux,mom,n", [(False, False, 64), (True, False, 64), (True, True, 64),
+                                        (False, False, 128)])
+def test_network_gradients_match_reference(flux, mom, n):
+    """Plain increment, flux form, and flux form with the momentum state; at
+    n = 128 the full-resolution layers (rows of 128 pixels) run on the
+    persistent tensor-core kernel, forward and input gradient."""
     from paper_2212_07848_gb300.surrogate import LAYERS, SurrogateNet
-    n, nb = 64, 2
+    nb = 2 if n == 64 else 1
     net = SurrogateNet(n, nb, seed=3, flux=flux, momentum=mom, jweight=0.7)
     g = torch.Generator(device="cpu").manual_seed(4)
     for i in range(len(LAYERS)):                   # a non-trivial output layer and biases

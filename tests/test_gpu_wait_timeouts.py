@@ -71,7 +71,8 @@ def test_persistent_ensemble_barrier_timeout_is_reported_and_recoverable():
         assert np.array_equal(a.populations(r), b.populations(r)), r
 
 
-def test_tensor_core_conv_mma_wait_timeout_is_reported_and_recoverable():
+@pytest.mark.parametrize("path", [2, 3])    # per-tile and persistent tcgen05 kernels
+def test_tensor_core_conv_mma_wait_timeout_is_reported_and_recoverable(path):
     torch = pytest.importorskip("torch")
     from paper_2212_07848_gb300 import abi
     L = abi.load()
@@ -85,7 +86,7 @@ def test_tensor_core_conv_mma_wait_timeout_is_reported_and_recoverable():
     b = torch.randn(cout, generator=gen).cuda()
     y0 = torch.empty((nb, h, w, cout), dtype=torch.bfloat16, device="cuda")
     y1 = torch.zeros_like(y0)
-    assert L.lb_nn_set_conv_path(2) == 0       # tcgen05 wherever it has a kernel
+    assert L.lb_nn_set_conv_path(path) == 0    # a tcgen05 kernel wherever it has one
     try:
         assert L.lb_nn_conv3x3(p(x), p(wt), p(b), p(y0), nb, h, w, cin, cout, 1, 0, None) == 0
         assert L.lb_nn_status() == abi.LB_OK
