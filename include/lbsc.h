@@ -359,7 +359,7 @@ int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
  * paragraph after Eq. (16): modes a > 3), z from Philox4x32-10 blocks 0-2 of
  * counter (site, step, replica, block), site = x + nx (y + ny z).
  * Storage: deviations [19][nz][ny][nx], FP32 or FP64; the context owns its
- * device memory.  nx % 32 == 0, ny % 8 == 0, nz >= 3, 19 nx ny nz < 2^32,
+ * device memory.  nx % 32 == 0, ny % 4 == 0, nz >= 3, 19 nx ny nz < 2^32,
  * tau > 1/2, kT >= 0 (LB_ERR_ARG otherwise).  Calls are asynchronous on the
  * context's stream except the read-outs, which synchronise. */
 typedef struct lb3_ctx lb3_ctx;

@@ -3,11 +3,11 @@
 // a > 3 (the noise paragraph after Eq. (16)).  Deviations delta f_i = f_i -
 // w_i rho0 are stored structure-of-arrays [19][nz][ny][nx], two buffers.
 //
-// Work decomposition: a CTA owns a 32 x 8 tile of (x, y) columns and marches
-// a strip of z planes.  Its 34 x 10 threads cover the tile and its one-column
+// Work decomposition: a CTA owns a 32 x 4 tile of (x, y) columns and marches
+// a strip of z planes.  Its 34 x 6 threads cover the tile and its one-column
 // halo ring: every thread pulls its column's populations for plane z + 1 and
 // writes that plane's pseudopotential deviation into a shared-memory ring of
-// four planes; after the barrier the 32 x 8 interior threads pull plane z
+// four planes; after the barrier the 32 x 4 interior threads pull plane z
 // again (L1 hits: they pulled it one iteration earlier) and collide it.
 // The force is Eq. (1) over the 18 D3Q19 neighbours with the fourth-order
 // isotropic weights 1/6 (axes) and 1/12 (face diagonals), summed as
@@ -87,9 +87,15 @@ constexpr bool norms_agree() {
 }
 static_assert(norms_agree(), "moment norms");
 
-constexpr int kTX3 = 32, kTY3 = 8;
+// A CTA owns a 32 x 4 tile of (x, y) columns plus their one-column halo ring
+// (34 x 6 = 204 threads, 72 registers, four CTAs per SM in FP32; two in FP64).  The step is
+// latency-bound, so more resident warps beat a smaller halo share: 32 x 4
+// measured faster than 32 x 8 (two CTAs per SM), 16 x 8, 64 x 4, 32 x 16 and
+// 64 x 8 at 256^3 on GB300.
+constexpr int kTX3 = 32, kTY3 = 4;
 constexpr int kBX3 = kTX3 + 2, kBY3 = kTY3 + 2;      // tile + halo ring
-constexpr int kThreads3 = kBX3 * kBY3;               // 340
+constexpr int kThreads3 = kBX3 * kBY3;               // 204
+constexpr int kCtasPerSm3 = 4;
 
 template <typename T> struct K3 {
     const T *__restrict__ src;
@@ -166,10 +172,12 @@ __device__ __forceinline__ double inv3(double rho) { return 1.0 / rho; }
 // the pulled populations are not needed (stress modes become their
 // equilibrium plus source, ghosts zero, before the noise); the result is
 // that of the general path with gamma = 0.
-template <typename T, bool UNIT = false>
-__device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const K3<T> &p,
-                                         uint32_t site, const float2 *ring, T f[19]) {
-    // pair sums and differences: pair q = velocities 2q+1 (c) and 2q+2 (-c)
+// Moments m_k = sum_i e_ki g_i of the pulled populations, k < NK (NK = 4:
+// mass and momentum only), from pair sums and differences: pair q =
+// velocities 2q+1 (c) and 2q+2 (-c); even polynomials use the sums, odd the
+// differences.
+template <typename T, int NK>
+__device__ __forceinline__ void moments3(const T g[19], T *m) {
     T s[10], d[10];
     s[0] = g[0];
     d[0] = T(0);
@@ -178,10 +186,8 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         s[q + 1] = g[2 * q + 1] + g[2 * q + 2];
         d[q + 1] = g[2 * q + 1] - g[2 * q + 2];
     }
-    // m_k = sum over pairs of e_k(c) (s or d): even polynomials use s, odd use d
-    T m[19];
 #pragma unroll
-    for (int k = 0; k < (UNIT ? 4 : 19); ++k) {
+    for (int k = 0; k < NK; ++k) {
         const bool odd = (k >= 1 && k <= 3) || (k >= 10 && k <= 15);
         T acc = odd ? T(0) : T(mom3(k, 0)) * s[0];
 #pragma unroll
@@ -191,6 +197,25 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
         }
         m[k] = acc;
     }
+}
+
+template <typename T, bool UNIT = false>
+__device__ __forceinline__ void collide3_m(const T m[19], T Fx, T Fy, T Fz, const K3<T> &p,
+                                           uint32_t site, const float2 *ring, T f[19]);
+
+template <typename T, bool UNIT = false>
+__device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const K3<T> &p,
+                                         uint32_t site, const float2 *ring, T f[19]) {
+    T m[19];
+    moments3<T, UNIT ? 4 : 19>(g, m);
+    collide3_m<T, UNIT>(m, Fx, Fy, Fz, p, site, ring, f);
+}
+
+// The collision from the moments of the pulled populations (UNIT: only
+// m_0 .. m_3 are read).
+template <typename T, bool UNIT>
+__device__ __forceinline__ void collide3_m(const T m[19], T Fx, T Fy, T Fz, const K3<T> &p,
+                                           uint32_t site, const float2 *ring, T f[19]) {
     const T rho = p.rho0 + m[0];
     const T inv = inv3(rho);
     const T jx = fma(T(0.5), Fx, m[1]), jy = fma(T(0.5), Fy, m[2]), jz = fma(T(0.5), Fz, m[3]);
@@ -294,7 +319,8 @@ __device__ __forceinline__ void collide3(const T g[19], T Fx, T Fy, T Fz, const 
 
 
 template <typename T, bool SAMPLE, bool UNIT = false>
-__global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
+__global__ void __launch_bounds__(kThreads3, sizeof(T) == 4 ? kCtasPerSm3 : 2)
+step3_kernel(const K3<T> p) {
     __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
     __shared__ float2 s_ring[kRing3];    // noise angles (FP32 path; read after the first barrier)
     if (std::is_same<T, float>::value && p.noise)
@@ -317,15 +343,23 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
     const uint32_t nxy = (uint32_t)nx * ny;
 
     uint32_t zprev[3] = {0u, 0u, 0u};   // offsets of the plane pulled one iteration ago
+    // UNIT: the collision needs only the mass and momentum of the pulled
+    // populations, so they are kept from the pull of the previous iteration
+    // (and the density deviation for a sample) instead of pulling again
+    T mprev[4] = {T(0), T(0), T(0), T(0)};
+    T dprev = T(0);
     for (int it = 0; it < it_end; ++it) {
         int zz = z0 - 1 + it;
         zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
         const uint32_t zo[3] = {(uint32_t)(zz == 0 ? nz - 1 : zz - 1) * nxy, (uint32_t)zz * nxy,
                                 (uint32_t)(zz == nz - 1 ? 0 : zz + 1) * nxy};
+        T mnew[4] = {T(0), T(0), T(0), T(0)}, dnew = T(0);
         {
             T g[19];
             pull3(p.src, plane, xo, yo, zo, g);
-            s_psi[it & 3][ty][tx] = delta_psi<T>(sum19(g), p.psi_kind, p.rho0, p.psi_c, p.psi_b);
+            dnew = sum19(g);
+            s_psi[it & 3][ty][tx] = delta_psi<T>(dnew, p.psi_kind, p.rho0, p.psi_c, p.psi_b);
+            if (UNIT) moments3<T, 4>(g, mnew);
         }
         __syncthreads();
         if (it >= 2 && interior) {
@@ -352,17 +386,31 @@ __global__ void __launch_bounds__(kThreads3, 2) step3_kernel(const K3<T> p) {
             const T Fx = p.force_pref * psic * Sx, Fy = p.force_pref * psic * Sy,
                     Fz = p.force_pref * psic * Sz;
             const uint32_t site = ((uint32_t)zc * ny + y) * nx + x;
-            T g[19], f[19];
-            pull3(p.src, plane, xo, yo, zprev, g);
-            collide3<T, UNIT>(g, Fx, Fy, Fz, p, site, s_ring, f);
+            T f[19];
+            if constexpr (UNIT) {
+                T m[19];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) m[k] = mprev[k];
+                collide3_m<T, true>(m, Fx, Fy, Fz, p, site, s_ring, f);
+                if (SAMPLE) p.drho_out[site] = dprev;
+            } else {
+                T g[19];
+                pull3(p.src, plane, xo, yo, zprev, g);
+                collide3<T, false>(g, Fx, Fy, Fz, p, site, s_ring, f);
+                if (SAMPLE) p.drho_out[site] = sum19(g);
+            }
 #pragma unroll
             for (int i = 0; i < 19; ++i) p.dst[(uint32_t)i * plane + site] = f[i];
-            if (SAMPLE) p.drho_out[site] = sum19(g);
             if (!isfinite(f[1] + f[7])) atomicOr(p.flag, LB_STEP_NONFINITE);
         }
         zprev[0] = zo[0];
         zprev[1] = zo[1];
         zprev[2] = zo[2];
+        if (UNIT) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) mprev[k] = mnew[k];
+            dprev = dnew;
+        }
         // slot (it + 1) & 3, written next, was last read in iteration it - 1,
         // before this iteration's barrier
     }

@@ -82,7 +82,7 @@ def test_fullsize_d3q19_256_one_step_sampled_sites():
     rng = np.random.default_rng(2)
     xs, ys, zs = (list(rng.integers(0, n, 1500)) for _ in range(3))
     for ex in (0, 1, 31, 32, 33, 255):
-        for ey in (0, 7, 8, 9, 255):
+        for ey in (0, 3, 4, 5, 7, 8, 9, 255):
             for ez in (0, 15, 16, 17, 255):
                 xs.append(ex)
                 ys.append(ey)
