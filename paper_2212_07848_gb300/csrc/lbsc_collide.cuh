@@ -80,9 +80,45 @@ __device__ __forceinline__ T sum9(const T g[9]) {
 // the non-conserved moments are replaced by their equilibrium, source and
 // noise, so m3..m8 of the pulled populations are not needed; the result is
 // bit-identical to the general path with gamma = 0.
+template <typename T>
+__device__ __forceinline__ void collide_tail(T drho, T m1, T m2, T m3, T m4, T m5, T m6, T m7,
+                                             T m8, T Fx, T Fy, const KParams<T> &p,
+                                             const uint32_t *__restrict__ rk, uint32_t site,
+                                             T f[9], bool unit);
+
+// Mass and momentum deviations of the pulled populations, with exactly the
+// arithmetic of the forward transform in collide (so that a kernel may keep
+// them instead of the nine populations on the unit-relaxation path).
+template <typename T>
+__device__ __forceinline__ void unit_moments(const T g[9], T &drho, T &m1, T &m2) {
+    const T e13 = g[1] - g[3], e24 = g[2] - g[4];
+    const T s13 = g[1] + g[3], s24 = g[2] + g[4];
+    const T d57 = g[5] - g[7], d86 = g[8] - g[6];
+    const T s57 = g[5] + g[7], s68 = g[6] + g[8];
+    const T sa = s13 + s24, sd = s57 + s68;
+    drho = g[0] + (sa + sd);
+    const T t1 = d57 + d86, t2 = d57 - d86;
+    m1 = e13 + t1;
+    m2 = e24 + t2;
+}
+
+// The unit-relaxation collision from the mass and momentum deviations alone.
+template <typename T>
+__device__ __forceinline__ void collide_unit_m(T drho, T m1, T m2, T Fx, T Fy, const KParams<T> &p,
+                                               const uint32_t *__restrict__ rk, uint32_t site,
+                                               T f[9]) {
+    collide_tail<T>(drho, m1, m2, T(0), T(0), T(0), T(0), T(0), T(0), Fx, Fy, p, rk, site, f, true);
+}
+
 template <typename T, bool UNIT = false>
 __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<T> &p,
                                         const uint32_t *__restrict__ rk, uint32_t site, T f[9]) {
+    if constexpr (UNIT) {
+        T drho, m1, m2;
+        unit_moments(g, drho, m1, m2);
+        collide_unit_m(drho, m1, m2, Fx, Fy, p, rk, site, f);
+        return;
+    }
     // forward transform (integer coefficients, shared subexpressions)
     const T e13 = g[1] - g[3], e24 = g[2] - g[4];
     const T s13 = g[1] + g[3], s24 = g[2] + g[4];
@@ -99,7 +135,16 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T m6 = fma(T(2), t1, -e13);                        // (3c^2 - 4) cx
     const T m7 = fma(T(2), t2, -e24);                        // (3c^2 - 4) cy
     const T m8 = fma(T(8), sd, fma(T(-4), sa, g[0] + g[0])); // 9c^4 - 15c^2 + 2
+    collide_tail<T>(drho, m1, m2, m3, m4, m5, m6, m7, m8, Fx, Fy, p, rk, site, f, false);
+}
 
+// Everything after the forward transform: Guo velocity, relaxation with the
+// source, noise, inverse transform.  unit: every rate is 1 (m3 .. m8 unused).
+template <typename T>
+__device__ __forceinline__ void collide_tail(T drho, T m1, T m2, T m3, T m4, T m5, T m6, T m7,
+                                             T m8, T Fx, T Fy, const KParams<T> &p,
+                                             const uint32_t *__restrict__ rk, uint32_t site,
+                                             T f[9], bool unit) {
     const T rho = p.rho0 + drho;
     const T inv_rho = inv_rho_of(rho);
     const T jxh = fma(T(0.5), Fx, m1), jyh = fma(T(0.5), Fy, m2);   // rho u
@@ -107,7 +152,7 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T qxx = jxh * ux, qyy = jyh * uy, qxy = jxh * uy;          // rho u u
     const T pxx = ux * Fx, pyy = uy * Fy, pxy = fma(ux, Fy, uy * Fx);
     T m3s, m4s, m5s, m6s, m7s, m8s;
-    if constexpr (UNIT) {
+    if (unit) {
         m3s = fma(p.c3a, qxx + qyy, p.c3b * (pxx + pyy));
         m4s = fma(p.c4a, qxx - qyy, p.c4b * (pxx - pyy));
         m5s = fma(p.c5a, qxy, p.c5b * pxy);
