@@ -122,16 +122,25 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
         s_cur = cur;
     }
     __syncthreads();
+    // replicas with every relaxation rate 1 (tau = 1) take the unit path,
+    // which keeps only the conserved moments of the pulled rows
+    const bool unit = sp.gamma == 0.f;
     if (OV) {
-        if (s_sample)
-            step_strip_ov<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
-        else
-            step_strip_ov<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        if (unit) {
+            if (s_sample) step_strip_ov<float, ORDER, true, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            else step_strip_ov<float, ORDER, false, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        } else {
+            if (s_sample) step_strip_ov<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            else step_strip_ov<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        }
     } else {
-        if (s_sample)
-            step_strip<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
-        else
-            step_strip<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        if (unit) {
+            if (s_sample) step_strip<float, ORDER, true, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            else step_strip<float, ORDER, false, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        } else {
+            if (s_sample) step_strip<float, ORDER, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+            else step_strip<float, ORDER, false>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -227,19 +236,17 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
                 go = false;
                 break;
             }
+            const bool unit = sp.gamma == 0.f;   // every rate 1: the unit path
+            const bool smp = sp.drho_out != nullptr;
+#define ENS_STRIP(FN, S, U) FN<float, ORDER, S, true, U>(sp, keys.rk, tile.x0, tile.y0, tile.y1)
             if (OV) {
-                if (sp.drho_out)
-                    step_strip_ov<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0,
-                                                            tile.y1);
-                else
-                    step_strip_ov<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0,
-                                                             tile.y1);
+                if (unit) { if (smp) ENS_STRIP(step_strip_ov, true, true); else ENS_STRIP(step_strip_ov, false, true); }
+                else { if (smp) ENS_STRIP(step_strip_ov, true, false); else ENS_STRIP(step_strip_ov, false, false); }
             } else {
-                if (sp.drho_out)
-                    step_strip<float, ORDER, true, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
-                else
-                    step_strip<float, ORDER, false, true>(sp, keys.rk, tile.x0, tile.y0, tile.y1);
+                if (unit) { if (smp) ENS_STRIP(step_strip, true, true); else ENS_STRIP(step_strip, false, true); }
+                else { if (smp) ENS_STRIP(step_strip, true, false); else ENS_STRIP(step_strip, false, false); }
             }
+#undef ENS_STRIP
             __syncthreads();   // the tile's stores are done, and sp may be refilled
             if (threadIdx.x == 0) {
                 __threadfence();

@@ -57,11 +57,15 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
 
     const T rho0 = p.rho0;
 
-    T q[H + 1][9];   // pulled populations of rows yy-H .. yy
+    // what a row keeps for its collision H rows later: the nine pulled
+    // populations, or on the unit-relaxation path only (sum for the sample,
+    // mass, momentum x, momentum y), which that collision reads
+    constexpr int NQ = UNIT ? 4 : 9;
+    T q[H + 1][NQ];   // rows yy-H .. yy
 #pragma unroll
     for (int r = 0; r <= H; ++r)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) q[r][i] = T(0);
+        for (int i = 0; i < NQ; ++i) q[r][i] = T(0);
 
     const int it_end = (y1 - y0) + 2 * H;
     // Register prefetch: the loads of row it+1 are issued before row it is
@@ -86,14 +90,20 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
             pull<CG>(p.src, plane, nx, x, xm, xp, yc, ym, yp, gn);
         }
         const int yy = y0 - H + it;
+        const T s9 = sum9(g);
         if (active)
-            s_dpsi[slot][slot_col] = delta_psi<T>(sum9(g), p.psi_kind, rho0, p.psi_c, p.psi_b);
+            s_dpsi[slot][slot_col] = delta_psi<T>(s9, p.psi_kind, rho0, p.psi_c, p.psi_b);
 #pragma unroll
         for (int r = 0; r < H; ++r)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) q[r][i] = q[r + 1][i];
+            for (int i = 0; i < NQ; ++i) q[r][i] = q[r + 1][i];
+        if constexpr (UNIT) {
+            q[H][0] = s9;
+            unit_moments(g, q[H][1], q[H][2], q[H][3]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) q[H][i] = g[i];
+            for (int i = 0; i < 9; ++i) q[H][i] = g[i];
+        }
         __syncthreads();
         if (it < 2 * H || !collides) continue;
 
@@ -119,7 +129,9 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
         const T Fy = p.force_pref * psic * sy;
 
         T f[9];
-        collide<T, UNIT>(q[0], Fx, Fy, p, rk, (uint32_t)x + (uint32_t)nx * (uint32_t)yr, f);
+        const uint32_t site = (uint32_t)x + (uint32_t)nx * (uint32_t)yr;
+        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, f);
+        else collide<T, false>(q[0], Fx, Fy, p, rk, site, f);
 
         const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
         p.dst[o] = f[0];
@@ -131,7 +143,10 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
         p.dst[o + 6u * pl] = f[6];
         p.dst[o + 7u * pl] = f[7];
         p.dst[o + 8u * pl] = f[8];
-        if (SAMPLE) p.drho_out[o] = sum9(q[0]);
+        if (SAMPLE) {
+            if constexpr (UNIT) p.drho_out[o] = q[0][0];
+            else p.drho_out[o] = sum9(q[0]);
+        }
         if (!isfinite(f[1] + f[5])) atomicOr(p.flag, LB_STEP_NONFINITE);
     }
 }
