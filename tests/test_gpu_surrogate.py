@@ -140,6 +140,26 @@ def test_rollout_stable_and_faster_than_solver(trained):
     assert t_net < t_lb
 
 
+# Rollout scores of the small training case (12 quenches of 256^2 -> 64^2,
+# 1000 iterations, held-out quenches 10 and 11 from frame 3 over 10 strides),
+# the regression bounds of the bench's surrogate metrics at this size.  The
+# training is bit-reproducible, so on the same GPU the scores are fixed; the
+# bounds sit about 30% above the measured values: L(t) 0.083 (bound 0.11) and
+# S(k, t) L1 gap 0.28 (bound 0.36); a short training on a 64^2 grid is far
+# from the 2% of the paper-scale target, whose figures are the bench's.
+ROLLOUT_BOUNDS = {"L_mean_max_rel_err": 0.11, "Sk_l1_rel_err": 0.36}
+
+
+def test_rollout_scores_against_the_solver(trained):
+    S, net, frames, Gs, _, _ = trained
+    ev = S.evaluate_rollouts(net, frames, Gs, [10, 11], 3, 10)
+    got = {k: ev[k] for k in ("L_mean_max_rel_err", "L_traj_max_rel_err", "Sk_peak_max_rel_err",
+                              "Sk_l1_rel_err")}
+    print("rollout scores", got)
+    for k, bound in ROLLOUT_BOUNDS.items():
+        assert np.isfinite(got[k]) and got[k] < bound, (k, got[k])
+
+
 def test_guarded_rollout_hands_back_to_the_solver(trained):
     """Rollout increments have zero mean, so the field's mass stays at its
     initial value to FP32 rounding and the mass guard accepts the rollout
