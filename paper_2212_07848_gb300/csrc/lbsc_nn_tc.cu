@@ -98,6 +98,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)1 << 46;
     return d;
 }
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout that TMA writes with CU_TENSOR_MAP_SWIZZLE_128B: rows of
+// 64 BF16 (128 bytes) whose 16-byte chunks are permuted by the row's index
+// within each 8-row, 1024-byte group (SBO = 1024), layout type 2 at bits
+// 61-63.  The permutation follows the absolute shared-memory address (the
+// groups start on 1024-byte boundaries), so an operand may start at any row
+// of a group, or 32 bytes into a row for the next K step, with the base
+// offset field left at 0 (checked against the CPU reference on GB300; the
+// field set to the start row's index gave wrong results).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;              // SBO: 8 rows of 128 bytes
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -345,22 +362,33 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, 
 // ---------------------------------------------------------------------------
 template <int BN, int CIN>
 struct PCfg {
+    // SW: 64 or 128 input channels, staged in the 128-byte swizzled layout
+    // (TMA boxes of 64 channels: 128-byte rows); otherwise the no-swizzle
+    // layout of 16-byte K chunks (boxes of 8 channels)
+    static constexpr bool SW = CIN >= 64;
     static constexpr int KC = CIN / 8;
-    // a staged K chunk (8 channels) of one input row holds pixels x0-8 ..
-    // x0+135 at 16-byte pitch; column c = pixel x0-1+c sits at byte 112 + 16c
-    // (the three copies that fill it start on 128-byte boundaries)
-    static constexpr uint32_t LBO_A = 144 * 16;
-    static constexpr uint32_t COL0 = 112;
-    static constexpr int ROW_BYTES = KC * LBO_A;
+    static constexpr int KB = CIN / 64;           // 64-channel blocks (SW)
+    // no-swizzle: a staged K chunk (8 channels) of one input row holds pixels
+    // x0-8 .. x0+135 at 16-byte pitch; column c = pixel x0-1+c sits at byte
+    // 112 + 16c of its chunk (the three copies start on 128-byte boundaries).
+    // SW: a 64-channel block holds the same 144 pixels as 128-byte rows;
+    // column c is row c + 7.
+    static constexpr uint32_t LBO_A = SW ? 144 * 128 : 144 * 16;
+    static constexpr uint32_t COL0 = SW ? 7 * 128 : 112;
+    static constexpr uint32_t PIX = SW ? 128 : 16;        // bytes between pixels
+    static constexpr int ROW_BYTES = SW ? KB * 144 * 128 : KC * 144 * 16;
     static constexpr int TAP_BYTES = BN * CIN * 2;
     static constexpr int B_BYTES = 9 * TAP_BYTES;
     static constexpr int R0 = (220 * 1024 - B_BYTES) / ROW_BYTES;
     static constexpr int R = R0 < 4 ? 4 : (R0 > 8 ? 8 : R0);   // ring slots
     static constexpr int A_BYTES = R * ROW_BYTES;
     static constexpr int SMEM = A_BYTES + B_BYTES;
-    // B per tap: K chunk kc of output channel n at kc * BN * 16 + n * 16
-    static constexpr uint32_t LBO_B = BN * 16;
-    static constexpr uint32_t ROW_TX = (uint32_t)KC * 144 * 16;   // bytes landing per row
+    // B per tap, no-swizzle: K chunk kc of output channel n at kc * BN * 16 +
+    // n * 16; SW: 64-channel block kb of output channel n at kb * BN * 128 +
+    // n * 128 (chunks swizzled)
+    static constexpr uint32_t LBO_B = SW ? BN * 128 : BN * 16;
+    static constexpr uint32_t ROW_TX = (uint32_t)CIN * 144 * 2;   // bytes landing per row
+    static constexpr int ALIGN = SW ? 1024 : 128;               // staging alignment
     static constexpr uint32_t NCOLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : 256));
 };
 constexpr int kTcpThreads = 192;
@@ -412,9 +440,11 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
     __shared__ int s_abort, s_drained;
     __shared__ float s_bias[BN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // 128-byte aligned base (the launch adds 128 bytes of slack)
+    // aligned base for the bulk copies (128 bytes, 1024 for the swizzled
+    // layout; the launch adds that much slack)
     uint8_t *smem = reinterpret_cast<uint8_t *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+        (reinterpret_cast<uintptr_t>(smem_raw) + (C::ALIGN - 1)) &
+        ~static_cast<uintptr_t>(C::ALIGN - 1));
     uint8_t *sA = smem;
     uint8_t *sB = smem + C::A_BYTES;
     constexpr uint32_t IDESC = idesc_bf16(128, BN);
@@ -438,9 +468,19 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
             const uint4 q = *reinterpret_cast<const uint4 *>(
                 w + ((size_t)(8 - tap) * CIN + c) * Cout + n0 + nc * 8);
             const bf16 *e = reinterpret_cast<const bf16 *>(&q);
-            uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 3) * C::LBO_B + nc * 128 + (c & 7) * 2;
+            if constexpr (C::SW) {
+                // row n = nc * 8 + j of block c / 64; its 16-byte chunk (c % 64) / 8
+                // sits at chunk index ((c % 64) / 8) ^ (n % 8)
+                uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 6) * C::LBO_B + nc * 1024 + (c & 7) * 2;
+                const int ch = (c & 63) >> 3;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16 *>(d + j * 16) = e[j];
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<bf16 *>(d + j * 128 + ((ch ^ j) << 4)) = e[j];
+            } else {
+                uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 3) * C::LBO_B + nc * 128 + (c & 7) * 2;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16 *>(d + j * 16) = e[j];
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -479,9 +519,11 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
         if (lane == 0) {
             if (!DG) {
                 mbar_expect_tx(&wfull, (uint32_t)C::B_BYTES);
+                constexpr int NBLK = C::SW ? C::KB : C::KC;   // boxes per tap
+                constexpr int BCH = C::SW ? 64 : 8;             // channels per box
                 for (int tap = 0; tap < 9; ++tap)
-                    for (int kc = 0; kc < C::KC; ++kc)
-                        tma_load3(sB + tap * C::TAP_BYTES + kc * C::LBO_B, &tm_w, kc * 8, n0, tap,
+                    for (int kc = 0; kc < NBLK; ++kc)
+                        tma_load3(sB + tap * C::TAP_BYTES + kc * C::LBO_B, &tm_w, kc * BCH, n0, tap,
                                   &wfull);
             }
             for (long u = u_begin; u < u_end && !*abort;) {
@@ -503,11 +545,14 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     const int yy = b * H + ys;
                     uint8_t *dst = sA + slot * C::ROW_BYTES;
                     mbar_expect_tx(&full[slot], C::ROW_TX);
-                    for (int kc = 0; kc < C::KC; ++kc) {
+                    constexpr int NBLK = C::SW ? C::KB : C::KC;   // channel blocks
+                    constexpr int BCH = C::SW ? 64 : 8;             // channels per block
+                    for (int kc = 0; kc < NBLK; ++kc) {
                         uint8_t *ch = dst + kc * C::LBO_A;
-                        tma_load3(ch, &tm_xh, kc * 8, xl, yy, &full[slot]);              // x0-8 .. x0-1
-                        tma_load3(ch + 128, &tm_x, kc * 8, x0, yy, &full[slot]);         // x0 .. x0+127
-                        tma_load3(ch + 128 + 2048, &tm_xh, kc * 8, xr, yy, &full[slot]); // x0+128 ..
+                        // x0-8 .. x0-1, x0 .. x0+127, x0+128 .. x0+135
+                        tma_load3(ch, &tm_xh, kc * BCH, xl, yy, &full[slot]);
+                        tma_load3(ch + 8 * C::PIX, &tm_x, kc * BCH, x0, yy, &full[slot]);
+                        tma_load3(ch + 136 * C::PIX, &tm_xh, kc * BCH, xr, yy, &full[slot]);
                     }
                 }
                 if (stop) break;
@@ -527,7 +572,7 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
         bool ok = true;
         int nfreed[C::R];   // commits issued to each slot_free barrier
         for (int i = 0; i < R; ++i) nfreed[i] = 0;
-        const uint64_t bdesc0 = smem_desc(smem_u32(sB), C::LBO_B, 128);
+        const uint64_t bdesc0 = C::SW ? 0 : smem_desc(smem_u32(sB), C::LBO_B, 128);
         if (lane == 0) {
             if (!DG) ok = mbar_wait_ab(&wfull, 0, limit, abort);
             for (long u = u_begin; u < u_end && ok;) {
@@ -552,15 +597,27 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     // issuing thread spends about one add per operand
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
-                        const uint64_t arow = smem_desc(
-                            smem_u32(sA + ((seq0 + tt + dy) % R) * C::ROW_BYTES) + C::COL0, C::LBO_A, 128);
+                        const uint32_t abase =
+                            smem_u32(sA + ((seq0 + tt + dy) % R) * C::ROW_BYTES) + C::COL0;
+                        const uint64_t arow = C::SW ? 0 : smem_desc(abase, C::LBO_A, 128);
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
-                            for (int j = 0; j < CIN / 16; ++j)
-                                tc_mma(acc, arow + (uint64_t)((dx * 16 + 2 * j * C::LBO_A) >> 4),
-                                       bdesc0 + (uint64_t)(((3 * dy + dx) * C::TAP_BYTES + 2 * j * C::LBO_B) >> 4),
-                                       IDESC, (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
+                            for (int j = 0; j < CIN / 16; ++j) {
+                                uint64_t ad, bd;
+                                if constexpr (C::SW) {
+                                    // K step j: block j / 4, 32 bytes per step within it
+                                    ad = smem_desc_sw128(abase + dx * 128 + (j >> 2) * C::LBO_A +
+                                                         (j & 3) * 32);
+                                    bd = smem_desc_sw128(smem_u32(sB) + (3 * dy + dx) * C::TAP_BYTES +
+                                                         (j >> 2) * C::LBO_B + (j & 3) * 32);
+                                } else {
+                                    ad = arow + (uint64_t)((dx * 16 + 2 * j * C::LBO_A) >> 4);
+                                    bd = bdesc0 + (uint64_t)(((3 * dy + dx) * C::TAP_BYTES +
+                                                              2 * j * C::LBO_B) >> 4);
+                                }
+                                tc_mma(acc, ad, bd, IDESC, (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
+                            }
                         }
                         if (dy == 0) {
                             // the row above is read by no later output row: hand
@@ -673,9 +730,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tcp_encode_fn() {
     return fn;
 }
 
-// A BF16 tensor [d2][d1][d0] (d0 innermost) with a box of b0 x b1 x 1.
+// A BF16 tensor [d2][d1][d0] (d0 innermost) with a box of b0 x b1 x 1, copied
+// with the 128-byte swizzle when sw (then b0 = 64: 128-byte rows).
 bool tcp_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
-             uint32_t b1) {
+             uint32_t b1, bool sw = false) {
     auto fn = tcp_encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {d0, d1, d2};
@@ -683,7 +741,8 @@ bool tcp_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_
     const cuuint32_t box[3] = {b0, b1, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              sw ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -691,21 +750,22 @@ template <int BN, int CIN, bool DG>
 cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, int nb, int h,
                        int wd, int cout, int relu, cudaStream_t s) {
     using C = PCfg<BN, CIN>;
-    static_assert(C::SMEM + 128 <= 226 * 1024, "shared-memory plan too large");
+    static_assert(C::SMEM + C::ALIGN <= 226 * 1024, "shared-memory plan too large");
     // at most 512 / NCOLS CTAs may share an SM's 512 tensor-memory columns:
     // the shared-memory request is padded so that no more fit
     constexpr int kPerSm = 512 / (int)C::NCOLS;
     constexpr int kMinSmem = 233472 / (kPerSm + 1) + 1;   // 228 KB of shared memory per SM
-    constexpr int kSmem = C::SMEM + 128 > kMinSmem ? C::SMEM + 128 : kMinSmem;
+    constexpr int kSmem = C::SMEM + C::ALIGN > kMinSmem ? C::SMEM + C::ALIGN : kMinSmem;
     // TMA: 16-byte aligned base addresses
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w)) & 15)
         return cudaErrorNotSupported;
     CUtensorMap mx, mxh, mw;
-    if (!tcp_map(&mx, x, CIN, wd, (uint64_t)nb * h, 8, 128) ||
-        !tcp_map(&mxh, x, CIN, wd, (uint64_t)nb * h, 8, 8))
+    constexpr uint32_t BCH = C::SW ? 64 : 8;   // channels per box
+    if (!tcp_map(&mx, x, CIN, wd, (uint64_t)nb * h, BCH, 128, C::SW) ||
+        !tcp_map(&mxh, x, CIN, wd, (uint64_t)nb * h, BCH, 8, C::SW))
         return cudaErrorNotSupported;
     if (!DG) {
-        if (!tcp_map(&mw, w, CIN, cout, 9, 8, BN)) return cudaErrorNotSupported;
+        if (!tcp_map(&mw, w, CIN, cout, 9, BCH, BN, C::SW)) return cudaErrorNotSupported;
     } else {
         mw = mx;   // unused by the input gradient
     }
