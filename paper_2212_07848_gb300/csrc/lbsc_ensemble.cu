@@ -158,12 +158,14 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
 
 // ---------------------------------------------------------------------------
 // Persistent variant: one cooperative launch advances every replica by
-// `nsteps` steps.  CTA c takes tiles c, c + gridDim.x, ... of every step in
-// turn.  A tile of replica r at step s may start once all tiles of r have
-// finished step s - 1 (a per-replica completion counter, bounded wait), which
-// is all it reads; every CTA finishes all its step-(s-1) tiles before any
-// step-s tile, and all CTAs are resident, so the waits always end.  The
-// buffers alternate inside the launch, so pulls go through L2
+// `nsteps` steps.  The (step, tile) pairs are handed out in order, step-major,
+// from one atomic counter: a CTA that finishes a tile takes the next pair, so
+// the work balances itself across CTAs and the tiles of step s + 1 start
+// while the last tiles of step s run.  A tile of replica r at step s may
+// start once all tiles of r have finished step s - 1 (a per-replica
+// completion counter, bounded wait), which is all it reads; those tiles were
+// handed out earlier to CTAs that are all resident, so the waits always end.
+// The buffers alternate inside the launch, so pulls go through L2
 // (ld.global.cg), not the read-only path.  The last CTA to finish resets the
 // counters and advances the device clock.
 // ---------------------------------------------------------------------------
@@ -171,6 +173,7 @@ struct EnsCtl {
     uint32_t finished;
     int abort;
     unsigned long long wait_ns;   // bound on a replica barrier (lb_ens_set_wait_ns)
+    uint32_t next;                // next (step, tile) pair to hand out
 };
 constexpr uint64_t kEnsWaitNs = 2000000000ull;   // default: 2 s
 
@@ -199,59 +202,77 @@ __device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abo
     }
 }
 
-template <int ORDER, bool OV>
+// UM: 1 every replica takes the unit path (all rates 1), 0 none does, 2 each
+// replica by its own rates.  One strip variant per kernel (two for UM 2):
+// more inlined variants in the loop push the strip past the register budget
+// the launch bounds leave, and it spills.  The persistent launch never
+// samples; a sampling step runs through the per-step kernel.
+template <int ORDER, bool OV, int UM>
 __global__ void __launch_bounds__(OV ? kStepTX : kStepTX + 32, OV ? (ORDER == 4 ? 8 : 5)
                                                                   : (ORDER == 4 ? 6 : 4))
 ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles,
                    int ntiles, const int *__restrict__ rep_ntiles, uint32_t *done, int nrep,
-                   EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys, int nsteps,
-                   int sample_last) {
+                   EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys, int nsteps) {
     __shared__ KParams<float> sp;
-    __shared__ int s_go, s_last;
-    const uint32_t t0 = __ldcg(&clk->t);
-    const int cur0 = __ldcg(&clk->cur);
-    const uint64_t wait_ns = __ldcg(&ctl->wait_ns);
-    bool go = true;
-    for (int s = 0; s < nsteps && go; ++s) {
-        const bool sample = sample_last && s == nsteps - 1;
-        for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
-            const EnsTile tile = tiles[i];
-            if (threadIdx.x == 0) {
-                int w = 1;
-                if (s > 0) w = wait_replica(&done[tile.r], (uint32_t)s * rep_ntiles[tile.r],
-                                            &ctl->abort, wait_ns);
-                if (w < 0) {
-                    atomicOr(flag, LB_STEP_TIMEOUT);
-                    atomicExch(&ctl->abort, 1);
-                }
-                if (w > 0) {
-                    const EnsRep &R = reps[tile.r];
-                    fill_tile_params(sp, R, tile, t0 + (uint32_t)s, cur0 ^ (s & 1),
-                                     sample && R.drho, flag);
-                }
-                s_go = w > 0;
+    __shared__ EnsTile s_tile;
+    __shared__ int s_go, s_last, s_cur0;
+    __shared__ uint32_t s_k[2], s_t0;
+    // what lives across the strip sits in shared memory: the strip needs
+    // every register the launch bounds leave
+    if (threadIdx.x == 0) {
+        s_t0 = __ldcg(&clk->t);
+        s_cur0 = __ldcg(&clk->cur);
+    }
+    const uint32_t npairs = (uint32_t)nsteps * (uint32_t)ntiles;
+    // Thread 0 claims the next pair while the current one runs, and another
+    // thread posts a finished tile while thread 0 sets up the next one, so
+    // neither round trip to L2 idles the CTA.  Pairs are still claimed in
+    // order and a CTA starts a claimed pair as soon as its current one ends,
+    // so the lowest unfinished pair always runs and every wait below ends.
+    constexpr int kPoster = 32;
+    if (threadIdx.x == 0) s_k[0] = atomicAdd(&ctl->next, 1u);
+    __syncthreads();
+    for (int it = 0;; it ^= 1) {
+        const uint32_t k = s_k[it];
+        if (k >= npairs) break;
+        uint32_t knext = 0;
+        if (threadIdx.x == 0) {
+            knext = atomicAdd(&ctl->next, 1u);
+            const int s = (int)(k / (uint32_t)ntiles);
+            const EnsTile tile = tiles[k % (uint32_t)ntiles];
+            s_tile = tile;
+            int w = 1;
+            if (s > 0) w = wait_replica(&done[tile.r], (uint32_t)s * rep_ntiles[tile.r],
+                                        &ctl->abort, __ldcg(&ctl->wait_ns));
+            if (w < 0) {
+                atomicOr(flag, LB_STEP_TIMEOUT);
+                atomicExch(&ctl->abort, 1);
             }
-            __syncthreads();
-            if (!s_go) {
-                go = false;
-                break;
-            }
-            const bool unit = sp.gamma == 0.f;   // every rate 1: the unit path
-            const bool smp = sp.drho_out != nullptr;
-#define ENS_STRIP(FN, S, U) FN<float, ORDER, S, true, U>(sp, keys.rk, tile.x0, tile.y0, tile.y1)
-            if (OV) {
-                if (unit) { if (smp) ENS_STRIP(step_strip_ov, true, true); else ENS_STRIP(step_strip_ov, false, true); }
-                else { if (smp) ENS_STRIP(step_strip_ov, true, false); else ENS_STRIP(step_strip_ov, false, false); }
+            if (w > 0)
+                fill_tile_params(sp, reps[tile.r], tile, s_t0 + (uint32_t)s, s_cur0 ^ (s & 1),
+                                 false, flag);
+            s_go = w > 0;
+        }
+        __syncthreads();
+        if (!s_go) break;
+#define ENS_STRIP(FN, U) FN<float, ORDER, false, true, U>(sp, keys.rk, s_tile.x0, s_tile.y0, s_tile.y1)
+        if (UM == 2) {
+            if (sp.gamma == 0.f) {
+                if (OV) ENS_STRIP(step_strip_ov, true); else ENS_STRIP(step_strip, true);
             } else {
-                if (unit) { if (smp) ENS_STRIP(step_strip, true, true); else ENS_STRIP(step_strip, false, true); }
-                else { if (smp) ENS_STRIP(step_strip, true, false); else ENS_STRIP(step_strip, false, false); }
+                if (OV) ENS_STRIP(step_strip_ov, false); else ENS_STRIP(step_strip, false);
             }
+        } else {
+            if (OV) ENS_STRIP(step_strip_ov, UM == 1); else ENS_STRIP(step_strip, UM == 1);
+        }
 #undef ENS_STRIP
-            __syncthreads();   // the tile's stores are done, and sp may be refilled
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(&done[tile.r], 1u);
-            }
+        if (threadIdx.x == 0) s_k[it ^ 1] = knext;
+        // read before the barrier: thread 0 overwrites s_tile after it
+        const int r = s_tile.r;
+        __syncthreads();   // the tile's stores are done, and sp may be refilled
+        if (threadIdx.x == kPoster) {
+            __threadfence();
+            atomicAdd(&done[r], 1u);
         }
     }
     // the last CTA to finish resets the barriers and advances the clock
@@ -265,8 +286,9 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
         if (threadIdx.x == 0) {
             ctl->finished = 0;
             ctl->abort = 0;
-            clk->t = t0 + (uint32_t)nsteps;
-            clk->cur = cur0 ^ (nsteps & 1);
+            ctl->next = 0;
+            clk->t = s_t0 + (uint32_t)nsteps;
+            clk->cur = s_cur0 ^ (nsteps & 1);
             clk->done = 0;
         }
         __threadfence();
@@ -344,6 +366,7 @@ struct lb_ens {
     int persist_grid = 0;                      // co-resident CTAs of the persistent kernel
     int kernel_mode = LB_KERNEL_AUTO;          // LB_KERNEL_PLAIN or _OVERLAP (strip layout)
     bool ov = false;                           // the layout in use
+    int umode = 2;                             // unit path: 1 every replica, 0 none, 2 mixed
 };
 
 namespace {
@@ -428,61 +451,75 @@ int build_tiles(lb_ens *e) {
     return LB_OK;
 }
 
-// One step of every replica; `sample` also runs the S(k) sample of all
-// replicas (the step kernel then writes delta rho: the device decides from
-// its own step counter, which agrees with the host's).
-template <int ORDER, bool OV>
-cudaError_t launch_persist_t(lb_ens *e, int nsteps, int sample_last) {
-    void *args[] = {&e->d_reps, &e->d_tiles,  &e->ntiles, &e->d_rep_ntiles,
-                    &e->d_done, &e->nrep,     &e->d_ctl,  &e->d_clk,
-                    &e->d_flag, &e->keys,     &nsteps,    &sample_last};
+template <int ORDER, bool OV, int UM>
+cudaError_t launch_persist_t(lb_ens *e, int nsteps) {
+    void *args[] = {&e->d_reps, &e->d_tiles, &e->ntiles, &e->d_rep_ntiles, &e->d_done,
+                    &e->nrep,   &e->d_ctl,   &e->d_clk,  &e->d_flag,       &e->keys,
+                    &nsteps};
     const int grid = std::min(e->persist_grid, e->ntiles);
-    return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER, OV>, dim3(grid),
-                                       dim3(OV ? kStepTX : kStepTX + 32), args, 0, e->stream);
+    return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER, OV, UM>,
+                                       dim3(grid), dim3(OV ? kStepTX : kStepTX + 32), args, 0,
+                                       e->stream);
 }
 
+// The persistent kernel of the ensemble's stencil, layout and unit mode.
+template <int ORDER, bool OV>
+const void *persist_fn_ov(int um) {
+    return um == 1   ? (const void *)ens_persist_kernel<ORDER, OV, 1>
+           : um == 0 ? (const void *)ens_persist_kernel<ORDER, OV, 0>
+                     : (const void *)ens_persist_kernel<ORDER, OV, 2>;
+}
 template <int ORDER>
-cudaError_t launch_persist_o(lb_ens *e, int nsteps, int sample_last) {
-    return e->ov ? launch_persist_t<ORDER, true>(e, nsteps, sample_last)
-                 : launch_persist_t<ORDER, false>(e, nsteps, sample_last);
+const void *persist_fn_o(const lb_ens *e) {
+    return e->ov ? persist_fn_ov<ORDER, true>(e->umode) : persist_fn_ov<ORDER, false>(e->umode);
+}
+const void *persist_fn(const lb_ens *e) {
+    return e->stencil == 4   ? persist_fn_o<4>(e)
+           : e->stencil == 6 ? persist_fn_o<6>(e)
+                             : persist_fn_o<8>(e);
 }
 
-// Co-resident CTAs of the persistent kernel of the ensemble's layout.
+template <int ORDER, bool OV>
+cudaError_t launch_persist_ov(lb_ens *e, int nsteps) {
+    return e->umode == 1   ? launch_persist_t<ORDER, OV, 1>(e, nsteps)
+           : e->umode == 0 ? launch_persist_t<ORDER, OV, 0>(e, nsteps)
+                           : launch_persist_t<ORDER, OV, 2>(e, nsteps);
+}
+template <int ORDER>
+cudaError_t launch_persist_o(lb_ens *e, int nsteps) {
+    return e->ov ? launch_persist_ov<ORDER, true>(e, nsteps)
+                 : launch_persist_ov<ORDER, false>(e, nsteps);
+}
+
+// Co-resident CTAs of the persistent kernel in use.
 cudaError_t persist_occupancy(lb_ens *e) {
     int per_sm = 0, nsm = 0;
-    const void *k;
-    if (e->ov)
-        k = e->stencil == 4   ? (const void *)ens_persist_kernel<4, true>
-            : e->stencil == 6 ? (const void *)ens_persist_kernel<6, true>
-                              : (const void *)ens_persist_kernel<8, true>;
-    else
-        k = e->stencil == 4   ? (const void *)ens_persist_kernel<4, false>
-            : e->stencil == 6 ? (const void *)ens_persist_kernel<6, false>
-                              : (const void *)ens_persist_kernel<8, false>;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k, e->ov ? kStepTX : kStepTX + 32, 0);
+        &per_sm, persist_fn(e), e->ov ? kStepTX : kStepTX + 32, 0);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->dev);
     e->persist_grid = per_sm * nsm;
     return err;
 }
 
-// `nsteps` steps of every replica in one persistent launch (the last one
-// sampling if sample_last), then the S(k) sample when sampling.
+cudaError_t launch_ens_step(lb_ens *e, bool sample);
+
+// `nsteps` steps of every replica: one persistent launch, except that a
+// sampling last step runs through the per-step kernel, which also takes the
+// S(k) sample.
 cudaError_t launch_ens_persistent(lb_ens *e, int nsteps, bool sample_last) {
-    const int sl = sample_last ? 1 : 0;
-    cudaError_t err = e->stencil == 4   ? launch_persist_o<4>(e, nsteps, sl)
-                      : e->stencil == 6 ? launch_persist_o<6>(e, nsteps, sl)
-                                        : launch_persist_o<8>(e, nsteps, sl);
+    const int n = sample_last ? nsteps - 1 : nsteps;
+    cudaError_t err = cudaSuccess;
+    if (n > 0)
+        err = e->stencil == 4   ? launch_persist_o<4>(e, n)
+              : e->stencil == 6 ? launch_persist_o<6>(e, n)
+                                : launch_persist_o<8>(e, n);
     if (err != cudaSuccess || !sample_last) return err;
-    ens_rows_kernel<<<e->nrows, 512, (size_t)e->max_nx * sizeof(float2), e->stream>>>(e->d_reps,
-                                                                                       e->d_rows);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    ens_cols_kernel<<<e->ncols, 512, (size_t)e->cpb * e->max_ny * sizeof(float2), e->stream>>>(
-        e->d_reps, e->d_cols, e->cpb);
-    return cudaGetLastError();
+    return launch_ens_step(e, true);
 }
 
+// One step of every replica; `sample` also runs the S(k) sample of all
+// replicas (the step kernel then writes delta rho: the device decides from
+// its own step counter, which agrees with the host's).
 cudaError_t launch_ens_step(lb_ens *e, bool sample) {
     const int sk_every = sample ? e->sk_every : 0;
 #define ENS_STEP(O, V, B)                                                                     \
@@ -633,8 +670,15 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
     if (err == cudaSuccess) err = cudaMemset(e->d_done, 0, nrep * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl, sizeof(EnsCtl));
     if (err == cudaSuccess) {
-        const EnsCtl c0 = {0u, 0, (unsigned long long)kEnsWaitNs};
+        const EnsCtl c0 = {0u, 0, (unsigned long long)kEnsWaitNs, 0u};
         err = cudaMemcpy(e->d_ctl, &c0, sizeof(EnsCtl), cudaMemcpyHostToDevice);
+    }
+    {
+        // a replica takes the unit path when its rate gamma rounds to 0 in
+        // FP32, the test the kernels make
+        int nunit = 0;
+        for (int r = 0; r < nrep; ++r) nunit += (float)(1.0 - 1.0 / reps[r].tau) == 0.0f;
+        e->umode = nunit == nrep ? 1 : nunit == 0 ? 0 : 2;
     }
     if (err == cudaSuccess) err = persist_occupancy(e);
     if (err != cudaSuccess) {

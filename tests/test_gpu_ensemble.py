@@ -134,3 +134,38 @@ def test_persistent_launch_many_tiles_per_cta():
         Sa, na = a.structure_factor(r)
         Sb, nb = b.structure_factor(r)
         assert na == nb and np.array_equal(Sa, Sb), r
+
+
+@pytest.mark.parametrize("kernel", [1, 3])
+@pytest.mark.parametrize("taus", ["unit", "none", "mixed"])
+def test_persistent_unit_modes_many_replicas(taus, kernel):
+    """The persistent kernel is specialised on whether every replica, none or
+    some take the unit-relaxation path; with many replicas of mixed sizes (so
+    the dynamic (step, tile) hand-out crosses steps and replicas all the
+    time) each specialisation gives the per-step bits, S(k) included."""
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    rng = np.random.default_rng(21)
+    n = 96
+    sizes = rng.choice([64, 128, 256], size=n)
+    tau = {"unit": np.ones(n), "none": rng.uniform(0.8, 1.3, n),
+           "mixed": np.where(rng.random(n) < 0.5, 1.0, 0.9)}[taus]
+    reps = [(int(s), int(s), float(rng.uniform(-4.8, -3.6)), float(t), 1e-6,
+             float(LN2 * (1 + rng.uniform(-0.1, 0.1)))) for s, t in zip(sizes, tau)]
+    a, b = Ensemble(reps, seed=13), Ensemble(reps, seed=13)
+    for e in (a, b):
+        e.set_kernel(kernel)
+        e.set_strip_height(8)
+        e.init(0.01)
+        e.sk_config(10, 10)
+    a.set_launch(abi.LB_ENS_PERSISTENT)
+    a.step(2)
+    a.step(43)
+    b.step(2)
+    b.step(43)
+    a.sync()
+    for r in range(n):
+        assert np.array_equal(a.populations(r), b.populations(r)), r
+        Sa, na = a.structure_factor(r)
+        Sb, nb = b.structure_factor(r)
+        assert na == nb == 4 and np.array_equal(Sa, Sb), r
