@@ -231,6 +231,49 @@ def ensemble_leg(stream_ptr, steps=20000, seq_steps=200, nrep=256, seed=7):
             "sizes": "uniform {64,128,256,512}^2, G~U[-4.8,-3.6], rho0=ln2(1+U[-0.1,0.1])"}
 
 
+def ensemble_small_leg(stream_ptr, steps=2000, seed=7):
+    """Ensembles of small replicas (4.2 M sites each: 1024 x 64^2, 4096 x
+    32^2, 256 x 128^2; G ~ U[-4.8, -3.6], rho0 = ln2, kT = 1e-6, S(k) every
+    50 steps, persistent launches): replicas resident in shared memory for
+    each window of steps against the same replicas as tiles.  The 128^2
+    replicas are resident over clusters of four CTAs (distributed shared
+    memory); the others in one CTA each."""
+    import torch
+
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for side, nrep in ((64, 1024), (32, 4096), (128, 256)):
+        rng = np.random.default_rng(seed)
+        reps = [(side, side, float(g), 1.0, 1e-6, RHO0) for g in rng.uniform(-4.8, -3.6, nrep)]
+        sites = side * side * nrep
+        row = {"replicas": nrep, "sites": sites, "steps": steps}
+        for name, mode in (("resident", abi.LB_ENS_RESIDENT_ON),
+                           ("tiled", abi.LB_ENS_RESIDENT_OFF)):
+            e = Ensemble(reps, seed=seed, stream=stream_ptr)
+            e.set_resident(mode)
+            e.set_launch(abi.LB_ENS_PERSISTENT)
+            e.init(0.0)
+            e.sk_config(50, 50)
+            e.autotune(10)
+            e.step(50)
+            e.sync()
+            a.record(stream)
+            e.step(steps)
+            b.record(stream)
+            b.synchronize()
+            e.sync()
+            row[name + "_mlups"] = sites * steps / (a.elapsed_time(b) * 1e-3) / 1e6
+            if mode == abi.LB_ENS_RESIDENT_ON:
+                row["resident_replicas"] = e.num_resident
+            e.close()
+        row["speedup"] = row["resident_mlups"] / row["tiled_mlups"]
+        out[f"{side}sq"] = row
+    return out
+
+
 def conv_layer_leg(nb=8, h=128, cin=64, cout=128, reps=20):
     """The surrogate's widest convolution (64 -> 128 channels on 8 images of
     128^2, BF16 operands, FP32 accumulation, bias + ReLU) on the path the
@@ -609,6 +652,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_3d:
         d3 = d3q19_leg()
     extras = rank == 0 and world == 1 and not args.no_extras
+    small = ensemble_small_leg(lat.stream()) if extras else None
     l2 = l2_assisted_leg() if extras else None
     c1 = c1_fp64_leg() if extras else None
     if rank == 0:
@@ -642,6 +686,8 @@ def run_gpu(args, rank, world, local_rank):
             line["surrogate"] = sur
         if d3 is not None:
             line["d3q19"] = d3
+        if small is not None:
+            line["ensemble_small"] = small
         if l2 is not None:
             line["l2_assisted_1024sq"] = l2
         if c1 is not None:
@@ -664,7 +710,8 @@ def main():
                     help="skip the learned-surrogate leg")
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 leg")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the 1024^2 L2-resident and 128^2 FP64 legs")
+                    help="skip the small-replica ensembles, 1024^2 L2-resident and 128^2 "
+                         "FP64 legs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

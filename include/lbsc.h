@@ -307,10 +307,12 @@ int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *cho
 /* How lb_ens_step launches the steps.  LB_ENS_PER_STEP: one launch per step
  * over every replica's tiles.  LB_ENS_PERSISTENT: each window of steps
  * (32 plain steps, or one S(k) sampling interval) is one cooperative
- * persistent launch in which a tile of a replica waits (bounded, 2 s) until
- * all tiles of that replica finished the previous step; a timeout makes the
- * next sync return LB_ERR_TIMEOUT.  Both give the same bits.
- * LB_ERR_UNSUPPORTED if the device cannot launch cooperatively. */
+ * persistent launch whose CTAs take (step, tile) pairs in order from a
+ * counter; a tile of a replica waits (bounded, 2 s) until all tiles of that
+ * replica finished the previous step; a timeout makes the next sync return
+ * LB_ERR_TIMEOUT.  A window's sampling step runs as a per-step launch.  Both
+ * give the same bits.  LB_ERR_UNSUPPORTED if the device cannot launch
+ * cooperatively. */
 #define LB_ENS_PER_STEP 0
 #define LB_ENS_PERSISTENT 1
 int lb_ens_set_launch(lb_ens *e, int mode);
@@ -333,6 +335,24 @@ int lb_ens_set_wait_ns(lb_ens *e, long long ns);
  * lb_ens_get_kernel returns the layout in use.  Errors: LB_ERR_ARG, LB_ERR_CUDA. */
 int lb_ens_set_kernel(lb_ens *e, int mode);
 int lb_ens_get_kernel(const lb_ens *e);
+/* Replicas resident in shared memory (the batched step of Eq. (12) kept on
+ * chip for a window of steps).  A replica with nx in {32, 64, 128} whose
+ * rows split into C = 1, 2, 4 or 8 equal parts of at most 4096 sites (64^2:
+ * one CTA; 128^2: a cluster of four CTAs reading each other's boundary rows
+ * through distributed shared memory) can live in shared memory for a whole
+ * window of steps, reading and writing HBM only at the window's ends (and
+ * delta rho at a sampling step).  LB_ENS_RESIDENT_OFF: none.
+ * LB_ENS_RESIDENT_ON: every replica whose shape allows it; the others run
+ * as tiles after them.  LB_ENS_RESIDENT_AUTO (the default): all replicas
+ * when each fits one CTA (C = 1), else none.  Same bits as the tile path.
+ * Synchronises the ensemble's stream and rebuilds the tile list.
+ * lb_ens_num_resident returns how many replicas are resident.
+ * Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+#define LB_ENS_RESIDENT_OFF 0
+#define LB_ENS_RESIDENT_ON 1
+#define LB_ENS_RESIDENT_AUTO 2
+int lb_ens_set_resident(lb_ens *e, int mode);
+int lb_ens_num_resident(const lb_ens *e);
 /* Advance every replica n steps (asynchronous); windows of steps replay
  * captured CUDA graphs. */
 int lb_ens_step(lb_ens *e, int n);

@@ -37,7 +37,7 @@ EXPORTED = [
     "lb_structure_factor_counts", "lb_conserved", "lb_save", "lb_load",
     "lb_device_ptr", "lb_stream", "lb_strerror", "lb_conserved_static",
     "lb_set_kernel", "lb_get_kernel", "lb_set_wait_ns", "lb_ens_set_wait_ns",
-    "lb_ens_set_kernel", "lb_ens_get_kernel",
+    "lb_ens_set_kernel", "lb_ens_get_kernel", "lb_ens_set_resident", "lb_ens_num_resident",
     "lb_ens_create", "lb_ens_destroy", "lb_ens_init", "lb_ens_sk_config",
     "lb_ens_set_strip_height", "lb_ens_autotune", "lb_ens_step", "lb_ens_sync",
     "lb_ens_get_step", "lb_ens_num_tiles", "lb_ens_populations", "lb_ens_density",
@@ -134,6 +134,8 @@ def bind(L):
         "lb_ens_set_wait_ns": (C.c_int, [P, C.c_longlong]),
         "lb_ens_set_kernel": (C.c_int, [P, C.c_int]),
         "lb_ens_get_kernel": (C.c_int, [P]),
+        "lb_ens_set_resident": (C.c_int, [P, C.c_int]),
+        "lb_ens_num_resident": (C.c_int, [P]),
         "lb_nn_set_wait_ns": (C.c_int, [C.c_longlong]),
         "lb_get_kernel": (C.c_int, [P]),
         "lb_ens_create": (C.c_int, [C.POINTER(P), C.POINTER(lb_replica), C.c_int, C.c_int,
@@ -387,6 +389,7 @@ def lb_ens_sk_config(h, every, start):
 
 
 LB_ENS_PER_STEP, LB_ENS_PERSISTENT = 0, 1
+LB_ENS_RESIDENT_OFF, LB_ENS_RESIDENT_ON, LB_ENS_RESIDENT_AUTO = 0, 1, 2
 
 
 def lb_ens_set_launch(h, mode):
@@ -403,6 +406,16 @@ def lb_ens_set_kernel(h, mode):
 
 def lb_ens_get_kernel(h):
     return load().lb_ens_get_kernel(h)
+
+
+def lb_ens_set_resident(h, mode):
+    _check(load().lb_ens_set_resident(h, int(mode)), "lb_ens_set_resident")
+
+
+def lb_ens_num_resident(h):
+    n = load().lb_ens_num_resident(h)
+    _check(min(n, 0), "lb_ens_num_resident")
+    return n
 
 
 def lb_ens_set_wait_ns(h, ns):

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbsc.so")
 
 SOURCES = ["lbsc_api.cu", "lbsc_step.cu", "lbsc_step_tma.cu", "lbsc_sk.cu", "lbsc_reduce.cu",
-           "lbsc_ensemble.cu", "lbsc_nn.cu", "lbsc_nn_tc.cu", "lbsc3.cu"]
+           "lbsc_ensemble.cu", "lbsc_resident.cu", "lbsc_nn.cu", "lbsc_nn_tc.cu", "lbsc3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

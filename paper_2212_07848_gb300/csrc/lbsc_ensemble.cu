@@ -32,70 +32,12 @@
 
 #include "lbsc.h"
 #include "lbsc_fft.cuh"
+#include "lbsc_ens.cuh"
 #include "lbsc_internal.cuh"
 #include "lbsc_strip.cuh"
 
 namespace lbsc {
 namespace {
-
-// Per-replica state on the device.
-struct EnsRep {
-    float *buf[2];
-    float *drho;
-    float2 *spec;
-    double *acc;
-    const float2 *tw_x, *tw_y;
-    int nx, ny, ldx, psi_kind;
-    int noise;
-    uint32_t replica;
-    float rho0, force_pref, psi_c, psi_b, psi0, gamma;
-    float c3a, c3b, c4a, c4b, c5a, c5b;
-    float amp[6];
-};   // single relaxation time per replica (BGK)
-struct EnsTile {
-    int r, x0, y0, y1;
-};
-struct EnsClock {
-    uint32_t t;
-    int cur;
-    uint32_t done;
-    uint32_t pad;
-};
-struct EnsKeys {
-    uint32_t rk[20];
-};
-
-// Kernel parameters of one tile of replica R at step t (current buffer cur).
-__device__ __forceinline__ void fill_tile_params(KParams<float> &sp, const EnsRep &R,
-                                                 const EnsTile &tile, uint32_t t, int cur,
-                                                 bool sample, int *flag) {
-    sp.src = R.buf[cur];
-    sp.dst = R.buf[cur ^ 1];
-    sp.drho_out = sample ? R.drho : nullptr;
-    sp.flag = flag;
-    sp.nx = R.nx;
-    sp.ny = R.ny;
-    sp.strip_h = tile.y1 - tile.y0;
-    sp.psi_kind = R.psi_kind;
-    sp.noise = R.noise;
-    sp.step = t;
-    sp.replica = R.replica;
-    sp.rho0 = R.rho0;
-    sp.force_pref = R.force_pref;
-    sp.psi_c = R.psi_c;
-    sp.psi_b = R.psi_b;
-    sp.psi0 = R.psi0;
-    sp.gamma = R.gamma;
-    sp.gamma_b = R.gamma;
-    sp.gamma_g = R.gamma;
-    sp.c3a = R.c3a;
-    sp.c3b = R.c3b;
-    sp.c4a = R.c4a;
-    sp.c4b = R.c4b;
-    sp.c5a = R.c5a;
-    sp.c5b = R.c5b;
-    for (int k = 0; k < 6; ++k) sp.amp[k] = R.amp[k];
-}
 
 // OV: the overlapped layout (kStepTX threads, strips of kStepTX - 2H
 // columns); otherwise strips of kStepTX columns and a halo warp.
@@ -316,6 +258,12 @@ __global__ void clock_set_kernel(EnsClock *clk, uint32_t t, int cur) {
     clk->cur = cur;
     clk->done = 0;
 }
+// The clock of an ensemble whose replicas are all resident (no tile kernel
+// advances it).
+__global__ void clock_advance_kernel(EnsClock *clk, int n) {
+    clk->t += (uint32_t)n;
+    clk->cur ^= n & 1;
+}
 
 constexpr double kCs2 = 1.0 / 3.0;
 constexpr double kB[6] = {4.0, 4.0 / 9.0, 1.0 / 9.0, 2.0 / 3.0, 2.0 / 3.0, 16.0};
@@ -329,6 +277,14 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 }  // namespace lbsc
 
 using namespace lbsc;
+
+// Resident replicas of one shape: C CTAs of hb-row bands per replica.
+struct ResClass {
+    int nx, ny, C, hb;
+    size_t smem;
+    std::vector<int> reps;
+    int *d_list = nullptr;
+};
 
 struct lb_ens {
     int nrep = 0, stencil = 4, psi_kind = 0, dev = 0;
@@ -367,6 +323,10 @@ struct lb_ens {
     int kernel_mode = LB_KERNEL_AUTO;          // LB_KERNEL_PLAIN or _OVERLAP (strip layout)
     bool ov = false;                           // the layout in use
     int umode = 2;                             // unit path: 1 every replica, 0 none, 2 mixed
+    int resident_mode = LB_ENS_RESIDENT_AUTO;  // which replicas live in shared memory
+    std::vector<ResClass> rclasses;            // resident replicas, one launch per shape
+    std::vector<char> is_res;                  // replica r is resident
+    int nres = 0;
 };
 
 namespace {
@@ -420,6 +380,93 @@ void drop_graphs(lb_ens *e) {
 }
 
 // Tiles of 128 columns x strip rows, largest replicas first.
+// Launch shape of a resident replica of nx x ny sites: the fewest CTAs per
+// replica (C, at most max_c) and then the shortest bands (hb) whose shared
+// memory fits one CTA and whose clusters can be resident; false if there is
+// none.
+bool resident_shape(const lb_ens *e, int nx, int ny, int max_c, ResClass *out) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->dev) !=
+        cudaSuccess)
+        return false;
+    const size_t limit = optin > 1024 ? (size_t)optin - 1024 : 0;   // static shared memory
+    for (int c : {1, 2, 4, 8}) {
+        if (c > max_c || ny % c) continue;
+        const int rows = ny / c;
+        for (int hb : {8, 16, 32}) {
+            if (rows % hb) continue;
+            const size_t sm = resident_smem(nx, rows, hb, e->stencil);
+            if (!sm || sm > limit) continue;
+            if (resident_prepare(e->stencil, c, limit) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (resident_max_clusters(e->stencil, c, nx, rows, hb, sm) < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            out->nx = nx;
+            out->ny = ny;
+            out->C = c;
+            out->hb = hb;
+            out->smem = sm;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Which replicas live in shared memory (resident_mode): none; every one
+// whose shape allows it; or, AUTO, all of them when each fits one CTA.
+// AUTO leaves out the clusters (128^2 over four CTAs measured 42 against 63
+// GLUPS tiled: a tile already fills its 128 columns, clusters of four
+// 200 KB CTAs leave SMs of each GPC idle and each step waits at two cluster
+// barriers) and mixed ensembles (the resident launch runs before the tiles,
+// so its few CTAs would hold up the rest of the GPU).
+int setup_resident(lb_ens *e) {
+    for (auto &c : e->rclasses) cudaFree(c.d_list);
+    e->rclasses.clear();
+    e->is_res.assign(e->nrep, 0);
+    e->nres = 0;
+    if (e->resident_mode == LB_ENS_RESIDENT_OFF) return LB_OK;
+    std::vector<ResClass> cls;
+    std::vector<std::pair<long, int>> tried;   // shape -> class index or -1
+    int n = 0;
+    for (int r = 0; r < e->nrep; ++r) {
+        const int nx = e->reps[r].nx, ny = e->reps[r].ny;
+        const long key = (long)nx * 1000003L + ny;
+        int k = -2;
+        for (const auto &t : tried)
+            if (t.first == key) k = t.second;
+        if (k == -2) {
+            ResClass c;
+            const int max_c = e->resident_mode == LB_ENS_RESIDENT_AUTO ? 1 : 8;
+            if (resident_shape(e, nx, ny, max_c, &c)) {
+                cls.push_back(c);
+                k = (int)cls.size() - 1;
+            } else {
+                k = -1;
+            }
+            tried.push_back({key, k});
+        }
+        if (k < 0) {
+            if (e->resident_mode == LB_ENS_RESIDENT_AUTO) return LB_OK;
+            continue;
+        }
+        cls[k].reps.push_back(r);
+        ++n;
+    }
+    for (auto &c : cls) {
+        ENS_CHECK(cudaMalloc(&c.d_list, c.reps.size() * sizeof(int)));
+        ENS_CHECK(cudaMemcpy(c.d_list, c.reps.data(), c.reps.size() * sizeof(int),
+                             cudaMemcpyHostToDevice));
+        for (int r : c.reps) e->is_res[r] = 1;
+    }
+    e->rclasses = std::move(cls);
+    e->nres = n;
+    return LB_OK;
+}
+
 int build_tiles(lb_ens *e) {
     std::vector<EnsTile> tiles;
     std::vector<int> order(e->nrep);
@@ -429,6 +476,7 @@ int build_tiles(lb_ens *e) {
     });
     std::vector<int> per_rep(e->nrep, 0);
     for (int r : order) {
+        if (e->is_res[r]) continue;   // advanced by the resident kernel
         const int nx = e->reps[r].nx, ny = e->reps[r].ny;
         const int h = std::min(e->strip_h, ny);
         const int cols = e->ov ? kStepTX - 2 * (e->stencil == 4 ? 1 : 2) : kStepTX;
@@ -440,9 +488,11 @@ int build_tiles(lb_ens *e) {
     }
     if (e->d_tiles) cudaFree(e->d_tiles);
     e->d_tiles = nullptr;
-    ENS_CHECK(cudaMalloc(&e->d_tiles, tiles.size() * sizeof(EnsTile)));
-    ENS_CHECK(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
-                         cudaMemcpyHostToDevice));
+    if (!tiles.empty()) {
+        ENS_CHECK(cudaMalloc(&e->d_tiles, tiles.size() * sizeof(EnsTile)));
+        ENS_CHECK(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
+                             cudaMemcpyHostToDevice));
+    }
     if (!e->d_rep_ntiles) ENS_CHECK(cudaMalloc(&e->d_rep_ntiles, e->nrep * sizeof(int)));
     ENS_CHECK(cudaMemcpy(e->d_rep_ntiles, per_rep.data(), e->nrep * sizeof(int),
                          cudaMemcpyHostToDevice));
@@ -509,7 +559,10 @@ cudaError_t launch_ens_step(lb_ens *e, bool sample);
 cudaError_t launch_ens_persistent(lb_ens *e, int nsteps, bool sample_last) {
     const int n = sample_last ? nsteps - 1 : nsteps;
     cudaError_t err = cudaSuccess;
-    if (n > 0)
+    if (n > 0 && e->ntiles == 0) {
+        clock_advance_kernel<<<1, 1, 0, e->stream>>>(e->d_clk, n);
+        err = cudaGetLastError();
+    } else if (n > 0)
         err = e->stencil == 4   ? launch_persist_o<4>(e, n)
               : e->stencil == 6 ? launch_persist_o<6>(e, n)
                                 : launch_persist_o<8>(e, n);
@@ -526,7 +579,9 @@ cudaError_t launch_ens_step(lb_ens *e, bool sample) {
     ens_step_kernel<O, V><<<e->ntiles, B, 0, e->stream>>>(e->d_reps, e->d_tiles, e->ntiles,   \
                                                           e->d_clk, e->d_flag, e->keys,       \
                                                           sk_every, e->sk_start)
-    if (e->ov) {
+    if (e->ntiles == 0) {
+        clock_advance_kernel<<<1, 1, 0, e->stream>>>(e->d_clk, 1);
+    } else if (e->ov) {
         if (e->stencil == 4) ENS_STEP(4, true, kStepTX);
         else if (e->stencil == 6) ENS_STEP(6, true, kStepTX);
         else ENS_STEP(8, true, kStepTX);
@@ -552,16 +607,39 @@ bool is_sample_step(const lb_ens *e, long long tn) {
            (tn - e->sk_start) % e->sk_every == 0;
 }
 
+// `steps` consecutive steps of every replica, the last one sampling if
+// sample_last: the resident replicas in one launch per shape, then the
+// tiles (which advance the device clock and take the S(k) sample).
+cudaError_t launch_window(lb_ens *e, int steps, bool sample_last) {
+    cudaError_t err = cudaSuccess;
+    for (const auto &c : e->rclasses) {
+        ResLaunch a;
+        a.reps = e->d_reps;
+        a.list = c.d_list;
+        a.nres = (int)c.reps.size();
+        a.nx = c.nx;
+        a.ny = c.ny;
+        a.C = c.C;
+        a.hb = c.hb;
+        a.stencil = e->stencil;
+        a.clk = e->d_clk;
+        a.flag = e->d_flag;
+        a.keys = e->keys;
+        a.nsteps = steps;
+        a.sample = sample_last ? 1 : 0;
+        if ((err = launch_ens_resident(a, e->stream)) != cudaSuccess) return err;
+    }
+    if (e->launch_mode == LB_ENS_PERSISTENT) return launch_ens_persistent(e, steps, sample_last);
+    for (int s = 0; s < steps && err == cudaSuccess; ++s)
+        err = launch_ens_step(e, sample_last && s == steps - 1);
+    return err;
+}
+
 // Capture `steps` consecutive steps, the last one sampling if sample_last.
 int capture(lb_ens *e, int steps, bool sample_last, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     ENS_CHECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
-    if (e->launch_mode == LB_ENS_PERSISTENT)
-        err = launch_ens_persistent(e, steps, sample_last);
-    else
-        for (int s = 0; s < steps && err == cudaSuccess; ++s)
-            err = launch_ens_step(e, sample_last && s == steps - 1);
+    cudaError_t err = launch_window(e, steps, sample_last);
     cudaError_t err2 = cudaStreamEndCapture(e->stream, &g);
     if (err != cudaSuccess || err2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -575,6 +653,8 @@ int capture(lb_ens *e, int steps, bool sample_last, cudaGraphExec_t *out) {
 
 void free_ens(lb_ens *e) {
     drop_graphs(e);
+    for (auto &c : e->rclasses) cudaFree(c.d_list);
+    e->rclasses.clear();
     cudaFree(e->pool);
     cudaFree(e->sk_pool);
     cudaFree(e->d_reps);
@@ -698,7 +778,8 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
         e->max_nx = std::max(e->max_nx, R.nx);
         e->max_ny = std::max(e->max_ny, R.ny);
     }
-    int rc = build_tiles(e);
+    int rc = setup_resident(e);
+    if (rc == LB_OK) rc = build_tiles(e);
     if (rc == LB_OK && cudaMemcpy(e->d_reps, e->h_reps.data(), nrep * sizeof(EnsRep),
                                   cudaMemcpyHostToDevice) != cudaSuccess)
         rc = LB_ERR_CUDA;
@@ -841,6 +922,19 @@ int lb_ens_set_kernel(lb_ens *e, int mode) {
     return build_tiles(e);
 }
 
+int lb_ens_set_resident(lb_ens *e, int mode) {
+    if (!e || (mode != LB_ENS_RESIDENT_OFF && mode != LB_ENS_RESIDENT_ON &&
+               mode != LB_ENS_RESIDENT_AUTO))
+        return LB_ERR_ARG;
+    ENS_CHECK(cudaSetDevice(e->dev));
+    ENS_CHECK(cudaStreamSynchronize(e->stream));
+    e->resident_mode = mode;
+    const int rc = setup_resident(e);
+    return rc != LB_OK ? rc : build_tiles(e);
+}
+
+int lb_ens_num_resident(const lb_ens *e) { return e ? e->nres : LB_ERR_ARG; }
+
 int lb_ens_get_kernel(const lb_ens *e) {
     if (!e) return LB_ERR_ARG;
     return e->ov ? LB_KERNEL_OVERLAP : LB_KERNEL_PLAIN;
@@ -884,7 +978,7 @@ int lb_ens_step(lb_ens *e, int n) {
             continue;
         }
         const bool sample = is_sample_step(e, t + 1);
-        ENS_CHECK(launch_ens_step(e, sample));
+        ENS_CHECK(launch_window(e, 1, sample));
         e->t += 1;
         e->cur ^= 1;
         if (sample) e->sk_count += 1;
@@ -985,15 +1079,22 @@ int lb_ens_structure_factor(lb_ens *e, int r, double *host_out, int nbins,
 
 // Autotuner: time each candidate strip height on a snapshot of the state and
 // keep the fastest; the state, clock and S(k) sums are restored afterwards.
-// The choice is cached in `cache_path` (one "key strip" line per ensemble
-// shape and device) when the path is not NULL.
+// The candidates run in the launch mode and strip layout in use.  The choice
+// is cached in `cache_path` (one "key strip" line per ensemble shape, launch
+// mode, layout and device) when the path is not NULL.
 int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *chosen) {
     if (!e || trial_steps < 1) return LB_ERR_ARG;
     if (!e->inited) return LB_ERR_STATE;
     ENS_CHECK(cudaSetDevice(e->dev));
+    if (e->ntiles == 0) {   // every replica resident: there is no tile shape to tune
+        if (chosen) *chosen = e->strip_h;
+        return LB_OK;
+    }
     cudaDeviceProp prop;
     ENS_CHECK(cudaGetDeviceProperties(&prop, e->dev));
-    std::string key = std::string(prop.name) + "|E" + std::to_string(e->stencil);
+    std::string key = std::string(prop.name) + "|E" + std::to_string(e->stencil) +
+                      (e->launch_mode == LB_ENS_PERSISTENT ? "|P" : "|S") +
+                      (e->ov ? "|ov" : "|hw") + "|R" + std::to_string(e->nres);
     {
         std::vector<long> sizes;
         for (const auto &q : e->reps) sizes.push_back((long)q.nx * 100000 + q.ny);
@@ -1038,11 +1139,17 @@ int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *cho
     cudaEventCreate(&b);
     e->sk_every = 0;
     int rc = LB_OK;
+    // each candidate runs the way steps will run: one launch per step, or
+    // one persistent launch for the whole trial
+    const bool persist = e->launch_mode == LB_ENS_PERSISTENT;
     for (int c : cand) {
         if ((rc = lb_ens_set_strip_height(e, c)) != LB_OK) break;
-        for (int w = 0; w < 2 && rc == LB_OK; ++w) rc = cuda_status(launch_ens_step(e, false));
+        if (persist) rc = cuda_status(launch_ens_persistent(e, 2, false));
+        else
+            for (int w = 0; w < 2 && rc == LB_OK; ++w) rc = cuda_status(launch_ens_step(e, false));
         cudaEventRecord(a, e->stream);
-        for (int s = 0; s < trial_steps && rc == LB_OK; ++s)
+        if (persist && rc == LB_OK) rc = cuda_status(launch_ens_persistent(e, trial_steps, false));
+        for (int s = 0; s < trial_steps && rc == LB_OK && !persist; ++s)
             rc = cuda_status(launch_ens_step(e, false));
         cudaEventRecord(b, e->stream);
         if (rc != LB_OK) break;

@@ -51,6 +51,14 @@ class Ensemble:
     def kernel(self):
         return abi.lb_ens_get_kernel(self._h)
 
+    def set_resident(self, mode):
+        """Shared-memory-resident replicas: abi.LB_ENS_RESIDENT_OFF / _ON / _AUTO."""
+        abi.lb_ens_set_resident(self._h, mode)
+
+    @property
+    def num_resident(self):
+        return abi.lb_ens_num_resident(self._h)
+
     def set_strip_height(self, rows):
         abi.lb_ens_set_strip_height(self._h, rows)
 

@@ -169,3 +169,99 @@ def test_persistent_unit_modes_many_replicas(taus, kernel):
         Sa, na = a.structure_factor(r)
         Sb, nb = b.structure_factor(r)
         assert na == nb == 4 and np.array_equal(Sa, Sb), r
+
+
+# shapes that live in shared memory: one CTA (64^2, 32^2, 32 x 128) or a
+# cluster of CTAs reading each other's rows (128 x 64: two, 128^2: four)
+RESIDENT_SHAPES = [(64, 64), (32, 32), (32, 128), (128, 64), (128, 128)]
+
+
+def _resident_pair(reps, stencil, launch, seed=31):
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    a = Ensemble(reps, stencil=stencil, seed=seed)
+    b = Ensemble(reps, stencil=stencil, seed=seed)
+    a.set_resident(abi.LB_ENS_RESIDENT_ON)
+    b.set_resident(abi.LB_ENS_RESIDENT_OFF)
+    assert b.num_resident == 0
+    for e in (a, b):
+        e.set_launch(launch)
+        e.set_strip_height(16)
+        e.init(0.01)
+        e.sk_config(5, 10)
+        e.step(3)          # single steps
+        e.step(37)         # sampling windows of 5 steps
+        e.step(33)         # a plain 32-step window + 1
+    a.sync()
+    b.sync()
+    return a, b
+
+
+@pytest.mark.parametrize("stencil", [4, 6, 8])
+@pytest.mark.parametrize("shape", RESIDENT_SHAPES)
+def test_resident_replicas_match_tiles(shape, stencil):
+    """Replicas kept in shared memory over whole windows of steps (in place,
+    band by band, boundary rows copied each step, across a cluster through
+    distributed shared memory) give the tile path's bits, S(k) included,
+    for unit and general relaxation rates."""
+    nx, ny = shape
+    reps = [(nx, ny, -4.4, 1.0, 1e-5, LN2), (nx, ny, -3.9, 0.8, 1e-5, 0.7),
+            (nx, ny, -4.7, 1.0, 0.0, 0.72)]
+    a, b = _resident_pair(reps, stencil, 0)
+    assert a.num_resident == len(reps)
+    assert a.num_tiles == 0
+    for r in range(len(reps)):
+        assert np.array_equal(a.populations(r), b.populations(r)), r
+        Sa, na = a.structure_factor(r)
+        Sb, nb = b.structure_factor(r)
+        assert na == nb == 13 and np.array_equal(Sa, Sb), r
+
+
+@pytest.mark.parametrize("launch", [0, 1])
+def test_resident_and_tiled_replicas_together(launch):
+    """Resident replicas next to replicas that stay tiled (too wide or too
+    narrow for shared memory), per-step and persistent tile launches: every
+    replica keeps the bits of a single lattice."""
+    reps = [(64, 64, -4.4, 1.0, 1e-5, LN2), (256, 64, -4.0, 1.0, 1e-5, 0.7),
+            (128, 128, -4.6, 0.9, 1e-5, 0.68), (16, 64, -3.8, 1.0, 1e-5, LN2),
+            (32, 32, -4.2, 1.0, 1e-5, 0.7)]
+    a, b = _resident_pair(reps, 4, launch)
+    assert a.num_resident == 3
+    for r, rep in enumerate(reps):
+        assert np.array_equal(a.populations(r), b.populations(r)), r
+        Sa, na = a.structure_factor(r)
+        Sb, nb = b.structure_factor(r)
+        assert na == nb and np.array_equal(Sa, Sb), r
+    # and against single lattices
+    for r, rep in enumerate(reps):
+        g = _single(r, rep, 31, 0.01, (5, 10))
+        g.step(73)
+        assert np.array_equal(a.populations(r), g.populations()), r
+
+
+def test_resident_auto_policy():
+    """AUTO keeps an ensemble in shared memory only when every replica fits
+    one CTA; clusters only when asked for."""
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    small = [(64, 64, -4.4, 1.0, 1e-6, LN2)] * 4
+    e = Ensemble(small, seed=1)
+    assert e.num_resident == 4 and e.num_tiles == 0
+    e.set_resident(abi.LB_ENS_RESIDENT_OFF)
+    assert e.num_resident == 0 and e.num_tiles > 0
+    mixed = small + [(256, 256, -4.4, 1.0, 1e-6, LN2)]
+    m = Ensemble(mixed, seed=1)
+    assert m.num_resident == 0
+    m.set_resident(abi.LB_ENS_RESIDENT_ON)
+    assert m.num_resident == 4
+    m.init(0.0)
+    assert m.autotune(3) in (8, 12, 16, 24, 32, 48)
+    c = Ensemble([(128, 128, -4.4, 1.0, 1e-6, LN2)] * 2, seed=1)
+    assert c.num_resident == 0
+    c.set_resident(abi.LB_ENS_RESIDENT_ON)
+    assert c.num_resident == 2
+    e.set_resident(abi.LB_ENS_RESIDENT_AUTO)
+    e.init(0.0)
+    e.autotune(3)          # nothing tiled: the call keeps the strip height
+    e.step(40)
+    e.sync()
