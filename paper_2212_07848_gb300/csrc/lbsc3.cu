@@ -96,6 +96,25 @@ constexpr int kTX3 = 32, kTY3 = 4;
 constexpr int kBX3 = kTX3 + 2, kBY3 = kTY3 + 2;      // tile + halo ring
 constexpr int kThreads3 = kBX3 * kBY3;               // 204
 constexpr int kCtasPerSm3 = 4;
+static_assert(kTX3 == 32, "one warp per interior row");
+
+// Thread -> (tx, ty) of the 34 x 6 block: warps 0..3 are the four interior
+// rows (ty = 1..4, tx = 1..32), so the collision runs on full warps; then
+// the two ring rows (ty = 0, 5) and the twelve ring columns (tx = 0, 33).
+__device__ __forceinline__ void ring_xy3(int t, int &tx, int &ty) {
+    if (t < kTX3 * kTY3) {
+        tx = 1 + (t & 31);
+        ty = 1 + (t >> 5);
+    } else if (t < kTX3 * (kTY3 + 2)) {
+        t -= kTX3 * kTY3;
+        tx = 1 + (t & 31);
+        ty = t < kTX3 ? 0 : kBY3 - 1;
+    } else {
+        t -= kTX3 * (kTY3 + 2);
+        tx = t < kBY3 ? 0 : kBX3 - 1;
+        ty = t < kBY3 ? t : t - kBY3;
+    }
+}
 
 template <typename T> struct K3 {
     const T *__restrict__ src;
@@ -325,7 +344,8 @@ step3_kernel(const K3<T> p) {
     __shared__ float2 s_ring[kRing3];    // noise angles (FP32 path; read after the first barrier)
     if (std::is_same<T, float>::value && p.noise)
         for (int i = threadIdx.x; i < kRing3; i += blockDim.x) s_ring[i] = p.ring[i];
-    const int tx = threadIdx.x % kBX3, ty = threadIdx.x / kBX3;
+    int tx, ty;
+    ring_xy3(threadIdx.x, tx, ty);
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const uint32_t plane = (uint32_t)nx * ny * nz;
     int x = blockIdx.x * kTX3 - 1 + tx, y = blockIdx.y * kTY3 - 1 + ty;
