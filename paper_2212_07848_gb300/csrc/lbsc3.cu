@@ -87,32 +87,39 @@ constexpr bool norms_agree() {
 }
 static_assert(norms_agree(), "moment norms");
 
-// A CTA owns a 32 x 4 tile of (x, y) columns plus their one-column halo ring
-// (34 x 6 = 204 threads, 72 registers, four CTAs per SM in FP32; two in FP64).  The step is
-// latency-bound, so more resident warps beat a smaller halo share: 32 x 4
-// measured faster than 32 x 8 (two CTAs per SM), 16 x 8, 64 x 4, 32 x 16 and
-// 64 x 8 at 256^3 on GB300.
-constexpr int kTX3 = 32, kTY3 = 4;
-constexpr int kBX3 = kTX3 + 2, kBY3 = kTY3 + 2;      // tile + halo ring
-constexpr int kThreads3 = kBX3 * kBY3;               // 204
-constexpr int kCtasPerSm3 = 4;
+// A CTA owns a 32 x TY tile of (x, y) columns plus their one-column halo ring
+// (34 x (TY + 2) threads).  Each interior row is one warp, so the collision
+// runs on full warps; the ring rows and columns take the remaining threads.
+// FP32 uses 32 x 8 tiles (340 threads, 80 registers, two CTAs per SM) when
+// ny is a multiple of 8, else 32 x 4 (204 threads, four per SM); FP64 always
+// 32 x 4 (two per SM).  Measured at 256^3 FP32 on GB300: 32 x 8 30.1 GLUPS,
+// 32 x 4 28.9, 32 x 8 at three CTAs per SM (56 registers, spilling) 26.0;
+// with the rows split across warps (the linear thread order) 32 x 4 ran at
+// 24.5.  Prefetching the next plane (into registers at three CTAs per SM, or
+// by cp.async into shared memory) measured slower: the step is bound by issue
+// and resident warps, not by the loads' latency.
+constexpr int kTX3 = 32;
+constexpr int kTYMin3 = 4;   // ny must be a multiple of this
 static_assert(kTX3 == 32, "one warp per interior row");
+template <int TY> constexpr int threads3() { return (kTX3 + 2) * (TY + 2); }
 
-// Thread -> (tx, ty) of the 34 x 6 block: warps 0..3 are the four interior
-// rows (ty = 1..4, tx = 1..32), so the collision runs on full warps; then
-// the two ring rows (ty = 0, 5) and the twelve ring columns (tx = 0, 33).
+// Thread -> (tx, ty) of the 34 x (TY + 2) block: warps 0 .. TY - 1 are the
+// interior rows (ty = 1 .. TY, tx = 1 .. 32); then the two ring rows
+// (ty = 0, TY + 1) and the 2 (TY + 2) ring columns (tx = 0, 33).
+template <int TY>
 __device__ __forceinline__ void ring_xy3(int t, int &tx, int &ty) {
-    if (t < kTX3 * kTY3) {
+    constexpr int BY = TY + 2;
+    if (t < kTX3 * TY) {
         tx = 1 + (t & 31);
         ty = 1 + (t >> 5);
-    } else if (t < kTX3 * (kTY3 + 2)) {
-        t -= kTX3 * kTY3;
+    } else if (t < kTX3 * BY) {
+        t -= kTX3 * TY;
         tx = 1 + (t & 31);
-        ty = t < kTX3 ? 0 : kBY3 - 1;
+        ty = t < kTX3 ? 0 : BY - 1;
     } else {
-        t -= kTX3 * (kTY3 + 2);
-        tx = t < kBY3 ? 0 : kBX3 - 1;
-        ty = t < kBY3 ? t : t - kBY3;
+        t -= kTX3 * BY;
+        tx = t < BY ? 0 : kTX3 + 1;
+        ty = t < BY ? t : t - BY;
     }
 }
 
@@ -337,21 +344,22 @@ __device__ __forceinline__ void collide3_m(const T m[19], T Fx, T Fy, T Fz, cons
 }
 
 
-template <typename T, bool SAMPLE, bool UNIT = false>
-__global__ void __launch_bounds__(kThreads3, sizeof(T) == 4 ? kCtasPerSm3 : 2)
+template <typename T, bool SAMPLE, bool UNIT, int TY>
+__global__ void __launch_bounds__(threads3<TY>(), (sizeof(T) == 4 && TY == 4) ? 4 : 2)
 step3_kernel(const K3<T> p) {
+    constexpr int kBX3 = kTX3 + 2, kBY3 = TY + 2;
     __shared__ T s_psi[4][kBY3][kBX3];   // ring of planes: one barrier per plane suffices
     __shared__ float2 s_ring[kRing3];    // noise angles (FP32 path; read after the first barrier)
     if (std::is_same<T, float>::value && p.noise)
         for (int i = threadIdx.x; i < kRing3; i += blockDim.x) s_ring[i] = p.ring[i];
     int tx, ty;
-    ring_xy3(threadIdx.x, tx, ty);
+    ring_xy3<TY>(threadIdx.x, tx, ty);
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const uint32_t plane = (uint32_t)nx * ny * nz;
-    int x = blockIdx.x * kTX3 - 1 + tx, y = blockIdx.y * kTY3 - 1 + ty;
+    int x = blockIdx.x * kTX3 - 1 + tx, y = blockIdx.y * TY - 1 + ty;
     x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
     y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    const bool interior = tx >= 1 && tx <= kTX3 && ty >= 1 && ty <= kTY3;
+    const bool interior = tx >= 1 && tx <= kTX3 && ty >= 1 && ty <= TY;
     const int z0 = blockIdx.z * p.strip_z, z1 = min(z0 + p.strip_z, nz);
     const int it_end = (z1 - z0) + 2;
 
@@ -805,26 +813,31 @@ K3<T> params3(const lb3_ctx *h, bool sample) {
     return k;
 }
 
+template <typename T, int TY>
+int step3_launch(lb3_ctx *h, const K3<T> &k, bool sample) {
+    const dim3 grid(h->nx / kTX3, h->ny / TY, (h->nz + h->strip_z - 1) / h->strip_z);
+    const int nt = threads3<TY>();
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->tau == 1.0) {   // gamma = 0: the unit-relaxation path
+            if (sample) step3_kernel<T, true, true, TY><<<grid, nt, 0, h->stream>>>(k);
+            else step3_kernel<T, false, true, TY><<<grid, nt, 0, h->stream>>>(k);
+            done = true;
+        }
+    }
+    if (!done && sample) step3_kernel<T, true, false, TY><<<grid, nt, 0, h->stream>>>(k);
+    else if (!done) step3_kernel<T, false, false, TY><<<grid, nt, 0, h->stream>>>(k);
+    L3_CHECK(cudaGetLastError());
+    return LB_OK;
+}
+
 template <typename T>
 int step3_once(lb3_ctx *h, bool sample) {
     const K3<T> k = params3<T>(h, sample);
-    dim3 grid(h->nx / kTX3, h->ny / kTY3, (h->nz + h->strip_z - 1) / h->strip_z);
     if constexpr (std::is_same<T, float>::value) {
-        if (h->tau == 1.0) {       // gamma = 0: the unit-relaxation path
-            if (sample)
-                step3_kernel<T, true, true><<<grid, kThreads3, 0, h->stream>>>(k);
-            else
-                step3_kernel<T, false, true><<<grid, kThreads3, 0, h->stream>>>(k);
-            L3_CHECK(cudaGetLastError());
-            return LB_OK;
-        }
+        if (h->ny % 8 == 0) return step3_launch<T, 8>(h, k, sample);
     }
-    if (sample)
-        step3_kernel<T, true><<<grid, kThreads3, 0, h->stream>>>(k);
-    else
-        step3_kernel<T, false><<<grid, kThreads3, 0, h->stream>>>(k);
-    L3_CHECK(cudaGetLastError());
-    return LB_OK;
+    return step3_launch<T, 4>(h, k, sample);
 }
 
 // Lines per block of a length-n transform: as many as fit 128 KB (at most 64).
@@ -924,7 +937,7 @@ int lb3_create(lb3_ctx **out, int nx, int ny, int nz, double G, double tau, doub
                int precision, void *stream) {
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
-    if (nx < kTX3 || ny < kTY3 || nz < 3 || nx % kTX3 || ny % kTY3) return LB_ERR_ARG;
+    if (nx < kTX3 || ny < kTYMin3 || nz < 3 || nx % kTX3 || ny % kTYMin3) return LB_ERR_ARG;
     if (19.0 * (double)nx * ny * nz >= 4294967296.0) return LB_ERR_ARG;
     if (!(tau > 0.5) || !(kT >= 0.0) || !isfinite(G)) return LB_ERR_ARG;
     if (precision != LB_FP32 && precision != LB_FP64) return LB_ERR_ARG;

@@ -52,8 +52,12 @@ def test_pseudopotential_kinds_match_oracle(kind, p1, p2, rho0):
         assert max_rel(g.density(), o.density()) < tol, prec
 
 
-def test_fp32_matches_oracle():
-    g, o = _pair(32, 16, 8, -4.2, 1.0, 1e-5, "fp32", 0.6, 4, 0.005)
+# FP32 tiles are 32 x 8 when ny is a multiple of 8, else 32 x 4; tau = 1
+# takes the unit-relaxation path
+@pytest.mark.parametrize("nx,ny,nz,tau", [(32, 16, 8, 1.0), (32, 12, 8, 1.0), (64, 20, 6, 0.8),
+                                          (32, 24, 7, 0.9)])
+def test_fp32_matches_oracle(nx, ny, nz, tau):
+    g, o = _pair(nx, ny, nz, -4.2, tau, 1e-5, "fp32", 0.6, 4, 0.005)
     g.step(100)
     o.step(100)
     assert max_rel(g.populations(), o.populations()) < 1e-4
