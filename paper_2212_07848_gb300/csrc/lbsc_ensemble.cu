@@ -103,10 +103,11 @@ ens_step_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ til
 // `nsteps` steps.  The (step, tile) pairs are handed out in order, step-major,
 // from one atomic counter: a CTA that finishes a tile takes the next pair, so
 // the work balances itself across CTAs and the tiles of step s + 1 start
-// while the last tiles of step s run.  A tile of replica r at step s may
-// start once all tiles of r have finished step s - 1 (a per-replica
-// completion counter, bounded wait), which is all it reads; those tiles were
-// handed out earlier to CTAs that are all resident, so the waits always end.
+// while the last tiles of step s run.  A tile at step s may start once the
+// tiles whose cells it pulls (itself and its neighbours within the stencil's
+// reach) have finished step s - 1 (per-tile completion counters, bounded
+// wait): they wrote what it reads, and its stores overwrite what they read.
+// Those pairs were handed out earlier, so the waits always end.
 // The buffers alternate inside the launch, so pulls go through L2
 // (ld.global.cg), not the read-only path.  The last CTA to finish resets the
 // counters and advances the device clock.
@@ -129,17 +130,32 @@ __device__ __forceinline__ uint64_t ens_global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// 1: the counter reached target; 0: another CTA aborted; -1: timed out.
-// A limit of 0 gives up at the first check that finds the counter short.
-__device__ int wait_replica(const uint32_t *cnt, uint32_t target, const int *abort,
-                            uint64_t limit_ns) {
-    if (ld_acquire_u32(cnt) >= target) return 1;
+
+// Wait, as one warp, until counter nbr[q0 + q] of tdone reaches target for
+// every q < cnt: lane l checks q = l, l + 32, ... and the warp decides
+// together (one round trip to L2 per check, not one per counter).  Every
+// lane returns 1 when they did, 0 when another CTA aborted, -1 on a timeout;
+// a limit of 0 gives up at the first check that finds a counter short.
+__device__ int wait_tiles(const uint32_t *tdone, const int *__restrict__ nbr, int q0, int cnt,
+                          uint32_t target, const int *abort, uint64_t limit_ns) {
+    const int lane = threadIdx.x & 31;
+    auto ready = [&]() {
+        bool ok = true;
+        for (int q = lane; q < cnt; q += 32) ok = ok && ld_acquire_u32(&tdone[nbr[q0 + q]]) >= target;
+        return __all_sync(0xffffffffu, ok);
+    };
+    if (ready()) return 1;
     if (limit_ns == 0) return -1;
     const uint64_t t0 = ens_global_ns();
     for (;;) {
-        if (ld_acquire_u32(cnt) >= target) return 1;
-        if (*(volatile const int *)abort) return 0;
-        if (ens_global_ns() - t0 > limit_ns) return -1;
+        if (ready()) return 1;
+        int stop = 2;   // lane 0 decides: 0 another CTA aborted, -1 timed out
+        if (lane == 0) {
+            if (*(volatile const int *)abort) stop = 0;
+            else if (ens_global_ns() - t0 > limit_ns) stop = -1;
+        }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop != 2) return stop;
         __nanosleep(100);
     }
 }
@@ -153,11 +169,12 @@ template <int ORDER, bool OV, int UM>
 __global__ void __launch_bounds__(OV ? kStepTX : kStepTX + 32, OV ? (ORDER == 4 ? 8 : 5)
                                                                   : (ORDER == 4 ? 6 : 4))
 ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ tiles,
-                   int ntiles, const int *__restrict__ rep_ntiles, uint32_t *done, int nrep,
-                   EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys, int nsteps) {
+                   int ntiles, const int *__restrict__ nbr_off, const int *__restrict__ nbr,
+                   uint32_t *tdone, EnsCtl *ctl, EnsClock *clk, int *flag, const EnsKeys keys,
+                   int nsteps) {
     __shared__ KParams<float> sp;
     __shared__ EnsTile s_tile;
-    __shared__ int s_go, s_last, s_cur0;
+    __shared__ int s_go, s_last, s_cur0, s_ti;
     __shared__ uint32_t s_k[2], s_t0;
     // what lives across the strip sits in shared memory: the strip needs
     // every register the launch bounds leave
@@ -178,22 +195,31 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
         const uint32_t k = s_k[it];
         if (k >= npairs) break;
         uint32_t knext = 0;
-        if (threadIdx.x == 0) {
-            knext = atomicAdd(&ctl->next, 1u);
-            const int s = (int)(k / (uint32_t)ntiles);
-            const EnsTile tile = tiles[k % (uint32_t)ntiles];
-            s_tile = tile;
+        if (threadIdx.x < 32) {   // warp 0 sets the tile up
+            const int s = (int)(k / (uint32_t)ntiles), i = (int)(k % (uint32_t)ntiles);
+            if (threadIdx.x == 0) knext = atomicAdd(&ctl->next, 1u);
+            // the tiles whose cells this one pulls (itself included) must have
+            // finished step s - 1: they wrote what it reads, and its stores
+            // overwrite what they read in step s - 1
             int w = 1;
-            if (s > 0) w = wait_replica(&done[tile.r], (uint32_t)s * rep_ntiles[tile.r],
-                                        &ctl->abort, __ldcg(&ctl->wait_ns));
-            if (w < 0) {
-                atomicOr(flag, LB_STEP_TIMEOUT);
-                atomicExch(&ctl->abort, 1);
+            if (s > 0) {
+                const int q0 = nbr_off[i];
+                w = wait_tiles(tdone, nbr, q0, nbr_off[i + 1] - q0, (uint32_t)s, &ctl->abort,
+                               __ldcg(&ctl->wait_ns));
             }
-            if (w > 0)
-                fill_tile_params(sp, reps[tile.r], tile, s_t0 + (uint32_t)s, s_cur0 ^ (s & 1),
-                                 false, flag);
-            s_go = w > 0;
+            if (threadIdx.x == 0) {
+                const EnsTile tile = tiles[i];
+                s_tile = tile;
+                s_ti = i;
+                if (w < 0) {
+                    atomicOr(flag, LB_STEP_TIMEOUT);
+                    atomicExch(&ctl->abort, 1);
+                }
+                if (w > 0)
+                    fill_tile_params(sp, reps[tile.r], tile, s_t0 + (uint32_t)s,
+                                     s_cur0 ^ (s & 1), false, flag);
+                s_go = w > 0;
+            }
         }
         __syncthreads();
         if (!s_go) break;
@@ -209,12 +235,12 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
         }
 #undef ENS_STRIP
         if (threadIdx.x == 0) s_k[it ^ 1] = knext;
-        // read before the barrier: thread 0 overwrites s_tile after it
-        const int r = s_tile.r;
+        // read before the barrier: thread 0 overwrites s_ti after it
+        const int ti = s_ti;
         __syncthreads();   // the tile's stores are done, and sp may be refilled
         if (threadIdx.x == kPoster) {
             __threadfence();
-            atomicAdd(&done[r], 1u);
+            atomicAdd(&tdone[ti], 1u);   // one step more of tile ti is done
         }
     }
     // the last CTA to finish resets the barriers and advances the clock
@@ -224,7 +250,7 @@ ens_persist_kernel(const EnsRep *__restrict__ reps, const EnsTile *__restrict__ 
     }
     __syncthreads();
     if (s_last) {
-        for (int r = threadIdx.x; r < nrep; r += blockDim.x) done[r] = 0;
+        for (int i = threadIdx.x; i < ntiles; i += blockDim.x) tdone[i] = 0;
         if (threadIdx.x == 0) {
             ctl->finished = 0;
             ctl->abort = 0;
@@ -316,8 +342,8 @@ struct lb_ens {
     cudaGraphExec_t graph_plain = nullptr;     // kGraphSteps steps, no sampling
     cudaGraphExec_t graph_window = nullptr;    // sk_every steps, sampling at the last
     int launch_mode = LB_ENS_PER_STEP;         // LB_ENS_PER_STEP or LB_ENS_PERSISTENT
-    int *d_rep_ntiles = nullptr;               // tiles per replica (persistent barriers)
-    uint32_t *d_done = nullptr;                // per-replica completion counters
+    int *d_nbr_off = nullptr, *d_nbr = nullptr;   // tiles each tile pulls from (CSR)
+    uint32_t *d_tdone = nullptr;               // steps each tile has finished (persistent)
     EnsCtl *d_ctl = nullptr;
     int persist_grid = 0;                      // co-resident CTAs of the persistent kernel
     int kernel_mode = LB_KERNEL_AUTO;          // LB_KERNEL_PLAIN or _OVERLAP (strip layout)
@@ -474,28 +500,62 @@ int build_tiles(lb_ens *e) {
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return (long)e->reps[a].nx * e->reps[a].ny > (long)e->reps[b].nx * e->reps[b].ny;
     });
-    std::vector<int> per_rep(e->nrep, 0);
+    // Tiles of a replica form a grid of row strips x column strips.  A tile
+    // pulls rows y0 - H - 1 .. y1 + H and columns x0 - H - 1 .. x1 + H
+    // (periodic); the tiles holding those cells are its dependencies in the
+    // persistent launch (CSR: nbr_off, nbr).
+    const int H = e->stencil == 4 ? 1 : 2;
+    std::vector<int> nbr_off(1, 0), nbr;
     for (int r : order) {
         if (e->is_res[r]) continue;   // advanced by the resident kernel
         const int nx = e->reps[r].nx, ny = e->reps[r].ny;
         const int h = std::min(e->strip_h, ny);
-        const int cols = e->ov ? kStepTX - 2 * (e->stencil == 4 ? 1 : 2) : kStepTX;
-        for (int y0 = 0; y0 < ny; y0 += h)
-            for (int x0 = 0; x0 < nx; x0 += cols) {
+        const int cols = e->ov ? kStepTX - 2 * H : kStepTX;
+        const int nry = (ny + h - 1) / h, ncx = (nx + cols - 1) / cols;
+        const int base = (int)tiles.size();
+        // strips whose cells the tiles of one row (column) strip read
+        auto strips = [](int a0, int a1, int n, int w, int halo) {
+            std::vector<int> out;
+            for (int a = a0 - halo - 1; a <= a1 - 1 + halo + 1; ++a) {
+                const int idx = (((a % n) + n) % n) / w;
+                if (std::find(out.begin(), out.end(), idx) == out.end()) out.push_back(idx);
+            }
+            return out;
+        };
+        std::vector<std::vector<int>> rset(nry), cset(ncx);
+        for (int ry = 0; ry < nry; ++ry) rset[ry] = strips(ry * h, std::min(ry * h + h, ny), ny, h, H);
+        for (int cx = 0; cx < ncx; ++cx)
+            cset[cx] = strips(cx * cols, std::min(cx * cols + cols, nx), nx, cols, H);
+        for (int ry = 0; ry < nry; ++ry)
+            for (int cx = 0; cx < ncx; ++cx) {
+                const int y0 = ry * h, x0 = cx * cols;
                 tiles.push_back({r, x0, y0, std::min(y0 + h, ny)});
-                per_rep[r] += 1;
+                for (int a : rset[ry])
+                    for (int b : cset[cx]) nbr.push_back(base + a * ncx + b);
+                nbr_off.push_back((int)nbr.size());
             }
     }
-    if (e->d_tiles) cudaFree(e->d_tiles);
+    cudaFree(e->d_tiles);
+    cudaFree(e->d_nbr_off);
+    cudaFree(e->d_nbr);
+    cudaFree(e->d_tdone);
     e->d_tiles = nullptr;
+    e->d_nbr_off = e->d_nbr = nullptr;
+    e->d_tdone = nullptr;
+    e->ntiles = 0;
     if (!tiles.empty()) {
         ENS_CHECK(cudaMalloc(&e->d_tiles, tiles.size() * sizeof(EnsTile)));
         ENS_CHECK(cudaMemcpy(e->d_tiles, tiles.data(), tiles.size() * sizeof(EnsTile),
                              cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaMalloc(&e->d_nbr_off, nbr_off.size() * sizeof(int)));
+        ENS_CHECK(cudaMemcpy(e->d_nbr_off, nbr_off.data(), nbr_off.size() * sizeof(int),
+                             cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaMalloc(&e->d_nbr, nbr.size() * sizeof(int)));
+        ENS_CHECK(cudaMemcpy(e->d_nbr, nbr.data(), nbr.size() * sizeof(int),
+                             cudaMemcpyHostToDevice));
+        ENS_CHECK(cudaMalloc(&e->d_tdone, tiles.size() * sizeof(uint32_t)));
+        ENS_CHECK(cudaMemset(e->d_tdone, 0, tiles.size() * sizeof(uint32_t)));
     }
-    if (!e->d_rep_ntiles) ENS_CHECK(cudaMalloc(&e->d_rep_ntiles, e->nrep * sizeof(int)));
-    ENS_CHECK(cudaMemcpy(e->d_rep_ntiles, per_rep.data(), e->nrep * sizeof(int),
-                         cudaMemcpyHostToDevice));
     e->ntiles = (int)tiles.size();
     drop_graphs(e);
     return LB_OK;
@@ -503,8 +563,8 @@ int build_tiles(lb_ens *e) {
 
 template <int ORDER, bool OV, int UM>
 cudaError_t launch_persist_t(lb_ens *e, int nsteps) {
-    void *args[] = {&e->d_reps, &e->d_tiles, &e->ntiles, &e->d_rep_ntiles, &e->d_done,
-                    &e->nrep,   &e->d_ctl,   &e->d_clk,  &e->d_flag,       &e->keys,
+    void *args[] = {&e->d_reps,  &e->d_tiles, &e->ntiles, &e->d_nbr_off, &e->d_nbr,
+                    &e->d_tdone, &e->d_ctl,   &e->d_clk,  &e->d_flag,    &e->keys,
                     &nsteps};
     const int grid = std::min(e->persist_grid, e->ntiles);
     return cudaLaunchCooperativeKernel((const void *)ens_persist_kernel<ORDER, OV, UM>,
@@ -666,8 +726,9 @@ void free_ens(lb_ens *e) {
     cudaFree(e->d_io);
     cudaFree(e->d_partials);
     cudaFree(e->d_out);
-    cudaFree(e->d_rep_ntiles);
-    cudaFree(e->d_done);
+    cudaFree(e->d_nbr_off);
+    cudaFree(e->d_nbr);
+    cudaFree(e->d_tdone);
     cudaFree(e->d_ctl);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
 }
@@ -746,8 +807,6 @@ int lb_ens_create(lb_ens **out, const lb_replica *reps, int nrep, int psi_kind, 
     if (err == cudaSuccess) err = cudaMalloc(&e->d_partials, 3 * (size_t)e->nred * sizeof(double));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_out, 4 * sizeof(double));
     if (err == cudaSuccess) err = cudaMemset(e->d_flag, 0, sizeof(int));
-    if (err == cudaSuccess) err = cudaMalloc(&e->d_done, nrep * sizeof(uint32_t));
-    if (err == cudaSuccess) err = cudaMemset(e->d_done, 0, nrep * sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl, sizeof(EnsCtl));
     if (err == cudaSuccess) {
         const EnsCtl c0 = {0u, 0, (unsigned long long)kEnsWaitNs, 0u};

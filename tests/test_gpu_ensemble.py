@@ -265,3 +265,31 @@ def test_resident_auto_policy():
     e.autotune(3)          # nothing tiled: the call keeps the strip height
     e.step(40)
     e.sync()
+
+
+@pytest.mark.parametrize("stencil", [4, 8])
+@pytest.mark.parametrize("strip", [1, 3, 8])
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_persistent_tile_dependencies(stencil, strip, kernel):
+    """The persistent launch lets a tile start a step as soon as the tiles it
+    pulls from (its neighbours within the stencil's reach, wrapped) finished
+    the previous one.  Thin row strips (a tile's reach spans several), a
+    ragged last column strip and one large replica with many tiles per step:
+    the per-step bits."""
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.ensemble import Ensemble
+    reps = [(512, 256, -4.4, 1.0, 1e-5, LN2), (132, 64, -4.0, 1.0, 1e-5, 0.7),
+            (32, 16, -4.6, 0.9, 1e-5, 0.68)]
+    a = Ensemble(reps, stencil=stencil, seed=41)
+    b = Ensemble(reps, stencil=stencil, seed=41)
+    for e in (a, b):
+        e.set_resident(abi.LB_ENS_RESIDENT_OFF)
+        e.set_kernel(kernel)
+        e.set_strip_height(strip)
+        e.init(0.01)
+    a.set_launch(abi.LB_ENS_PERSISTENT)
+    a.step(70)
+    b.step(70)
+    a.sync()
+    for r in range(len(reps)):
+        assert np.array_equal(a.populations(r), b.populations(r)), r
