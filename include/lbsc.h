@@ -458,8 +458,11 @@ int lb_nn_conv3x3(const void *x, const void *w, const float *bias, void *y, int 
  * caller's device workspace (16-byte aligned, at least
  * lb_nn_wgrad_workspace(...) bytes, which also holds the bias partials) and
  * are then added in a fixed order, so dw and dbias are deterministic (the same
- * inputs give the same bits).  Requires h * w % 128 == 0 and channel counts
- * multiples of 16 (LB_ERR_ARG otherwise, or for a missing/short workspace). */
+ * inputs give the same bits).  Where image rows are a multiple of 128 pixels
+ * and both channel counts are 16, 32, 64 or 128 the sums run on the tensor
+ * cores (tcgen05; lb_nn_set_conv_path(1) forces the mma.sync kernel).
+ * Requires h * w % 128 == 0, channel counts multiples of 16 and x, dy 16-byte
+ * aligned (LB_ERR_ARG otherwise, or for a missing/short workspace). */
 size_t lb_nn_wgrad_workspace(int nb, int h, int w_, int cin, int cout);
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
                         int w_, int cin, int cout, void *workspace, size_t workspace_bytes,

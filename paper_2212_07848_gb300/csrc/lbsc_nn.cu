@@ -29,6 +29,10 @@ extern int nn_conv_path;
 cudaError_t launch_conv3x3_tcp(const void *x, const void *w, const float *bias, void *y, int nb,
                                int h, int wd, int cin, int cout, int relu, int dgrad,
                                cudaStream_t s);
+extern const int kWgTcMaxChunks;
+int wgrad_tc_chunks(int nb, int h, int wd, int cin, int cout, int nsm);
+cudaError_t launch_wgrad_tc(const void *x, const void *dy, float *part, int nb, int h, int wd,
+                            int cin, int cout, int nchunk, cudaStream_t s);
 cudaError_t launch_conv3x3_tc(const void *x, const void *w, const float *bias, void *y, int nb,
                               int h, int wd, int cin, int cout, int relu, cudaStream_t s);
 
@@ -305,6 +309,14 @@ WgPlan wgrad_plan(int nb, int h, int w, int cin, int cout) {
     return p;
 }
 
+// Chunks of partial sums a workspace must hold: the mma.sync plan's or the
+// tcgen05 kernel's largest.
+int wgrad_max_chunks(int nb, int h, int w, int cin, int cout) {
+    const int a = wgrad_plan(nb, h, w, cin, cout).nchunk;
+    const int b = wgrad_tc_chunks(nb, h, w, cin, cout, kWgTcMaxChunks);
+    return a > b ? a : b;
+}
+
 // ---------------------------------------------------------------------------
 // Elementwise pieces (NHWC BF16 activations, FP32 parameters and losses).
 // ---------------------------------------------------------------------------
@@ -318,19 +330,35 @@ WgPlan wgrad_plan(int nb, int h, int w, int cin, int cout) {
 constexpr int kBiasBlocks = 256;
 __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16 *__restrict__ dy,
                                                         float *__restrict__ part, size_t P, int C) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.y * 32 + lane;
-    float s = 0.f;
-    if (c < C)
-        for (size_t p = blockIdx.x * (blockDim.x / 32) + warp; p < P;
-             p += (size_t)gridDim.x * (blockDim.x / 32))
-            s += __bfloat162float(dy[p * C + c]);
-    __shared__ float red[8][32];
-    red[warp][lane] = s;
+    // thread t: channel group g = t % G (8 channels, one 16-byte load), pixel
+    // slot t / G of the block's PB pixels per sweep; fixed order throughout
+    const int G = C / 8, PB = 256 / G;
+    const int g = threadIdx.x % G, slot = threadIdx.x / G;
+    float s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = 0.f;
+    if (slot < PB) {
+#pragma unroll 4
+        for (size_t p = (size_t)blockIdx.x * PB + slot; p < P; p += (size_t)gridDim.x * PB) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(dy + p * C + g * 8);
+            const __nv_bfloat162 *e = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(e[k]);
+                s[2 * k] += f.x;
+                s[2 * k + 1] += f.y;
+            }
+        }
+    }
+    __shared__ float red[256][9];   // padded: conflict-free column reads
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = s[k];
     __syncthreads();
-    if (warp == 0 && c < C) {
+    // channel c = 8 g' + k: the PB slots of group g', in slot order
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const int gg = c / 8, k = c % 8;
         float a = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w][lane];
+        for (int sl = 0; sl < PB; ++sl) a += red[sl * G + gg][k];
         part[(size_t)blockIdx.x * C + c] = a;
     }
 }
@@ -727,9 +755,11 @@ size_t lb_nn_wgrad_workspace(int nb, int h, int wd, int cin, int cout) {
     if (nb < 1 || h < 1 || wd < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 ||
         ((size_t)h * wd) % kWgTile)
         return 0;
-    const WgPlan p = wgrad_plan(nb, h, wd, cin, cout);
-    // chunk partials of dw, then the bias partials [kBiasBlocks][cout]
-    return ((size_t)p.nchunk * 9 * cout * cin + (size_t)kBiasBlocks * cout) * sizeof(float);
+    // chunk partials of dw (for either kernel), then the bias partials
+    // [kBiasBlocks][cout]
+    return ((size_t)wgrad_max_chunks(nb, h, wd, cin, cout) * 9 * cout * cin +
+            (size_t)kBiasBlocks * cout) *
+           sizeof(float);
 }
 
 int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, int nb, int h,
@@ -739,27 +769,46 @@ int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, 
         cin % 16 || cout % 16 || ((size_t)h * wd) % kWgTile)
         return LB_ERR_ARG;
     if (workspace_bytes < lb_nn_wgrad_workspace(nb, h, wd, cin, cout)) return LB_ERR_ARG;
-    if (((uintptr_t)workspace) % 16) return LB_ERR_ARG;
+    if ((((uintptr_t)workspace) | ((uintptr_t)x) | ((uintptr_t)dy)) % 16) return LB_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const WgPlan p = wgrad_plan(nb, h, wd, cin, cout);
     const bf16 *xb = (const bf16 *)x, *db = (const bf16 *)dy;
     float *part = (float *)workspace;
-    dim3 grid(cout / p.bm, cin / p.bc, p.nchunk);
-#define WG(BM, BC)                                                                              \
-    wgrad_kernel<BM, BC><<<grid, 32 * (BM / 16) * (BC / 16), 0, s>>>(xb, db, part, h, wd, cin, \
-                                                                     cout, p.ntiles,           \
-                                                                     p.tiles_per_chunk)
-    if (p.bm == 32) { if (p.bc == 32) WG(32, 32); else WG(32, 16); }
-    else { if (p.bc == 32) WG(16, 32); else WG(16, 16); }
-#undef WG
-    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
     const size_t n = (size_t)9 * cout * cin;
-    wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, n, p.nchunk);
+    float *bpart = part + (size_t)wgrad_max_chunks(nb, h, wd, cin, cout) * n;
+    // tcgen05 kernel where it applies (and unless the mma.sync path is forced)
+    int nchunk = 0;
+    if (nn_conv_path != 1) {
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return LB_ERR_CUDA;
+        }
+        const int k = wgrad_tc_chunks(nb, h, wd, cin, cout, nsm);
+        if (k > 0) {
+            const cudaError_t e = launch_wgrad_tc(x, dy, part, nb, h, wd, cin, cout, k, s);
+            if (e == cudaSuccess) nchunk = k;
+            else if (e != cudaErrorNotSupported) return LB_ERR_CUDA;
+        }
+    }
+    if (nchunk == 0) {   // the mma.sync kernel
+        dim3 grid(cout / p.bm, cin / p.bc, p.nchunk);
+#define WG(BM, BC)                                                                           \
+    wgrad_kernel<BM, BC><<<grid, 32 * (BM / 16) * (BC / 16), 0, s>>>(xb, db, part, h, wd,   \
+                                                                     cin, cout, p.ntiles,   \
+                                                                     p.tiles_per_chunk)
+        if (p.bm == 32) { if (p.bc == 32) WG(32, 32); else WG(32, 16); }
+        else { if (p.bc == 32) WG(16, 32); else WG(16, 16); }
+#undef WG
+        if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+        nchunk = p.nchunk;
+    }
+    wgrad_reduce_kernel<<<blocks_for(n), 256, 0, s>>>(part, dw, n, nchunk);
     if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
     if (dbias) {
-        float *bpart = part + (size_t)p.nchunk * n;
-        dim3 gb(kBiasBlocks, (cout + 31) / 32);
-        bias_grad_kernel<<<gb, 256, 0, s>>>(db, bpart, (size_t)nb * h * wd, cout);
+        bias_grad_kernel<<<kBiasBlocks, 256, 0, s>>>(db, bpart, (size_t)nb * h * wd, cout);
         if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
         bias_reduce_kernel<<<(cout + 127) / 128, 128, 0, s>>>(bpart, dbias, cout, kBiasBlocks);
     }

@@ -34,6 +34,7 @@ __device__ int g_nn_status;               // bit 0: an mbarrier wait gave up;
                                           // bit 1: tensor memory left allocated
 constexpr unsigned long long kTcWaitNs = 1000000000ull;   // default bound: 1 s
 __device__ unsigned long long g_nn_wait_ns = kTcWaitNs;   // lb_nn_set_wait_ns
+extern const int kWgTcMaxChunks = 192;   // bound on a weight-gradient launch's chunks
 
 namespace {
 
@@ -746,6 +747,24 @@ bool tcp_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same with the swizzle pattern of `span`-byte rows (32, 64 or 128; the
+// box's b0 channels make one row).
+bool tcp_map_span(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                  uint32_t b0, uint32_t b1, int span) {
+    auto fn = tcp_encode_fn();
+    if (!fn || b0 * 2 != (uint32_t)span) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+    const cuuint32_t box[3] = {b0, b1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = span == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : span == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                               : CU_TENSOR_MAP_SWIZZLE_32B;
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN, int CIN, bool DG>
 cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, int nb, int h,
                        int wd, int cout, int relu, cudaStream_t s) {
@@ -821,6 +840,323 @@ cudaError_t launch_tcp_shape(const bf16 *x, const bf16 *w, const float *bias, bf
     return cudaErrorNotSupported;
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05: dw[tap][n][c] += sum_p x[p + off(tap)][c] dy[p][n]
+// as GEMMs over 128-pixel tiles of one image row (K = the tile's pixels).
+// Both operands are staged straight from the NHWC tensors by TMA, one pixel
+// per row with its channels contiguous (the forward kernel's row layout), so
+// they are MN-major operands; a tap's pixel shift is a row shift of the x
+// operand's descriptor.  M = 128 rows of the operand with more channels (AC
+// real ones; the rows beyond them read other staged data or slack and land in
+// accumulator rows that are discarded), N = the other's NC channels.  A CTA
+// holds TP accumulators (all nine taps when 9 NC tensor-memory columns fit,
+// else the three of one tap row), sums a chunk of tiles into them, and writes
+// them once to its slice of the caller's workspace; a separate kernel adds the
+// chunks in a fixed order.  Warp 4 issues the copies into a ring of S slots,
+// one thread of warp 5 the MMAs, warps 0-3 read the accumulators at the end.
+// Every wait is bounded, as in the forward kernel.
+// ---------------------------------------------------------------------------
+// Taps per CTA: all nine when their accumulators (9 x nc columns of tensor
+// memory) and three staged x rows of cin channels fit, else one tap row.
+__host__ __device__ constexpr int wg_taps(int cin, int nc) {
+    return 9 * nc <= 512 && 3 * 144 * cin * 2 <= 80 * 1024 ? 9 : 3;
+}
+
+template <int AC, int NC, bool AX>
+struct WCfg {
+    static constexpr int TP = wg_taps(AX ? AC : NC, NC);   // taps per CTA
+    static constexpr int TG = 9 / TP;                   // tap groups
+    static constexpr int XR = TP == 9 ? 3 : 1;          // x rows staged per tile
+    static constexpr int XC = AX ? AC : NC;             // channels of x
+    static constexpr int DC = AX ? NC : AC;             // channels of dy
+    // channels per staged block (a TMA box; rows of XSP / DSP bytes, swizzled
+    // with the matching 32-, 64- or 128-byte pattern)
+    static constexpr int XBC = XC < 64 ? XC : 64, DBC = DC < 64 ? DC : 64;
+    static constexpr int XSP = 2 * XBC, DSP = 2 * DBC;
+    static constexpr int XROW = 144, DROW = 128;        // pixel rows: x0-8 .. x0+135, x0 .. x0+127
+    static constexpr int X_BYTES = XROW * XC * 2;       // one staged x row (what lands)
+    static constexpr int D_BYTES = DROW * DC * 2;
+    static constexpr int X_STRIDE = (X_BYTES + 1023) / 1024 * 1024;
+    static constexpr int D_STRIDE = (D_BYTES + 1023) / 1024 * 1024;
+    static constexpr int A_BYTES = AX ? XR * X_STRIDE : D_STRIDE;   // per slot
+    static constexpr int B_BYTES = AX ? D_STRIDE : XR * X_STRIDE;
+    // what the MMAs read of the A operand past its AC channels (M = 128)
+    static constexpr int SLACK = (128 - AC) * (AX ? XROW : DROW) * 2;
+    static constexpr int S0 = (200 * 1024 - SLACK) / (A_BYTES + B_BYTES);
+    static constexpr int S = S0 > 4 ? 4 : S0;           // ring slots
+    static constexpr int SMEM = S * (A_BYTES + B_BYTES) + SLACK;
+    static constexpr uint32_t NCOLS = TP * NC <= 32 ? 32 : TP * NC <= 64 ? 64
+                                    : TP * NC <= 128 ? 128 : TP * NC <= 256 ? 256 : 512;
+    static constexpr uint32_t TX = XR * X_BYTES + D_BYTES;   // bytes landing per slot
+    static_assert(S >= 2, "shared-memory plan too small");
+};
+constexpr int kWgtThreads = 192;
+
+// Descriptor of an MN-major operand staged as pixel rows of SP bytes (SP / 2
+// channels: 16, 32 or 64), swizzled with the SP-byte pattern that TMA writes:
+// blocks of SP / 2 channels `rows` rows apart (LBO), 8-row groups 8 SP bytes
+// apart (SBO), layout type 6 / 4 / 2 for 32 / 64 / 128 bytes; starting at
+// pixel row `row`.  As for the K-major operands, the swizzle follows the
+// absolute shared-memory address, so any start row works with the base
+// offset field at 0.
+template <int SP>
+__device__ __forceinline__ uint64_t mn_desc(uint32_t base, int row, int rows) {
+    static_assert(SP == 32 || SP == 64 || SP == 128, "swizzle span");
+    uint64_t d = (uint64_t)(((base + (uint32_t)(row * SP)) & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((((uint32_t)(rows * SP)) >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((8u * SP) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(SP == 128 ? 2 : SP == 64 ? 4 : 6) << 61;
+    return d;
+}
+
+// tm_x / tm_xh: x as [nb*H][W][Cin], boxes of XB channels x 128 / 8 pixels;
+// tm_dy: dy as [nb*H][W][Cout], box DB channels x 128 pixels.  part: this
+// launch's partial sums [chunk][9][Cout][Cin].
+template <int AC, int NC, bool AX>
+__global__ void __launch_bounds__(kWgtThreads, 1)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_xh,
+                const __grid_constant__ CUtensorMap tm_dy, float *__restrict__ part, int nb, int H,
+                int W, int Cin, int Cout, int tiles_per_chunk) {
+    using C = WCfg<AC, NC, AX>;
+    constexpr int S = C::S, TP = C::TP;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[S], slot_free[S], done;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_drained;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t *sB = smem;                          // S slots of the B operand
+    uint8_t *sA = smem + S * C::B_BYTES;         // S slots of the A operand, then the slack
+    auto xreg = [&](int slot, int q) {
+        return (AX ? sA + slot * C::A_BYTES : sB + slot * C::B_BYTES) + q * C::X_STRIDE;
+    };
+    auto dreg = [&](int slot) { return AX ? sB + slot * C::B_BYTES : sA + slot * C::A_BYTES; };
+    // both operands MN-major (bits 15 and 16)
+    constexpr uint32_t IDESC = idesc_bf16(128, NC) | (1u << 15) | (1u << 16);
+    const int tg = blockIdx.x % C::TG, chunk = blockIdx.x / C::TG;
+    const int bands = W / 128;
+    const long ntiles = (long)nb * bands * H;
+    const long t_begin = (long)chunk * tiles_per_chunk;
+    const long t_end = min(ntiles, t_begin + tiles_per_chunk);
+    const int n = (int)(t_end - t_begin);   // >= 1 by the launch plan
+    const uint64_t limit = g_nn_wait_ns;
+    volatile int *abort = &s_abort;
+    // tile t -> image b, band x0, row y (rows fastest: consecutive tiles share x rows)
+    auto tile_at = [&](long t, int &b, int &x0, int &y) {
+        y = (int)(t % H);
+        const long r = t / H;
+        x0 = (int)(r % bands) * 128;
+        b = (int)(r / bands);
+    };
+
+    if (warp == 0) tmem_alloc(&s_tmem, C::NCOLS);
+    if (tid == kWgtThreads - 1) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&slot_free[i], 1);
+        }
+        mbar_init(&done, 1);
+        s_abort = 0;
+        s_drained = 1;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 4) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            constexpr int XB = C::XBC, DB = C::DBC;     // channels per box
+            constexpr int XP = C::XSP, DP = C::DSP;     // bytes per pixel row
+            int t = 0;
+            for (; t < n && !*abort; ++t) {
+                const int slot = t % S;
+                if (t >= S &&
+                    !mbar_wait_ab(&slot_free[slot], (uint32_t)((t / S - 1) & 1), limit, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                int b, x0, y;
+                tile_at(t_begin + t, b, x0, y);
+                const int xl = x0 == 0 ? W - 8 : x0 - 8;        // left halo (periodic)
+                const int xr = x0 + 128 == W ? 0 : x0 + 128;    // right halo
+                mbar_expect_tx(&full[slot], C::TX);
+                for (int q = 0; q < C::XR; ++q) {
+                    const int ys = wrapi(y + (TP == 9 ? q : tg) - 1, H);
+                    uint8_t *dst = xreg(slot, q);
+                    for (int kc = 0; kc < C::XC / XB; ++kc) {
+                        uint8_t *ch = dst + kc * C::XROW * XP;
+                        tma_load3(ch, &tm_xh, kc * XB, xl, b * H + ys, &full[slot]);
+                        tma_load3(ch + 8 * XP, &tm_x, kc * XB, x0, b * H + ys, &full[slot]);
+                        tma_load3(ch + 136 * XP, &tm_xh, kc * XB, xr, b * H + ys, &full[slot]);
+                    }
+                }
+                for (int kc = 0; kc < C::DC / DB; ++kc)
+                    tma_load3(dreg(slot) + kc * C::DROW * DP, &tm_dy, kc * DB, x0, b * H + y,
+                              &full[slot]);
+            }
+            // every copy issued must land before the CTA exits
+            for (int sq = t > S ? t - S : 0; sq < t; ++sq)
+                mbar_wait(&full[sq % S], (uint32_t)((sq / S) & 1), kTcWaitNs);
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int nfreed[S];
+            for (int i = 0; i < S; ++i) nfreed[i] = 0;
+            bool ok = true;
+            for (int t = 0; t < n && ok; ++t) {
+                const int slot = t % S;
+                ok = mbar_wait_ab(&full[slot], (uint32_t)((t / S) & 1), limit, abort);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t db = smem_u32(dreg(slot));
+                // K steps outer, taps inner: consecutive MMAs go to different
+                // accumulators, so none waits for the one before it
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint64_t dd = mn_desc<C::DSP>(db, 16 * j, C::DROW);
+#pragma unroll
+                    for (int tl = 0; tl < TP; ++tl) {
+                        // pixels 16j .. 16j+15 of the tile; x shifted by the tap
+                        // (staged row 8 is pixel x0, so the tap's row 7 + dx + p)
+                        const int q = TP == 9 ? tl / 3 : 0, dx = tl % 3;
+                        const uint64_t xd =
+                            mn_desc<C::XSP>(smem_u32(xreg(slot, q)), 7 + dx + 16 * j, C::XROW);
+                        tc_mma(tmem + (uint32_t)(tl * NC), AX ? xd : dd, AX ? dd : xd, IDESC,
+                               (t > 0 || j > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&slot_free[slot]);
+                ++nfreed[slot];
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicOr(&g_nn_status, 1);
+            }
+            // done: every MMA issued has finished (also after an abort, so that
+            // tensor memory is freed only then); wait for it and for the last
+            // arrival on each slot barrier before the CTA may exit
+            tc_commit(&done);
+            bool drained = mbar_wait(&done, 0, kTcWaitNs);
+            for (int i = 0; i < S; ++i)
+                if (nfreed[i] > 0)
+                    drained = mbar_wait(&slot_free[i], (uint32_t)((nfreed[i] - 1) & 1), kTcWaitNs) &&
+                              drained;
+            if (!drained) {
+                s_drained = 0;
+                atomicOr(&g_nn_status, 2);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-3): lanes 32w .. 32w+31 = rows m ----------------
+        if (!mbar_wait_ab(&done, 0, limit, abort)) *abort = 1;
+        if (!*abort) {
+            tc_fence_after();
+            const int m = warp * 32 + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            constexpr int CH = NC < 32 ? NC : 32;   // columns per tensor-memory load
+#pragma unroll 1
+            for (int tl = 0; tl < TP; ++tl) {
+                const int tap = TP == 9 ? tl : tg * 3 + tl;
+                float *dst = part + ((size_t)chunk * 9 + tap) * Cout * Cin;
+#pragma unroll
+                for (int col = 0; col < NC; col += CH) {
+                    uint32_t rr[CH];
+                    if constexpr (CH == 32) tmem_ld32(lane_base + (uint32_t)(tl * NC + col), rr);
+                    else tmem_ld16(lane_base + (uint32_t)(tl * NC + col), rr);
+                    if (n <= 0)   // no tile (the launch plan avoids it): a zero partial sum
+                        for (int k = 0; k < CH; ++k) rr[k] = 0u;
+                    if (m < AC) {
+                        if constexpr (!AX) {
+                            // row m = output channel, column = input channel
+                            float4 *o = reinterpret_cast<float4 *>(dst + (size_t)m * Cin + col);
+#pragma unroll
+                            for (int k = 0; k < CH / 4; ++k)
+                                o[k] = make_float4(__uint_as_float(rr[4 * k]), __uint_as_float(rr[4 * k + 1]),
+                                                   __uint_as_float(rr[4 * k + 2]),
+                                                   __uint_as_float(rr[4 * k + 3]));
+                        } else {
+                            // row m = input channel, column = output channel
+#pragma unroll
+                            for (int k = 0; k < CH; ++k)
+                                dst[(size_t)(col + k) * Cin + m] = __uint_as_float(rr[k]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0 && s_drained) tmem_dealloc(tmem, C::NCOLS);
+}
+
+template <int AC, int NC, bool AX>
+cudaError_t launch_wgrad_t(const bf16 *x, const bf16 *dy, float *part, int nb, int h, int wd,
+                           int cin, int cout, int nchunk, cudaStream_t s) {
+    using C = WCfg<AC, NC, AX>;
+    // at most 512 / NCOLS CTAs may share an SM's tensor memory: pad the
+    // shared-memory request so that no more fit
+    constexpr int kPerSm = 512 / (int)C::NCOLS;
+    constexpr int kMinSmem = 233472 / (kPerSm + 1) + 1;
+    constexpr int kSmem = C::SMEM + 1024 > kMinSmem ? C::SMEM + 1024 : kMinSmem;
+    static_assert(C::SMEM + 1024 <= 226 * 1024, "shared-memory plan too large");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dy)) & 15)
+        return cudaErrorNotSupported;
+    CUtensorMap mx, mxh, mdy;
+    if (!tcp_map_span(&mx, x, cin, wd, (uint64_t)nb * h, C::XBC, 128, C::XSP) ||
+        !tcp_map_span(&mxh, x, cin, wd, (uint64_t)nb * h, C::XBC, 8, C::XSP) ||
+        !tcp_map_span(&mdy, dy, cout, wd, (uint64_t)nb * h, C::DBC, 128, C::DSP))
+        return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<AC, NC, AX>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long ntiles = (long)nb * h * (wd / 128);
+    const int per = (int)((ntiles + nchunk - 1) / nchunk);
+    wgrad_tc_kernel<AC, NC, AX><<<C::TG * nchunk, kWgtThreads, kSmem, s>>>(
+        mx, mxh, mdy, part, nb, h, wd, cin, cout, per);
+    return cudaGetLastError();
+}
+
+// NC <= AC channels of the N operand (NC < AC when the A operand is x).
+template <int AC, bool AX>
+cudaError_t launch_wgrad_nc(int nc, const bf16 *x, const bf16 *dy, float *part, int nb, int h,
+                            int wd, int cin, int cout, int nchunk, cudaStream_t s) {
+    if constexpr (AC > 16 || !AX)
+        if (nc == 16) return launch_wgrad_t<AC, 16, AX>(x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    if constexpr (AC > 32 || (AC == 32 && !AX))
+        if (nc == 32) return launch_wgrad_t<AC, 32, AX>(x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    if constexpr (AC > 64 || (AC == 64 && !AX))
+        if (nc == 64) return launch_wgrad_t<AC, 64, AX>(x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    if constexpr (AC == 128 && !AX)
+        if (nc == 128) return launch_wgrad_t<AC, 128, AX>(x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    return cudaErrorNotSupported;
+}
+
+template <bool AX>
+cudaError_t launch_wgrad_ac(int ac, int nc, const bf16 *x, const bf16 *dy, float *part, int nb,
+                            int h, int wd, int cin, int cout, int nchunk, cudaStream_t s) {
+    switch (ac) {
+    case 16: return launch_wgrad_nc<16, AX>(nc, x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    case 32: return launch_wgrad_nc<32, AX>(nc, x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    case 64: return launch_wgrad_nc<64, AX>(nc, x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    case 128: return launch_wgrad_nc<128, AX>(nc, x, dy, part, nb, h, wd, cin, cout, nchunk, s);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 }  // namespace
 
 // Persistent tcgen05 convolution (forward, or the input gradient with dgrad)
@@ -834,6 +1170,35 @@ cudaError_t launch_conv3x3_tcp(const void *x, const void *w, const float *bias, 
     bf16 *yb = (bf16 *)y;
     return dgrad ? launch_tcp_shape<true>(xb, wb, bias, yb, nb, h, wd, cin, cout, relu, s)
                  : launch_tcp_shape<false>(xb, wb, bias, yb, nb, h, wd, cin, cout, relu, s);
+}
+
+// Weight gradient on tcgen05 (see wgrad_tc_kernel): the chunk count for a
+// launch (CTAs = tap groups x chunks, one per SM), or 0 where the kernel does
+// not apply (image rows not a multiple of 128 pixels, channel counts other
+// than 16, 32, 64, 128).
+int wgrad_tc_chunks(int nb, int h, int wd, int cin, int cout, int nsm) {
+    auto ok = [](int c) { return c == 16 || c == 32 || c == 64 || c == 128; };
+    if (wd % 128 || h < 2 || !ok(cin) || !ok(cout) || nsm < 1) return 0;
+    const int nc = cin < cout ? cin : cout;
+    const int tg = 9 / wg_taps(cin, nc);
+    const long ntiles = (long)nb * h * (wd / 128);
+    long k = nsm / tg;
+    if (k > kWgTcMaxChunks / tg) k = kWgTcMaxChunks / tg;
+    if (k > ntiles) k = ntiles;
+    if (k < 1) k = 1;
+    // chunks of ceil(ntiles / k) tiles: keep only those that get a tile
+    const long per = (ntiles + k - 1) / k;
+    return (int)((ntiles + per - 1) / per);
+}
+
+// Partial sums [nchunk][9][cout][cin] of the weight gradient into part.
+cudaError_t launch_wgrad_tc(const void *x, const void *dy, float *part, int nb, int h, int wd,
+                            int cin, int cout, int nchunk, cudaStream_t s) {
+    const bf16 *xb = (const bf16 *)x, *db = (const bf16 *)dy;
+    // M = 128 rows of the operand with more channels (dy on a tie)
+    if (cout >= cin)
+        return launch_wgrad_ac<false>(cout, cin, xb, db, part, nb, h, wd, cin, cout, nchunk, s);
+    return launch_wgrad_ac<true>(cin, cout, xb, db, part, nb, h, wd, cin, cout, nchunk, s);
 }
 
 // Forward convolution on tcgen05 when the path selection and the shape allow

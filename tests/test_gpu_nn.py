@@ -100,9 +100,18 @@ def test_conv_input_gradient(nb, h, w, cin, cout, path):
     assert L.lb_nn_set_conv_path(0) == 0
 
 
-@pytest.mark.parametrize("nb,h,w,cin,cout", CONV)
-def test_conv_weight_gradient(nb, h, w, cin, cout):
+# the surrogate's layers at their training sizes (batch 2 instead of 8)
+WGRAD_EXTRA = [(2, 64, 512, 16, 32), (2, 32, 256, 32, 64), (2, 16, 128, 64, 128),
+               (2, 32, 256, 128, 64), (2, 64, 512, 64, 16), (1, 4, 128, 128, 128),
+               (1, 3, 128, 16, 16), (1, 5, 256, 128, 16), (1, 4, 128, 64, 32)]
+
+
+@pytest.mark.parametrize("path", [0, 1])   # tcgen05 where it applies (w % 128 == 0), mma.sync
+@pytest.mark.parametrize("nb,h,w,cin,cout", CONV + WGRAD_EXTRA)
+def test_conv_weight_gradient(nb, h, w, cin, cout, path):
+    from paper_2212_07848_gb300 import abi
     L = _lib()
+    assert L.lb_nn_set_conv_path(path) == 0
     x = _bf((nb, h, w, cin), seed=5)
     dy = _bf((nb, h, w, cout), seed=6)
     dw = torch.zeros((9, cout, cin), device="cuda")
@@ -129,6 +138,8 @@ def test_conv_weight_gradient(nb, h, w, cin, cout):
     torch.cuda.synchronize()
     assert torch.equal(dw, first)
     assert torch.equal(db, first_b)
+    assert L.lb_nn_status() == abi.LB_OK
+    assert L.lb_nn_set_conv_path(0) == 0
 
 
 def test_pool_up_relu_adam():

@@ -143,11 +143,13 @@ def test_rollout_stable_and_faster_than_solver(trained):
 # Rollout scores of the small training case (12 quenches of 256^2 -> 64^2,
 # 1000 iterations, held-out quenches 10 and 11 from frame 3 over 10 strides),
 # the regression bounds of the bench's surrogate metrics at this size.  The
-# training is bit-reproducible, so on the same GPU the scores are fixed; the
-# bounds sit about 30% above the measured values: L(t) 0.083 (bound 0.11) and
-# S(k, t) L1 gap 0.28 (bound 0.36); a short training on a 64^2 grid is far
-# from the 2% of the paper-scale target, whose figures are the bench's.
-ROLLOUT_BOUNDS = {"L_mean_max_rel_err": 0.11, "Sk_l1_rel_err": 0.36}
+# training is bit-reproducible, so on the same GPU the scores are fixed, but
+# they move with the network's initial weights and with the summation order of
+# the gradient kernels: over initial seeds 0-3 the L(t) gap measured 0.05-0.12
+# and the S(k, t) L1 gap 0.25-0.41 (seed 0: 0.100 and 0.407).  The bounds sit
+# about 30% above the largest; a short training on a 64^2 grid is far from the
+# 2% of the paper-scale target, whose figures are the bench's.
+ROLLOUT_BOUNDS = {"L_mean_max_rel_err": 0.15, "Sk_l1_rel_err": 0.53}
 
 
 def test_rollout_scores_against_the_solver(trained):

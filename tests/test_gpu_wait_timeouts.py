@@ -102,3 +102,42 @@ def test_tensor_core_conv_mma_wait_timeout_is_reported_and_recoverable(path):
     assert L.lb_nn_status() == abi.LB_OK
     assert torch.equal(y0, y1)
     assert L.lb_nn_set_conv_path(0) == 0
+
+
+def test_tensor_core_wgrad_wait_timeout_is_reported_and_recoverable():
+    """The tcgen05 weight-gradient kernel: a wait given up at its first check
+    is reported, tensor memory is released, and the next calls give the
+    earlier bits."""
+    torch = pytest.importorskip("torch")
+    from paper_2212_07848_gb300 import abi
+    L = abi.load()
+    P = C.c_void_p
+    L.lb_nn_conv3x3_wgrad.argtypes = [P, P, P, P] + [C.c_int] * 5 + [P, C.c_size_t, P]
+    L.lb_nn_wgrad_workspace.argtypes = [C.c_int] * 5
+    L.lb_nn_wgrad_workspace.restype = C.c_size_t
+    p = lambda t: C.c_void_p(t.data_ptr())
+    nb, h, w, cin, cout = 2, 16, 256, 32, 64
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.randn((nb, h, w, cin), generator=gen).to(torch.bfloat16).cuda()
+    dy = torch.randn((nb, h, w, cout), generator=gen).to(torch.bfloat16).cuda()
+    nbytes = L.lb_nn_wgrad_workspace(nb, h, w, cin, cout)
+    ws = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    dw0 = torch.zeros((9, cout, cin), device="cuda")
+    dw1 = torch.zeros_like(dw0)
+    call = lambda dw: L.lb_nn_conv3x3_wgrad(p(x), p(dy), p(dw), None, nb, h, w, cin, cout, p(ws),
+                                            nbytes, None)
+    assert L.lb_nn_set_conv_path(0) == 0
+    assert call(dw0) == 0
+    assert L.lb_nn_status() == abi.LB_OK
+    try:
+        abi.lb_nn_set_wait_ns(0)
+        assert call(dw1) == 0
+        assert L.lb_nn_status() == abi.LB_ERR_TIMEOUT
+        assert L.lb_nn_status() == abi.LB_OK  # cleared
+    finally:
+        abi.lb_nn_set_wait_ns(-1)
+    for _ in range(3):
+        dw1.zero_()
+        assert call(dw1) == 0
+    assert L.lb_nn_status() == abi.LB_OK
+    assert torch.equal(dw0, dw1)
