@@ -327,7 +327,7 @@ int wgrad_max_chunks(int nb, int h, int w, int cin, int cout) {
 // channel group g over its grid-stride share of pixels (each warp a strided
 // subset, then the warps in order) into part[b][c]; bias_reduce_kernel adds
 // the kBiasBlocks partials of each channel in order.
-constexpr int kBiasBlocks = 256;
+constexpr int kBiasBlocks = 1216;   // eight 256-thread blocks per SM
 __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16 *__restrict__ dy,
                                                         float *__restrict__ part, size_t P, int C) {
     // thread t: channel group g = t % G (8 channels, one 16-byte load), pixel
@@ -362,13 +362,22 @@ __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16 *__restrict__
         part[(size_t)blockIdx.x * C + c] = a;
     }
 }
-__global__ void bias_reduce_kernel(const float *__restrict__ part, float *__restrict__ db, int C,
-                                   int nblocks) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+// db[c] += the partials of channel c (block c): thread t adds partials t,
+// t + 256, ... in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(256) bias_reduce_kernel(const float *__restrict__ part,
+                                                          float *__restrict__ db, int C,
+                                                          int nblocks) {
+    const int c = blockIdx.x;
     float a = 0.f;
-    for (int b = 0; b < nblocks; ++b) a += part[(size_t)b * C + c];
-    db[c] += a;
+    for (int b = threadIdx.x; b < nblocks; b += 256) a += part[(size_t)b * C + c];
+    __shared__ float red[256];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] += red[0];
 }
 
 __global__ void relu_mask_kernel(const bf16 *__restrict__ dy, const bf16 *__restrict__ y,
@@ -810,7 +819,7 @@ int lb_nn_conv3x3_wgrad(const void *x, const void *dy, float *dw, float *dbias, 
     if (dbias) {
         bias_grad_kernel<<<kBiasBlocks, 256, 0, s>>>(db, bpart, (size_t)nb * h * wd, cout);
         if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-        bias_reduce_kernel<<<(cout + 127) / 128, 128, 0, s>>>(bpart, dbias, cout, kBiasBlocks);
+        bias_reduce_kernel<<<cout, 256, 0, s>>>(bpart, dbias, cout, kBiasBlocks);
     }
     NN_RET();
 }
