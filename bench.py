@@ -702,7 +702,9 @@ def run_gpu(args, rank, world, local_rank):
                     "d2h_bytes_per_step": dens_np.nbytes + bins.nbytes,
                     "steps": e2e_steps},
             "clocks": clk.summary(),
-            "gpu_launches": args.steps * (LB_PER_STEP + 2 + 2 + 1),
+            # per step: the lattice steps, one device-clock set per captured
+            # 32-step window, the S(k) sample (2), the reduction (2), the bins (1)
+            "gpu_launches": args.steps * (LB_PER_STEP + (LB_PER_STEP - 1) // 32 + 2 + 2 + 1),
         }
         if cb is not None:
             line["cpu_baseline"] = cb

@@ -4,6 +4,7 @@
 // lbsc_sk.cu and lbsc_reduce.cu.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <limits.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -50,6 +51,15 @@ struct lb_ctx {
     TmaMaps maps;                   // tensor maps of df[0], df[1] (FP32 only)
     long long wait_ns = -1;         // staged kernel's mbarrier bound (< 0: default)
     StepArgs base;
+    // captured windows of steps: [starting buffer][0: 32 plain steps, 1: one
+    // S(k) interval ending with its sample]; the step counter of the noise is
+    // read from d_clock, set before each replay
+    uint32_t *d_clock = nullptr;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int graph_len[2][2] = {{0, 0}, {0, 0}};
+    long long graph_ver[2][2] = {{-1, -1}, {-1, -1}};
+    long long ver = 0;              // bumped by every change that a captured window bakes in
+    bool graphs_ok = true;          // false once a capture failed (e.g. the legacy stream)
 };
 
 namespace {
@@ -188,7 +198,17 @@ int select_device(lb_ctx *h) {
     return LB_OK;
 }
 
+void drop_step_graphs(lb_ctx *h) {
+    for (auto &row : h->graph)
+        for (auto &g : row) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 void free_all(lb_ctx *h) {
+    drop_step_graphs(h);
+    cudaFree(h->d_clock);
     cudaFree(h->df[0]);
     cudaFree(h->df[1]);
     cudaFree(h->d_flag);
@@ -267,6 +287,7 @@ int lb_create_ex(lb_ctx **out, const lb_params *p) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->df[b], 9 * h->n * h->esize);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_clock, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, 3 * (size_t)h->nred * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_out, 4096 * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
@@ -314,6 +335,7 @@ int lb_init(lb_ctx *h, double rho0, uint64_t seed, double init_amp) {
     h->t = 0;
     h->cur = 0;
     fill_base(h);
+    ++h->ver;
     LB_CHECK(launch_init(h->p.precision, h->df[0], h->p.nx, h->p.ny, init_amp,
                          h->base.round_keys, h->replica, h->stream));
     if (h->acc) {
@@ -328,6 +350,7 @@ int lb_set_replica(lb_ctx *h, uint32_t replica) {
     if (!h) return LB_ERR_ARG;
     h->replica = replica;
     h->base.replica = replica;
+    ++h->ver;
     return LB_OK;
 }
 
@@ -335,6 +358,7 @@ int lb_set_strip_height(lb_ctx *h, int rows) {
     if (!h || rows < 1 || rows > h->p.ny) return LB_ERR_ARG;
     h->strip_h = rows;
     h->base.strip_h = rows;
+    ++h->ver;
     return LB_OK;
 }
 
@@ -342,12 +366,14 @@ int lb_set_kernel(lb_ctx *h, int mode) {
     if (!h || mode < LB_KERNEL_AUTO || mode > LB_KERNEL_OVERLAP) return LB_ERR_ARG;
     if (mode == LB_KERNEL_TMA && !h->maps.ok) return LB_ERR_UNSUPPORTED;
     h->kernel_mode = mode;
+    ++h->ver;
     return LB_OK;
 }
 
 int lb_set_wait_ns(lb_ctx *h, long long ns) {
     if (!h) return LB_ERR_ARG;
     h->wait_ns = ns < 0 ? -1 : ns;
+    ++h->ver;
     return LB_OK;
 }
 
@@ -366,33 +392,128 @@ int lb_get_kernel(const lb_ctx *h) {
     return h->p.nx >= 1024 ? LB_KERNEL_OVERLAP : LB_KERNEL_PLAIN;
 }
 
+namespace {
+
+__global__ void clock_set_kernel(uint32_t *clock, uint32_t t) { *clock = t; }
+
+// The first step after t that takes an S(k) sample (LLONG_MAX: none).
+long long next_sample(const lb_ctx *h, long long t) {
+    if (h->sk_every <= 0 || !h->acc) return LLONG_MAX;
+    if (t + 1 <= h->sk_start) return h->sk_start;
+    const long long r = (t + 1 - h->sk_start) % h->sk_every;
+    return r == 0 ? t + 1 : t + 1 + (h->sk_every - r);
+}
+
+// One step on the stream (the launch loop's body; len-step windows capture
+// the same launches with the step counter read from d_clock).
+cudaError_t launch_one(lb_ctx *h, int kern, int buf, bool sample, uint32_t step,
+                       const uint32_t *clock) {
+    StepArgs a = h->base;
+    a.src = h->df[buf];
+    a.dst = h->df[buf ^ 1];
+    a.drho_out = sample ? h->drho : nullptr;
+    a.step = step;
+    a.clock = clock;
+    a.wait_ns = h->wait_ns;
+    a.layout = kern == LB_KERNEL_OVERLAP ? 1 : 0;
+    if (kern == LB_KERNEL_TMA) return launch_step_tma(h->p.stencil, a, h->maps, buf, h->stream);
+    return launch_step(h->p.precision, h->p.stencil, a, h->stream);
+}
+
+// Capture `len` steps from buffer h->cur, the last one sampling S(k) when
+// sample_last; false if the stream cannot be captured.
+int capture_steps(lb_ctx *h, int kern, int len, bool sample_last, cudaGraphExec_t *out) {
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_ERR_UNSUPPORTED;
+    }
+    cudaError_t err = cudaSuccess;
+    int buf = h->cur;
+    for (int j = 0; j < len && err == cudaSuccess; ++j, buf ^= 1)
+        err = launch_one(h, kern, buf, sample_last && j == len - 1, (uint32_t)j, h->d_clock);
+    if (err == cudaSuccess && sample_last) {
+        SkArgs sk;
+        sk.drho = h->drho;
+        sk.spec = h->spec;
+        sk.acc = h->acc;
+        sk.tw_x = h->tw_x;
+        sk.tw_y = h->tw_y;
+        sk.nx = h->p.nx;
+        sk.ny = h->p.ny;
+        sk.ldx = h->ldx;
+        err = launch_sk_sample(h->p.precision, sk, h->stream);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LB_ERR_UNSUPPORTED;
+    }
+    err = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    LB_CHECK(err);
+    return LB_OK;
+}
+
+}  // namespace
+
+// Steps run as replays of captured windows where they can: 32 steps with no
+// sampling step inside, or one sampling interval ending with its sample
+// (bit-identical to the launch loop: the same kernels, with the noise
+// counter read from the device).  The rest, and the staged kernel, are
+// single launches.
 int lb_step(lb_ctx *h, int n) {
     if (!h || n < 0) return LB_ERR_ARG;
     if (!h->inited) return LB_ERR_STATE;
     int rc = select_device(h);
     if (rc) return rc;
     const int kern = lb_get_kernel(h);
-    for (int s = 0; s < n; ++s) {
-        const long long tn = h->t + 1;
-        const bool sample = h->sk_every > 0 && h->acc && tn >= h->sk_start &&
-                            (tn - h->sk_start) % h->sk_every == 0;
-        StepArgs a = h->base;
-        a.src = h->df[h->cur];
-        a.dst = h->df[h->cur ^ 1];
-        a.drho_out = sample ? h->drho : nullptr;
-        a.step = (uint32_t)h->t;
-        a.wait_ns = h->wait_ns;
-        a.layout = kern == LB_KERNEL_OVERLAP ? 1 : 0;
-        if (kern == LB_KERNEL_TMA)
-            LB_CHECK(launch_step_tma(h->p.stencil, a, h->maps, h->cur, h->stream));
-        else
-            LB_CHECK(launch_step(h->p.precision, h->p.stencil, a, h->stream));
+    constexpr int kWindow = 32;
+    while (n > 0) {
+        const long long t = h->t, ns = next_sample(h, t);
+        int kind = -1, len = 0;
+        if (h->graphs_ok && kern != LB_KERNEL_TMA) {
+            if (n >= kWindow && ns > t + kWindow) {
+                kind = 0;
+                len = kWindow;
+            } else if (h->sk_every >= 2 && n >= h->sk_every && ns == t + h->sk_every) {
+                kind = 1;
+                len = h->sk_every;
+            }
+        }
+        if (kind >= 0) {
+            cudaGraphExec_t &g = h->graph[h->cur][kind];
+            if (!g || h->graph_ver[h->cur][kind] != h->ver || h->graph_len[h->cur][kind] != len) {
+                if (g) cudaGraphExecDestroy(g);
+                g = nullptr;
+                rc = capture_steps(h, kern, len, kind == 1, &g);
+                if (rc == LB_ERR_UNSUPPORTED) {
+                    h->graphs_ok = false;   // take single launches from now on
+                    continue;
+                }
+                if (rc) return rc;
+                h->graph_ver[h->cur][kind] = h->ver;
+                h->graph_len[h->cur][kind] = len;
+            }
+            clock_set_kernel<<<1, 1, 0, h->stream>>>(h->d_clock, (uint32_t)t);
+            LB_CHECK(cudaGetLastError());
+            LB_CHECK(cudaGraphLaunch(g, h->stream));
+            h->t = t + len;
+            h->cur ^= len & 1;
+            if (kind == 1) h->sk_count += 1;
+            n -= len;
+            continue;
+        }
+        const bool sample = ns == t + 1;
+        LB_CHECK(launch_one(h, kern, h->cur, sample, (uint32_t)t, nullptr));
         h->cur ^= 1;
-        h->t = tn;
+        h->t = t + 1;
         if (sample) {
             rc = sample_sk(h);
             if (rc) return rc;
         }
+        n -= 1;
     }
     return LB_OK;
 }
@@ -527,6 +648,7 @@ int lb_sk_config(lb_ctx *h, int sample_every, long long start_step) {
     }
     h->sk_every = sample_every;
     h->sk_start = start_step;
+    ++h->ver;
     return LB_OK;
 }
 
@@ -750,6 +872,7 @@ int lb_load(lb_ctx *h, const char *path) {
     h->cur = 0;
     h->inited = true;
     fill_base(h);
+    ++h->ver;
     LB_CHECK(cudaMemcpyAsync(h->df[0], df.data(), df.size(), cudaMemcpyHostToDevice, h->stream));
     if (hd.has_acc) {
         LB_CHECK(cudaMemcpyAsync(h->acc, acc.data(), acc.size() * sizeof(double),

@@ -23,6 +23,9 @@ template <typename T> struct KParams {
     T c3a, c3b, c4a, c4b, c5a, c5b;   // folded relaxation/source constants
     T amp[6];
     uint32_t rk[20];
+    // when not null, the step counter of the noise is *clock + step (a
+    // captured window of steps replays for any starting step)
+    const uint32_t *__restrict__ clock;
 };
 
 __device__ __forceinline__ int wrap_once(int a, int n) {
@@ -84,7 +87,13 @@ template <typename T>
 __device__ __forceinline__ void collide_tail(T drho, T m1, T m2, T m3, T m4, T m5, T m6, T m7,
                                              T m8, T Fx, T Fy, const KParams<T> &p,
                                              const uint32_t *__restrict__ rk, uint32_t site,
-                                             T f[9], bool unit);
+                                             uint32_t step, T f[9], bool unit);
+
+// The step counter of the noise for a kernel launched with params p.
+template <typename T>
+__device__ __forceinline__ uint32_t step_of(const KParams<T> &p) {
+    return p.clock ? p.step + __ldg(p.clock) : p.step;
+}
 
 // Mass and momentum deviations of the pulled populations, with exactly the
 // arithmetic of the forward transform in collide (so that a kernel may keep
@@ -106,17 +115,19 @@ __device__ __forceinline__ void unit_moments(const T g[9], T &drho, T &m1, T &m2
 template <typename T>
 __device__ __forceinline__ void collide_unit_m(T drho, T m1, T m2, T Fx, T Fy, const KParams<T> &p,
                                                const uint32_t *__restrict__ rk, uint32_t site,
-                                               T f[9]) {
-    collide_tail<T>(drho, m1, m2, T(0), T(0), T(0), T(0), T(0), T(0), Fx, Fy, p, rk, site, f, true);
+                                               uint32_t step, T f[9]) {
+    collide_tail<T>(drho, m1, m2, T(0), T(0), T(0), T(0), T(0), T(0), Fx, Fy, p, rk, site, step, f,
+                    true);
 }
 
 template <typename T, bool UNIT = false>
 __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<T> &p,
-                                        const uint32_t *__restrict__ rk, uint32_t site, T f[9]) {
+                                        const uint32_t *__restrict__ rk, uint32_t site,
+                                        uint32_t step, T f[9]) {
     if constexpr (UNIT) {
         T drho, m1, m2;
         unit_moments(g, drho, m1, m2);
-        collide_unit_m(drho, m1, m2, Fx, Fy, p, rk, site, f);
+        collide_unit_m(drho, m1, m2, Fx, Fy, p, rk, site, step, f);
         return;
     }
     // forward transform (integer coefficients, shared subexpressions)
@@ -135,7 +146,7 @@ __device__ __forceinline__ void collide(const T g[9], T Fx, T Fy, const KParams<
     const T m6 = fma(T(2), t1, -e13);                        // (3c^2 - 4) cx
     const T m7 = fma(T(2), t2, -e24);                        // (3c^2 - 4) cy
     const T m8 = fma(T(8), sd, fma(T(-4), sa, g[0] + g[0])); // 9c^4 - 15c^2 + 2
-    collide_tail<T>(drho, m1, m2, m3, m4, m5, m6, m7, m8, Fx, Fy, p, rk, site, f, false);
+    collide_tail<T>(drho, m1, m2, m3, m4, m5, m6, m7, m8, Fx, Fy, p, rk, site, step, f, false);
 }
 
 // Everything after the forward transform: Guo velocity, relaxation with the
@@ -144,7 +155,7 @@ template <typename T>
 __device__ __forceinline__ void collide_tail(T drho, T m1, T m2, T m3, T m4, T m5, T m6, T m7,
                                              T m8, T Fx, T Fy, const KParams<T> &p,
                                              const uint32_t *__restrict__ rk, uint32_t site,
-                                             T f[9], bool unit) {
+                                             uint32_t step, T f[9], bool unit) {
     const T rho = p.rho0 + drho;
     const T inv_rho = inv_rho_of(rho);
     const T jxh = fma(T(0.5), Fx, m1), jyh = fma(T(0.5), Fy, m2);   // rho u
@@ -171,7 +182,7 @@ __device__ __forceinline__ void collide_tail(T drho, T m1, T m2, T m3, T m4, T m
     if (p.noise) {
         // one Philox call per site and step: radius words r.x, r.y, r.z and
         // three 10-bit angle indices of r.w (bits 0-9, 10-19, 20-29)
-        const uint4 r = philox4x32_10(make_uint4(site, p.step, p.replica, 0u), rk);
+        const uint4 r = philox4x32_10(make_uint4(site, step, p.replica, 0u), rk);
         T c, sn, rad;
         box_ring_polar(uniform01<T>(r.x), r.w & 1023u, rho, rad, c, sn);
         m3s = fma(p.amp[0] * rad, c, m3s);
@@ -217,6 +228,7 @@ inline KParams<T> make_params(const StepArgs &a) {
     k.psi_kind = (int)a.psi_kind;
     k.noise = a.noise;
     k.step = a.step;
+    k.clock = a.clock;
     k.replica = a.replica;
     k.rho0 = (T)a.rho0;
     k.force_pref = (T)a.force_pref;

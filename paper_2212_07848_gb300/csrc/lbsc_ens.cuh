@@ -52,6 +52,7 @@ __device__ __forceinline__ void fill_tile_params(KParams<float> &sp, const EnsRe
     sp.psi_kind = R.psi_kind;
     sp.noise = R.noise;
     sp.step = t;
+    sp.clock = nullptr;
     sp.replica = R.replica;
     sp.rho0 = R.rho0;
     sp.force_pref = R.force_pref;

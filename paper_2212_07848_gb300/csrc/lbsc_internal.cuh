@@ -49,6 +49,7 @@ struct StepArgs {
     int noise;            // kT > 0
     long long wait_ns;    // staged kernel: bound on an mbarrier wait (< 0: default)
     int layout;           // plain kernel: 0 = halo warp, 1 = overlapped strips
+    const uint32_t *clock;  // device step counter: the noise counter is *clock + step (or null)
 };
 
 // FFT / structure-factor buffers of one lattice.

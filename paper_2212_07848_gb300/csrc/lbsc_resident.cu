@@ -156,8 +156,8 @@ __device__ __forceinline__ void res_sweep(const KParams<float> &p, const uint32_
         float f[9];
         const int yg = ybase + yr;
         const uint32_t site = (uint32_t)tx + (uint32_t)nx * (uint32_t)yg;
-        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, f);
-        else collide<float, false>(q[0], Fx, Fy, p, rk, site, f);
+        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, p.step, f);
+        else collide<float, false>(q[0], Fx, Fy, p, rk, site, p.step, f);
         float *w = sm + yr * nx + tx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) w[i * P] = f[i];

@@ -286,7 +286,7 @@ step_kernel_tma(const __grid_constant__ CUtensorMap tm_src,
 
         float g[9], f[9];
         pull_smem(slot_of(it - H) + col, slot_of(it - H + 1) + col, slot_of(it - H + 2) + col, g);
-        collide(g, Fx, Fy, p, p.rk, (uint32_t)(x0 + tx) + (uint32_t)nx * (uint32_t)yr, f);
+        collide(g, Fx, Fy, p, p.rk, (uint32_t)(x0 + tx) + (uint32_t)nx * (uint32_t)yr, step_of(p), f);
         float *st = stage + (it & 1) * 9 * kTX + tx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) st[i * kTX] = f[i];

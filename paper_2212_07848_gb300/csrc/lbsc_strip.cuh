@@ -56,6 +56,7 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
     const int xp = x == nx - 1 ? 0 : x + 1;
 
     const T rho0 = p.rho0;
+    const uint32_t step = step_of(p);   // the noise counter of this step
 
     // what a row keeps for its collision H rows later: the nine pulled
     // populations, or on the unit-relaxation path only (sum for the sample,
@@ -130,8 +131,8 @@ __device__ __forceinline__ void step_strip(const KParams<T> &p, const uint32_t *
 
         T f[9];
         const uint32_t site = (uint32_t)x + (uint32_t)nx * (uint32_t)yr;
-        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, f);
-        else collide<T, false>(q[0], Fx, Fy, p, rk, site, f);
+        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, step, f);
+        else collide<T, false>(q[0], Fx, Fy, p, rk, site, step, f);
 
         const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
         p.dst[o] = f[0];
@@ -184,6 +185,7 @@ __device__ __forceinline__ void step_strip_ov(const KParams<T> &p,
     const int xp = x == nx - 1 ? 0 : x + 1;
 
     const T rho0 = p.rho0;
+    const uint32_t step = step_of(p);   // the noise counter of this step
 
     // what a row keeps for its collision H rows later: the nine pulled
     // populations, or on the unit-relaxation path only (sum for the sample,
@@ -250,8 +252,8 @@ __device__ __forceinline__ void step_strip_ov(const KParams<T> &p,
 
         T f[9];
         const uint32_t site = (uint32_t)x + (uint32_t)nx * (uint32_t)yr;
-        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, f);
-        else collide<T, false>(q[0], Fx, Fy, p, rk, site, f);
+        if constexpr (UNIT) collide_unit_m(q[0][1], q[0][2], q[0][3], Fx, Fy, p, rk, site, step, f);
+        else collide<T, false>(q[0], Fx, Fy, p, rk, site, step, f);
 
         const uint32_t o = (uint32_t)yr * nx + x, pl = (uint32_t)plane;
         p.dst[o] = f[0];

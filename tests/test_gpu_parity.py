@@ -164,3 +164,48 @@ def test_mrt_matches_oracle(precision, steps, tol, st, tau, tb, tg):
     g.step(steps)
     o.step(steps)
     _compare(g, o, tol)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_captured_windows_give_the_launch_loop_bits(precision):
+    """lb_step replays captured windows (32 plain steps; one S(k) interval
+    ending with its sample) with the noise counter read from the device: the
+    same bits as single launches, across window starts on either buffer and
+    after every change a window bakes in (replica, strip height, kernel
+    layout, sampling schedule, re-initialisation)."""
+    from paper_2212_07848_gb300 import abi
+    from paper_2212_07848_gb300.lattice import Lattice
+    a = Lattice(256, 128, -4.4, 1.0, 1e-5, precision=precision)
+    b = Lattice(256, 128, -4.4, 1.0, 1e-5, precision=precision)
+    for g in (a, b):
+        g.init(0.7, 11, 0.01)
+        g.sk_config(10, 40)
+    def run(g, counts):
+        for c in counts:
+            if g is a:
+                g.step(c)
+            else:
+                for _ in range(c):
+                    g.step(1)
+    run(a, [5, 64, 33, 40])   # windows from an odd and an even start, sampling windows
+    run(b, [5, 64, 33, 40])
+    assert np.array_equal(a.populations(), b.populations())
+    Sa, na = a.structure_factor()
+    Sb, nb = b.structure_factor()
+    assert na == nb and np.array_equal(Sa, Sb)
+    for g in (a, b):
+        g.set_replica(3)
+        g.set_strip_height(7)
+        g.set_kernel(abi.LB_KERNEL_OVERLAP)
+        g.sk_config(16, 200)
+    run(a, [70])
+    run(b, [70])
+    assert np.array_equal(a.populations(), b.populations())
+    for g in (a, b):
+        g.init(0.7, 12, 0.01)
+    run(a, [96])
+    run(b, [96])
+    assert np.array_equal(a.populations(), b.populations())
+    Sa, na = a.structure_factor()
+    Sb, nb = b.structure_factor()
+    assert na == nb and np.array_equal(Sa, Sb)
