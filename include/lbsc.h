@@ -163,7 +163,12 @@ int lb_set_wait_ns(lb_ctx *h, long long ns);
 
 /* Advance n >= 0 time steps of Eq. (12), asynchronously on the context
  * stream.  Sampling steps (lb_sk_config) also run the S(k) transform and
- * accumulation.  Returns the launch status (LB_ERR_CUDA if a launch failed,
+ * accumulation.  Windows of 32 steps without a sampling step, and sampling
+ * intervals ending with their sample, replay CUDA graphs captured on first
+ * use (the step counter of the noise read from device memory; recaptured
+ * after any setter that changes what they hold); other steps, the staged
+ * kernel and streams that cannot be captured use single launches, with the
+ * same results.  Returns the launch status (LB_ERR_CUDA if a launch failed,
  * LB_ERR_STATE before lb_init); NaN/Inf shows at the next synchronising
  * call. */
 int lb_step(lb_ctx *h, int n);
