@@ -52,12 +52,13 @@ struct lb_ctx {
     long long wait_ns = -1;         // staged kernel's mbarrier bound (< 0: default)
     StepArgs base;
     // captured windows of steps: [starting buffer][0: 32 plain steps, 1: one
-    // S(k) interval ending with its sample]; the step counter of the noise is
-    // read from d_clock, set before each replay
+    // S(k) interval ending with its sample, 2: 32 steps sampling at every
+    // step]; the step counter of the noise is read from d_clock, set before
+    // each replay
     uint32_t *d_clock = nullptr;
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    int graph_len[2][2] = {{0, 0}, {0, 0}};
-    long long graph_ver[2][2] = {{-1, -1}, {-1, -1}};
+    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int graph_len[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    long long graph_ver[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
     long long ver = 0;              // bumped by every change that a captured window bakes in
     bool graphs_ok = true;          // false once a capture failed (e.g. the legacy stream)
 };
@@ -420,28 +421,29 @@ cudaError_t launch_one(lb_ctx *h, int kern, int buf, bool sample, uint32_t step,
     return launch_step(h->p.precision, h->p.stencil, a, h->stream);
 }
 
-// Capture `len` steps from buffer h->cur, the last one sampling S(k) when
-// sample_last; false if the stream cannot be captured.
-int capture_steps(lb_ctx *h, int kern, int len, bool sample_last, cudaGraphExec_t *out) {
+// Capture `len` steps from buffer h->cur; sampling S(k) at the last step
+// (kind 1) or at every step (kind 2); LB_ERR_UNSUPPORTED if the stream
+// cannot be captured.
+int capture_steps(lb_ctx *h, int kern, int len, int kind, cudaGraphExec_t *out) {
     if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return LB_ERR_UNSUPPORTED;
     }
+    SkArgs sk;
+    sk.drho = h->drho;
+    sk.spec = h->spec;
+    sk.acc = h->acc;
+    sk.tw_x = h->tw_x;
+    sk.tw_y = h->tw_y;
+    sk.nx = h->p.nx;
+    sk.ny = h->p.ny;
+    sk.ldx = h->ldx;
     cudaError_t err = cudaSuccess;
     int buf = h->cur;
-    for (int j = 0; j < len && err == cudaSuccess; ++j, buf ^= 1)
-        err = launch_one(h, kern, buf, sample_last && j == len - 1, (uint32_t)j, h->d_clock);
-    if (err == cudaSuccess && sample_last) {
-        SkArgs sk;
-        sk.drho = h->drho;
-        sk.spec = h->spec;
-        sk.acc = h->acc;
-        sk.tw_x = h->tw_x;
-        sk.tw_y = h->tw_y;
-        sk.nx = h->p.nx;
-        sk.ny = h->p.ny;
-        sk.ldx = h->ldx;
-        err = launch_sk_sample(h->p.precision, sk, h->stream);
+    for (int j = 0; j < len && err == cudaSuccess; ++j, buf ^= 1) {
+        const bool sample = kind == 2 || (kind == 1 && j == len - 1);
+        err = launch_one(h, kern, buf, sample, (uint32_t)j, h->d_clock);
+        if (err == cudaSuccess && sample) err = launch_sk_sample(h->p.precision, sk, h->stream);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
@@ -459,10 +461,10 @@ int capture_steps(lb_ctx *h, int kern, int len, bool sample_last, cudaGraphExec_
 }  // namespace
 
 // Steps run as replays of captured windows where they can: 32 steps with no
-// sampling step inside, or one sampling interval ending with its sample
-// (bit-identical to the launch loop: the same kernels, with the noise
-// counter read from the device).  The rest, and the staged kernel, are
-// single launches.
+// sampling step inside, one sampling interval ending with its sample, or 32
+// steps that all sample (bit-identical to the launch loop: the same kernels,
+// with the noise counter read from the device).  The rest, and the staged
+// kernel, are single launches.
 int lb_step(lb_ctx *h, int n) {
     if (!h || n < 0) return LB_ERR_ARG;
     if (!h->inited) return LB_ERR_STATE;
@@ -480,6 +482,9 @@ int lb_step(lb_ctx *h, int n) {
             } else if (h->sk_every >= 2 && n >= h->sk_every && ns == t + h->sk_every) {
                 kind = 1;
                 len = h->sk_every;
+            } else if (h->sk_every == 1 && n >= kWindow && ns == t + 1) {
+                kind = 2;
+                len = kWindow;
             }
         }
         if (kind >= 0) {
@@ -487,7 +492,7 @@ int lb_step(lb_ctx *h, int n) {
             if (!g || h->graph_ver[h->cur][kind] != h->ver || h->graph_len[h->cur][kind] != len) {
                 if (g) cudaGraphExecDestroy(g);
                 g = nullptr;
-                rc = capture_steps(h, kern, len, kind == 1, &g);
+                rc = capture_steps(h, kern, len, kind, &g);
                 if (rc == LB_ERR_UNSUPPORTED) {
                     h->graphs_ok = false;   // take single launches from now on
                     continue;
@@ -502,6 +507,7 @@ int lb_step(lb_ctx *h, int n) {
             h->t = t + len;
             h->cur ^= len & 1;
             if (kind == 1) h->sk_count += 1;
+            if (kind == 2) h->sk_count += len;
             n -= len;
             continue;
         }

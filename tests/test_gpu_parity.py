@@ -209,3 +209,22 @@ def test_captured_windows_give_the_launch_loop_bits(precision):
     Sa, na = a.structure_factor()
     Sb, nb = b.structure_factor()
     assert na == nb and np.array_equal(Sa, Sb)
+
+
+def test_captured_windows_sampling_every_step():
+    """Sampling at every step (the 128^2 FP64 configuration's schedule):
+    32-step windows that sample at each step give the single launches' bits
+    and sample count."""
+    from paper_2212_07848_gb300.lattice import Lattice
+    a = Lattice(128, 128, -3.6, 1.0, 1e-5, precision="fp64")
+    b = Lattice(128, 128, -3.6, 1.0, 1e-5, precision="fp64")
+    for g in (a, b):
+        g.init(LN2, 0, 0.0)
+        g.sk_config(1, 21)
+    a.step(90)
+    for _ in range(90):
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+    Sa, na = a.structure_factor()
+    Sb, nb = b.structure_factor()
+    assert na == nb == 70 and np.array_equal(Sa, Sb)
