@@ -472,6 +472,7 @@ int lb_step(lb_ctx *h, int n) {
     if (rc) return rc;
     const int kern = lb_get_kernel(h);
     constexpr int kWindow = 32;
+    constexpr int kMaxWindow = 1024;   // longest sampling interval captured whole
     while (n > 0) {
         const long long t = h->t, ns = next_sample(h, t);
         int kind = -1, len = 0;
@@ -479,7 +480,8 @@ int lb_step(lb_ctx *h, int n) {
             if (n >= kWindow && ns > t + kWindow) {
                 kind = 0;
                 len = kWindow;
-            } else if (h->sk_every >= 2 && n >= h->sk_every && ns == t + h->sk_every) {
+            } else if (h->sk_every >= 2 && h->sk_every <= kMaxWindow && n >= h->sk_every &&
+                       ns == t + h->sk_every) {
                 kind = 1;
                 len = h->sk_every;
             } else if (h->sk_every == 1 && n >= kWindow && ns == t + 1) {
