@@ -1020,8 +1020,10 @@ int lb_ens_step(lb_ens *e, int n) {
         const bool plain_ok = n >= kGraphSteps &&
                               (!sk || t + kGraphSteps < e->sk_start);
         // a window t+1 .. t+every whose only sampling step is its last
+        // (one launch per step: intervals of at most 1024 steps are captured whole)
         const bool window_ok = sk && e->sk_every >= 2 && n >= e->sk_every && t >= e->sk_start &&
-                               (t - e->sk_start) % e->sk_every == 0;
+                               (t - e->sk_start) % e->sk_every == 0 &&
+                               (e->launch_mode == LB_ENS_PERSISTENT || e->sk_every <= 1024);
         if (plain_ok || window_ok) {
             cudaGraphExec_t *g = plain_ok ? &e->graph_plain : &e->graph_window;
             const int len = plain_ok ? kGraphSteps : e->sk_every;
