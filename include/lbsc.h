@@ -313,21 +313,21 @@ int lb_ens_autotune(lb_ens *e, int trial_steps, const char *cache_path, int *cho
  * over every replica's tiles.  LB_ENS_PERSISTENT: each window of steps
  * (32 plain steps, or one S(k) sampling interval) is one cooperative
  * persistent launch whose CTAs take (step, tile) pairs in order from a
- * counter; a tile of a replica waits (bounded, 2 s) until all tiles of that
- * replica finished the previous step; a timeout makes the next sync return
- * LB_ERR_TIMEOUT.  A window's sampling step runs as a per-step launch.  Both
+ * counter; a tile waits (bounded, 2 s) until the tiles it pulls from (its
+ * neighbours within the stencil's reach, and itself) finished the previous
+ * step; a timeout makes the next sync return LB_ERR_TIMEOUT.  A window's sampling step runs as a per-step launch.  Both
  * give the same bits.  LB_ERR_UNSUPPORTED if the device cannot launch
  * cooperatively. */
 #define LB_ENS_PER_STEP 0
 #define LB_ENS_PERSISTENT 1
 int lb_ens_set_launch(lb_ens *e, int mode);
 int lb_ens_get_launch(const lb_ens *e);
-/* Bound, in nanoseconds of the device's global timer, on each replica
- * barrier of the persistent launch (failure detection, the bounded waits of
- * a persistent kernel).  ns < 0 restores the default of 2 s; ns = 0 makes a
- * barrier give up at the first check that finds its replica's previous step
- * unfinished.  On a timeout the waiting CTA records it, every other CTA stops
- * at its next barrier, the launch ends, and lb_ens_sync returns
+/* Bound, in nanoseconds of the device's global timer, on each dependency
+ * wait of the persistent launch (failure detection, the bounded waits of a
+ * persistent kernel).  ns < 0 restores the default of 2 s; ns = 0 makes a
+ * wait give up at the first check that finds a tile it pulls from unfinished
+ * with the previous step.  On a timeout the waiting CTA records it, every
+ * other CTA stops at its next wait, the launch ends, and lb_ens_sync returns
  * LB_ERR_TIMEOUT; the replicas' state is then partly advanced and must be
  * re-initialised (lb_ens_init) before it is used again.  Synchronises the
  * ensemble's stream.  Errors: LB_ERR_ARG, LB_ERR_CUDA. */
