@@ -70,7 +70,14 @@ def test_network_gradients_match_reference(flux, mom, n):
     # The flux adjoint differences BF16 gradients, and its output sums to zero
     # over each image, so the bias gradients (pixel sums) are small residues
     # of cancellation that only the ReLU masks leave: looser bounds there.
-    tol, tol_b = (8e-2, 1.5e-1) if flux else (5e-2, 5e-2)
+    # Measured on GB300 (relative RMS errors, BF16 activations and gradients
+    # between layers): plain increments at most 0.012 (the first layer's
+    # weights, whose gradient sums BF16 gradients over every pixel) and 0.0024
+    # for biases; the flux form with the momentum state 0.038; the flux form
+    # alone 0.072 / 0.082, its adjoint differencing BF16 gradients.
+    tol, tol_b = (8e-2, 1.5e-1) if flux else (2.5e-2, 1e-2)
+    if flux and mom:
+        tol, tol_b = 6e-2, 4e-2
     for i in range(len(LAYERS)):
         assert _rel(net.dw[i].cpu().numpy(), dw[i]) < tol, i
         if flux and i == len(LAYERS) - 1:
@@ -234,6 +241,7 @@ def test_two_stride_gradients_match_reference():
                                       t2.cpu().numpy())
     dw, db = R.two_stride_backward(xr, w, b, t1.cpu().numpy(), t2.cpu().numpy(), mid)
     assert abs(float(loss.item()) - ref_loss) < 2e-2 * ref_loss
+    # measured on GB300: at most 0.022 (first layer's weights), biases 0.0034
     for i in range(len(LAYERS)):
-        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < 8e-2, i
-        assert _rel(net.db[i].cpu().numpy(), db[i]) < 8e-2, i
+        assert _rel(net.dw[i].cpu().numpy(), dw[i]) < 4e-2, i
+        assert _rel(net.db[i].cpu().numpy(), db[i]) < 1e-2, i
