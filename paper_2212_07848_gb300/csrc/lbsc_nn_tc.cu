@@ -34,7 +34,7 @@ __device__ int g_nn_status;               // bit 0: an mbarrier wait gave up;
                                           // bit 1: tensor memory left allocated
 constexpr unsigned long long kTcWaitNs = 1000000000ull;   // default bound: 1 s
 __device__ unsigned long long g_nn_wait_ns = kTcWaitNs;   // lb_nn_set_wait_ns
-extern const int kWgTcMaxChunks = 192;   // bound on a weight-gradient launch's chunks
+extern const int kWgTcMaxChunks = 192;   // bound on the SMs a weight-gradient launch plans for
 
 namespace {
 
@@ -788,7 +788,11 @@ cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
     } else {
         mw = mx;   // unused by the input gradient
     }
-    static int nsm = 0;
+    // CTAs resident per SM (shared memory, registers and the padding above):
+    // a narrow layer's output rows are short chains of copies, MMAs and a
+    // read-out whose latency one CTA per SM cannot hide, so the grid fills
+    // every resident slot
+    static int nsm = 0, per_sm = 1;
     if (!nsm) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -796,14 +800,18 @@ cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(conv3x3_tcp_kernel<BN, CIN, DG>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, conv3x3_tcp_kernel<BN, CIN, DG>, kTcpThreads, kSmem);
         if (e != cudaSuccess) {
             nsm = 0;
             return e;
         }
+        per_sm = std::max(1, std::min(per_sm, kPerSm));
     }
     const int nblk = cout / BN;
     const long units = (long)nb * h * (wd / 128);
-    int per_blk = std::max(1, nsm / nblk);
+    int per_blk = std::max(1, nsm * per_sm / nblk);
     if (per_blk > units) per_blk = (int)units;
     const int per = (int)((units + per_blk - 1) / per_blk);
     conv3x3_tcp_kernel<BN, CIN, DG><<<nblk * per_blk, kTcpThreads, kSmem, s>>>(
@@ -857,15 +865,35 @@ cudaError_t launch_tcp_shape(const bf16 *x, const bf16 *w, const float *bias, bf
 // one thread of warp 5 the MMAs, warps 0-3 read the accumulators at the end.
 // Every wait is bounded, as in the forward kernel.
 // ---------------------------------------------------------------------------
-// Taps per CTA: all nine when their accumulators (9 x nc columns of tensor
-// memory) and three staged x rows of cin channels fit, else one tap row.
-__host__ __device__ constexpr int wg_taps(int cin, int nc) {
-    return 9 * nc <= 512 && 3 * 144 * cin * 2 <= 80 * 1024 ? 9 : 3;
+// CTAs per SM for a weight gradient with cin input and cout output channels
+// and tp taps per CTA: two when their accumulators (at most 256
+// tensor-memory columns each) and a ring of at least two slots plus the
+// padding slack fit twice (a narrow layer's tiles are short chains of copies
+// and MMAs whose latency a second CTA hides), else one.
+__host__ __device__ constexpr int wg_ctas(int tp, int cin, int cout) {
+    const bool ax = cin > cout;
+    const int ac = ax ? cin : cout, nc = ax ? cout : cin;
+    const int xr = tp == 9 ? 3 : 1;
+    const int slot = xr * ((144 * cin * 2 + 1023) / 1024 * 1024) + (128 * cout * 2 + 1023) / 1024 * 1024;
+    const int slack = (128 - ac) * (ax ? 144 : 128) * 2;
+    return tp * nc <= 256 && (110 * 1024 - slack) / slot >= 2 ? 2 : 1;
+}
+// Taps per CTA: all nine (their accumulators take 9 nc tensor-memory
+// columns, and three staged x rows must fit) unless one tap row per CTA gives
+// two CTAs per SM where nine do not.
+__host__ __device__ constexpr int wg_taps(int cin, int cout) {
+    const int nc = cin < cout ? cin : cout;
+    const bool nine = 9 * nc <= 512 && 3 * 144 * cin * 2 <= 80 * 1024;
+    return nine && wg_ctas(9, cin, cout) == 2 ? 9 : (wg_ctas(3, cin, cout) == 2 ? 3 : (nine ? 9 : 3));
+}
+__host__ __device__ constexpr int wg_per_sm(int cin, int cout) {
+    return wg_ctas(wg_taps(cin, cout), cin, cout);
 }
 
 template <int AC, int NC, bool AX>
 struct WCfg {
-    static constexpr int TP = wg_taps(AX ? AC : NC, NC);   // taps per CTA
+    static constexpr int TP = wg_taps(AX ? AC : NC, AX ? NC : AC);   // taps per CTA
+    static constexpr int PER_SM = wg_per_sm(AX ? AC : NC, AX ? NC : AC);
     static constexpr int TG = 9 / TP;                   // tap groups
     static constexpr int XR = TP == 9 ? 3 : 1;          // x rows staged per tile
     static constexpr int XC = AX ? AC : NC;             // channels of x
@@ -883,7 +911,7 @@ struct WCfg {
     static constexpr int B_BYTES = AX ? D_STRIDE : XR * X_STRIDE;
     // what the MMAs read of the A operand past its AC channels (M = 128)
     static constexpr int SLACK = (128 - AC) * (AX ? XROW : DROW) * 2;
-    static constexpr int S0 = (200 * 1024 - SLACK) / (A_BYTES + B_BYTES);
+    static constexpr int S0 = ((PER_SM == 2 ? 110 : 200) * 1024 - SLACK) / (A_BYTES + B_BYTES);
     static constexpr int S = S0 > 4 ? 4 : S0;           // ring slots
     static constexpr int SMEM = S * (A_BYTES + B_BYTES) + SLACK;
     static constexpr uint32_t NCOLS = TP * NC <= 32 ? 32 : TP * NC <= 64 ? 64
@@ -1173,17 +1201,16 @@ cudaError_t launch_conv3x3_tcp(const void *x, const void *w, const float *bias, 
 }
 
 // Weight gradient on tcgen05 (see wgrad_tc_kernel): the chunk count for a
-// launch (CTAs = tap groups x chunks, one per SM), or 0 where the kernel does
+// launch (CTAs = tap groups x chunks, one or two per SM), or 0 where the kernel does
 // not apply (image rows not a multiple of 128 pixels, channel counts other
 // than 16, 32, 64, 128).
 int wgrad_tc_chunks(int nb, int h, int wd, int cin, int cout, int nsm) {
     auto ok = [](int c) { return c == 16 || c == 32 || c == 64 || c == 128; };
     if (wd % 128 || h < 2 || !ok(cin) || !ok(cout) || nsm < 1) return 0;
-    const int nc = cin < cout ? cin : cout;
-    const int tg = 9 / wg_taps(cin, nc);
+    const int tg = 9 / wg_taps(cin, cout), per_sm = wg_per_sm(cin, cout);
     const long ntiles = (long)nb * h * (wd / 128);
-    long k = nsm / tg;
-    if (k > kWgTcMaxChunks / tg) k = kWgTcMaxChunks / tg;
+    long k = (long)nsm * per_sm / tg;
+    if (k > (long)kWgTcMaxChunks * per_sm / tg) k = (long)kWgTcMaxChunks * per_sm / tg;
     if (k > ntiles) k = ntiles;
     if (k < 1) k = 1;
     // chunks of ceil(ntiles / k) tiles: keep only those that get a tile
