@@ -108,12 +108,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // of a group, or 32 bytes into a row for the next K step, with the base
 // offset field left at 0 (checked against the CPU reference on GB300; the
 // field set to the start row's index gave wrong results).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+// (The same holds for rows of SP = 32 or 64 bytes, 16 or 32 BF16, with the
+// matching 32- or 64-byte pattern: 8-row groups 8 SP bytes apart, layout type
+// 6 or 4.)
+template <int SP>
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr) {
+    static_assert(SP == 32 || SP == 64 || SP == 128, "swizzle span");
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;              // SBO: 8 rows of 128 bytes
+    d |= (uint64_t)((8u * SP) >> 4) << 32;         // SBO: 8 rows
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)(SP == 128 ? 2 : SP == 64 ? 4 : 6) << 61;
     return d;
 }
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
@@ -363,33 +368,29 @@ cudaError_t launch_tc(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, 
 // ---------------------------------------------------------------------------
 template <int BN, int CIN>
 struct PCfg {
-    // SW: 64 or 128 input channels, staged in the 128-byte swizzled layout
-    // (TMA boxes of 64 channels: 128-byte rows); otherwise the no-swizzle
-    // layout of 16-byte K chunks (boxes of 8 channels)
-    static constexpr bool SW = CIN >= 64;
-    static constexpr int KC = CIN / 8;
-    static constexpr int KB = CIN / 64;           // 64-channel blocks (SW)
-    // no-swizzle: a staged K chunk (8 channels) of one input row holds pixels
-    // x0-8 .. x0+135 at 16-byte pitch; column c = pixel x0-1+c sits at byte
-    // 112 + 16c of its chunk (the three copies start on 128-byte boundaries).
-    // SW: a 64-channel block holds the same 144 pixels as 128-byte rows;
-    // column c is row c + 7.
-    static constexpr uint32_t LBO_A = SW ? 144 * 128 : 144 * 16;
-    static constexpr uint32_t COL0 = SW ? 7 * 128 : 112;
-    static constexpr uint32_t PIX = SW ? 128 : 16;        // bytes between pixels
-    static constexpr int ROW_BYTES = SW ? KB * 144 * 128 : KC * 144 * 16;
+    // Input channels are staged in blocks of BC = min(CIN, 64) channels, one
+    // TMA box each, whose pixel rows of SP = 2 BC bytes carry the matching
+    // 32-, 64- or 128-byte swizzle: a block of one input row holds pixels
+    // x0-8 .. x0+135 as 144 rows; column c (pixel x0-1+c) is row c + 7.
+    static constexpr int BC = CIN < 64 ? CIN : 64;
+    static constexpr int SP = 2 * BC;                     // bytes per pixel row of a block
+    static constexpr int KB = CIN / BC;                   // channel blocks
+    static constexpr int KS = SP / 32;                    // K = 16 steps per block
+    static constexpr uint32_t LBO_A = 144 * SP;           // block stride of a staged row
+    static constexpr uint32_t COL0 = 7 * SP;
+    static constexpr uint32_t PIX = SP;                   // bytes between pixels
+    static constexpr int ROW_BYTES = KB * 144 * SP;
     static constexpr int TAP_BYTES = BN * CIN * 2;
     static constexpr int B_BYTES = 9 * TAP_BYTES;
     static constexpr int R0 = (220 * 1024 - B_BYTES) / ROW_BYTES;
     static constexpr int R = R0 < 4 ? 4 : (R0 > 8 ? 8 : R0);   // ring slots
     static constexpr int A_BYTES = R * ROW_BYTES;
     static constexpr int SMEM = A_BYTES + B_BYTES;
-    // B per tap, no-swizzle: K chunk kc of output channel n at kc * BN * 16 +
-    // n * 16; SW: 64-channel block kb of output channel n at kb * BN * 128 +
-    // n * 128 (chunks swizzled)
-    static constexpr uint32_t LBO_B = SW ? BN * 128 : BN * 16;
+    // B per tap: channel block kb of output channel n at kb * BN * SP + n * SP
+    // (16-byte chunks swizzled as TMA writes them)
+    static constexpr uint32_t LBO_B = BN * SP;
     static constexpr uint32_t ROW_TX = (uint32_t)CIN * 144 * 2;   // bytes landing per row
-    static constexpr int ALIGN = SW ? 1024 : 128;               // staging alignment
+    static constexpr int ALIGN = 1024;                            // staging alignment
     static constexpr uint32_t NCOLS = 2 * BN <= 32 ? 32 : (2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : 256));
 };
 constexpr int kTcpThreads = 192;
@@ -469,18 +470,17 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
             const uint4 q = *reinterpret_cast<const uint4 *>(
                 w + ((size_t)(8 - tap) * CIN + c) * Cout + n0 + nc * 8);
             const bf16 *e = reinterpret_cast<const bf16 *>(&q);
-            if constexpr (C::SW) {
-                // row n = nc * 8 + j of block c / 64; its 16-byte chunk (c % 64) / 8
-                // sits at chunk index ((c % 64) / 8) ^ (n % 8)
-                uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 6) * C::LBO_B + nc * 1024 + (c & 7) * 2;
-                const int ch = (c & 63) >> 3;
+            // row n = nc * 8 + j of block c / BC; its 16-byte chunk ch = (c % BC) / 8
+            // sits at chunk index ch ^ sw(n), the swizzle of an SP-byte row
+            // (128: n % 8; 64: (n / 2) % 4; 32: (n / 4) % 2)
+            uint8_t *d = sB + tap * C::TAP_BYTES + (c / C::BC) * C::LBO_B + nc * 8 * C::SP +
+                         (c & 7) * 2;
+            const int ch = (c % C::BC) >> 3;
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    *reinterpret_cast<bf16 *>(d + j * 128 + ((ch ^ j) << 4)) = e[j];
-            } else {
-                uint8_t *d = sB + tap * C::TAP_BYTES + (c >> 3) * C::LBO_B + nc * 128 + (c & 7) * 2;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16 *>(d + j * 16) = e[j];
+            for (int j = 0; j < 8; ++j) {
+                const int n = nc * 8 + j;
+                const int sw = C::SP == 128 ? (n & 7) : (C::SP == 64 ? ((n >> 1) & 3) : ((n >> 2) & 1));
+                *reinterpret_cast<bf16 *>(d + j * C::SP + ((ch ^ sw) << 4)) = e[j];
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -520,8 +520,7 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
         if (lane == 0) {
             if (!DG) {
                 mbar_expect_tx(&wfull, (uint32_t)C::B_BYTES);
-                constexpr int NBLK = C::SW ? C::KB : C::KC;   // boxes per tap
-                constexpr int BCH = C::SW ? 64 : 8;             // channels per box
+                constexpr int NBLK = C::KB, BCH = C::BC;      // boxes per tap, channels per box
                 for (int tap = 0; tap < 9; ++tap)
                     for (int kc = 0; kc < NBLK; ++kc)
                         tma_load3(sB + tap * C::TAP_BYTES + kc * C::LBO_B, &tm_w, kc * BCH, n0, tap,
@@ -546,8 +545,7 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     const int yy = b * H + ys;
                     uint8_t *dst = sA + slot * C::ROW_BYTES;
                     mbar_expect_tx(&full[slot], C::ROW_TX);
-                    constexpr int NBLK = C::SW ? C::KB : C::KC;   // channel blocks
-                    constexpr int BCH = C::SW ? 64 : 8;             // channels per block
+                    constexpr int NBLK = C::KB, BCH = C::BC;      // channel blocks, channels per block
                     for (int kc = 0; kc < NBLK; ++kc) {
                         uint8_t *ch = dst + kc * C::LBO_A;
                         // x0-8 .. x0-1, x0 .. x0+127, x0+128 .. x0+135
@@ -573,7 +571,6 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
         bool ok = true;
         int nfreed[C::R];   // commits issued to each slot_free barrier
         for (int i = 0; i < R; ++i) nfreed[i] = 0;
-        const uint64_t bdesc0 = C::SW ? 0 : smem_desc(smem_u32(sB), C::LBO_B, 128);
         if (lane == 0) {
             if (!DG) ok = mbar_wait_ab(&wfull, 0, limit, abort);
             for (long u = u_begin; u < u_end && ok;) {
@@ -600,23 +597,16 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     for (int dy = 0; dy < 3; ++dy) {
                         const uint32_t abase =
                             smem_u32(sA + ((seq0 + tt + dy) % R) * C::ROW_BYTES) + C::COL0;
-                        const uint64_t arow = C::SW ? 0 : smem_desc(abase, C::LBO_A, 128);
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                             for (int j = 0; j < CIN / 16; ++j) {
-                                uint64_t ad, bd;
-                                if constexpr (C::SW) {
-                                    // K step j: block j / 4, 32 bytes per step within it
-                                    ad = smem_desc_sw128(abase + dx * 128 + (j >> 2) * C::LBO_A +
-                                                         (j & 3) * 32);
-                                    bd = smem_desc_sw128(smem_u32(sB) + (3 * dy + dx) * C::TAP_BYTES +
-                                                         (j >> 2) * C::LBO_B + (j & 3) * 32);
-                                } else {
-                                    ad = arow + (uint64_t)((dx * 16 + 2 * j * C::LBO_A) >> 4);
-                                    bd = bdesc0 + (uint64_t)(((3 * dy + dx) * C::TAP_BYTES +
-                                                              2 * j * C::LBO_B) >> 4);
-                                }
+                                // K step j: block j / KS, 32 bytes per step within it
+                                const uint64_t ad = smem_desc_sw<C::SP>(
+                                    abase + dx * C::SP + (j / C::KS) * C::LBO_A + (j % C::KS) * 32);
+                                const uint64_t bd = smem_desc_sw<C::SP>(
+                                    smem_u32(sB) + (3 * dy + dx) * C::TAP_BYTES +
+                                    (j / C::KS) * C::LBO_B + (j % C::KS) * 32);
                                 tc_mma(acc, ad, bd, IDESC, (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
                             }
                         }
@@ -732,23 +722,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tcp_encode_fn() {
 }
 
 // A BF16 tensor [d2][d1][d0] (d0 innermost) with a box of b0 x b1 x 1, copied
-// with the 128-byte swizzle when sw (then b0 = 64: 128-byte rows).
-bool tcp_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
-             uint32_t b1, bool sw = false) {
-    auto fn = tcp_encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[3] = {d0, d1, d2};
-    const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
-    const cuuint32_t box[3] = {b0, b1, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              sw ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// The same with the swizzle pattern of `span`-byte rows (32, 64 or 128; the
-// box's b0 channels make one row).
+// with the swizzle pattern of `span`-byte rows (32, 64 or 128: the box's b0
+// channels make one row).
 bool tcp_map_span(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                   uint32_t b0, uint32_t b1, int span) {
     auto fn = tcp_encode_fn();
@@ -779,12 +754,11 @@ cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(w)) & 15)
         return cudaErrorNotSupported;
     CUtensorMap mx, mxh, mw;
-    constexpr uint32_t BCH = C::SW ? 64 : 8;   // channels per box
-    if (!tcp_map(&mx, x, CIN, wd, (uint64_t)nb * h, BCH, 128, C::SW) ||
-        !tcp_map(&mxh, x, CIN, wd, (uint64_t)nb * h, BCH, 8, C::SW))
+    if (!tcp_map_span(&mx, x, CIN, wd, (uint64_t)nb * h, C::BC, 128, C::SP) ||
+        !tcp_map_span(&mxh, x, CIN, wd, (uint64_t)nb * h, C::BC, 8, C::SP))
         return cudaErrorNotSupported;
     if (!DG) {
-        if (!tcp_map(&mw, w, CIN, cout, 9, BCH, BN, C::SW)) return cudaErrorNotSupported;
+        if (!tcp_map_span(&mw, w, CIN, cout, 9, C::BC, BN, C::SP)) return cudaErrorNotSupported;
     } else {
         mw = mx;   // unused by the input gradient
     }
