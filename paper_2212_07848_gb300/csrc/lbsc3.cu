@@ -93,7 +93,9 @@ static_assert(norms_agree(), "moment norms");
 // FP32 uses 32 x 8 tiles (340 threads, 80 registers, two CTAs per SM) when
 // ny is a multiple of 8, else 32 x 4 (204 threads, four per SM); FP64 always
 // 32 x 4 (two per SM).  Measured at 256^3 FP32 on GB300: 32 x 8 30.1 GLUPS,
-// 32 x 4 28.9, 32 x 8 at three CTAs per SM (56 registers, spilling) 26.0;
+// 32 x 4 28.9, 32 x 8 at three CTAs per SM (56 registers, spilling) 26.0,
+// 32 x 16 (612 threads, 96 registers, one CTA per SM: a sixth fewer ring
+// pulls, but nothing issues while the CTA waits at its plane barrier) 27.8;
 // with the rows split across warps (the linear thread order) 32 x 4 ran at
 // 24.5.  Prefetching the next plane (into registers at three CTAs per SM, or
 // by cp.async into shared memory) measured slower: the step is bound by issue
