@@ -111,15 +111,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // (The same holds for rows of SP = 32 or 64 bytes, 16 or 32 BF16, with the
 // matching 32- or 64-byte pattern: 8-row groups 8 SP bytes apart, layout type
 // 6 or 4.)
+// Its low word: start address / 16 (bits 0-13) and the LBO field (unused for
+// swizzled K-major, 1); its high word: SBO = 8 rows (bits 32-45), version 1
+// (bit 46), layout type (bits 61-63).
+__device__ __forceinline__ uint32_t desc_sw_lo(uint32_t saddr) {
+    return ((saddr & 0x3FFFFu) >> 4) | (1u << 16);
+}
+template <int SP> __host__ __device__ constexpr uint32_t desc_sw_hi() {
+    static_assert(SP == 32 || SP == 64 || SP == 128, "swizzle span");
+    return ((8u * SP) >> 4) | (1u << 14) | ((uint32_t)(SP == 128 ? 2 : SP == 64 ? 4 : 6) << 29);
+}
 template <int SP>
 __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr) {
-    static_assert(SP == 32 || SP == 64 || SP == 128, "swizzle span");
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                        // LBO (unused for swizzled K-major)
-    d |= (uint64_t)((8u * SP) >> 4) << 32;         // SBO: 8 rows
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)(SP == 128 ? 2 : SP == 64 ? 4 : 6) << 61;
-    return d;
+    return ((uint64_t)desc_sw_hi<SP>() << 32) | desc_sw_lo(saddr);
 }
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.
@@ -151,6 +155,17 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// The same with each descriptor given as its two 32-bit words (low words
+// differing, high words shared).
+__device__ __forceinline__ void tc_mma_lo(uint32_t dtmem, uint32_t alo, uint32_t blo, uint32_t hi,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 ad, bd;\n setp.ne.b32 p, %5, 0;\n"
+        " mov.b64 ad, {%1, %3};\n mov.b64 bd, {%2, %3};\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %4, p;\n}\n" ::"r"(dtmem),
+        "r"(alo), "r"(blo), "r"(hi), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
@@ -567,12 +582,20 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
         __syncwarp();
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
-        long t = 0, seq0 = 0;
+        // One thread issues, and per MMA it adds one constant to each
+        // operand's descriptor: the start-address field of a swizzled K-major
+        // descriptor (bits 0-13, address / 16) cannot carry for shared
+        // addresses below 2^18, so the descriptor of addr + off (off a
+        // multiple of 16) is the one of addr with off / 16 added to its low
+        // word, and the high word is the same for every operand.
+        int t = 0, nfree = 0;   // output rows issued; input rows whose slot was released
         bool ok = true;
-        int nfreed[C::R];   // commits issued to each slot_free barrier
-        for (int i = 0; i < R; ++i) nfreed[i] = 0;
         if (lane == 0) {
+            constexpr uint32_t DHI = desc_sw_hi<C::SP>();
+            const uint32_t a_lo = desc_sw_lo(smem_u32(sA) + C::COL0);
+            const uint32_t b_lo = desc_sw_lo(smem_u32(sB));
             if (!DG) ok = mbar_wait_ab(&wfull, 0, limit, abort);
+            int seq0 = 0;
             for (long u = u_begin; u < u_end && ok;) {
                 int b, x0, row0, len;
                 run_at(u, b, x0, row0, len);
@@ -581,7 +604,7 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     // seq0 + tt .. seq0 + tt + 2 (the first two were waited for
                     // with the previous row, except at the start of a run)
                     for (int q = tt == 0 ? 0 : 2; q < 3 && ok; ++q) {
-                        const long sq = seq0 + tt + q;
+                        const int sq = seq0 + tt + q;
                         ok = mbar_wait_ab(&full[sq % R], (uint32_t)((sq / R) & 1), limit, abort);
                     }
                     if (ok && t >= 2)
@@ -590,42 +613,41 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t acc = tmem + (uint32_t)((t & 1) * BN);
-                    // descriptors of the row and tap bases; each MMA adds a
-                    // compile-time offset (in 16-byte units) to them, so the
-                    // issuing thread spends about one add per operand
+                    const int s0 = (seq0 + tt) % R;
+                    const int s1 = s0 + 1 == R ? 0 : s0 + 1;
+                    const int s2 = s1 + 1 == R ? 0 : s1 + 1;
+                    constexpr uint32_t kRow = (uint32_t)C::ROW_BYTES >> 4;
+                    const uint32_t arow[3] = {a_lo + (uint32_t)s0 * kRow, a_lo + (uint32_t)s1 * kRow,
+                                              a_lo + (uint32_t)s2 * kRow};
 #pragma unroll
                     for (int dy = 0; dy < 3; ++dy) {
-                        const uint32_t abase =
-                            smem_u32(sA + ((seq0 + tt + dy) % R) * C::ROW_BYTES) + C::COL0;
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                             for (int j = 0; j < CIN / 16; ++j) {
                                 // K step j: block j / KS, 32 bytes per step within it
-                                const uint64_t ad = smem_desc_sw<C::SP>(
-                                    abase + dx * C::SP + (j / C::KS) * C::LBO_A + (j % C::KS) * 32);
-                                const uint64_t bd = smem_desc_sw<C::SP>(
-                                    smem_u32(sB) + (3 * dy + dx) * C::TAP_BYTES +
-                                    (j / C::KS) * C::LBO_B + (j % C::KS) * 32);
-                                tc_mma(acc, ad, bd, IDESC, (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
+                                const uint32_t oa =
+                                    (uint32_t)(dx * C::SP + (j / C::KS) * C::LBO_A + (j % C::KS) * 32) >> 4;
+                                const uint32_t ob =
+                                    (uint32_t)((3 * dy + dx) * C::TAP_BYTES + (j / C::KS) * C::LBO_B +
+                                               (j % C::KS) * 32) >> 4;
+                                tc_mma_lo(acc, arow[dy] + oa, b_lo + ob, DHI, IDESC,
+                                          (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
                             }
                         }
                         if (dy == 0) {
                             // the row above is read by no later output row: hand
                             // its slot back as soon as these MMAs finish
-                            const int sl = (int)((seq0 + tt) % R);
-                            tc_commit(&slot_free[sl]);
-                            ++nfreed[sl];
+                            tc_commit(&slot_free[s0]);
+                            ++nfree;
                         }
                     }
                     tc_commit(&acc_full[t & 1]);
                     if (tt + 1 == len) {
                         // end of the run: its last two input rows are free too
-                        for (int q = 1; q < 3; ++q) {
-                            const int sl = (int)((seq0 + tt + q) % R);
-                            tc_commit(&slot_free[sl]);
-                            ++nfreed[sl];
-                        }
+                        tc_commit(&slot_free[s1]);
+                        tc_commit(&slot_free[s2]);
+                        nfree += 2;
                     }
                 }
                 seq0 += len + 2;
@@ -638,14 +660,15 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
             // drain: every MMA committed must finish before the accumulator
             // is freed, and every commit's arrival must land before the CTA
             // exits: wait (default bound) for the last phase of each barrier
-            // this thread committed to
+            // this thread committed to.  The slot releases went to input rows
+            // 0 .. nfree - 1 in order, so slot i took (nfree - 1 - i) / R + 1.
             bool drained = true;
-            for (long g = t > 2 ? t - 2 : 0; g < t; ++g)
+            for (int g = t > 2 ? t - 2 : 0; g < t; ++g)
                 drained = mbar_wait(&acc_full[g & 1], (uint32_t)((g >> 1) & 1), kTcWaitNs) && drained;
-            for (int i = 0; i < R; ++i)
-                if (nfreed[i] > 0)
-                    drained = mbar_wait(&slot_free[i], (uint32_t)((nfreed[i] - 1) & 1), kTcWaitNs) &&
-                              drained;
+            for (int i = 0; i < R && i < nfree; ++i) {
+                const int n = (nfree - 1 - i) / R + 1;
+                drained = mbar_wait(&slot_free[i], (uint32_t)((n - 1) & 1), kTcWaitNs) && drained;
+            }
             if (!drained) {
                 s_drained = 0;
                 atomicOr(&g_nn_status, 2);
@@ -702,6 +725,18 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
     tc_fence_before();
     __syncthreads();
     if (warp == 0 && s_drained) tmem_dealloc(tmem, C::NCOLS);
+}
+
+// Resident CTAs of kTcpThreads threads per SM: registers are allocated per
+// warp in units of 256 and each of the SM's four schedulers holds a quarter
+// of the register file and at most ceil(warps / 4) of a CTA's warps; every
+// CTA also takes its shared memory plus 1 KB reserved by the system.
+int tcp_slots_per_sm(int regs, int smem_cta, int smem_sm, int regs_sm, int tmem_slots) {
+    const int warps = kTcpThreads / 32;
+    const int warp_regs = (regs * 32 + 255) / 256 * 256;
+    const int by_regs = (regs_sm / 4) / (warp_regs * ((warps + 3) / 4));
+    const int by_smem = smem_sm / (smem_cta + 1024);
+    return std::max(1, std::min(tmem_slots, std::min(by_regs, by_smem)));
 }
 
 // Tensor maps of the persistent convolution (cuTensorMapEncodeTiled through
@@ -762,26 +797,33 @@ cudaError_t launch_tcp(const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
     } else {
         mw = mx;   // unused by the input gradient
     }
-    // CTAs resident per SM (shared memory, registers and the padding above):
-    // a narrow layer's output rows are short chains of copies, MMAs and a
-    // read-out whose latency one CTA per SM cannot hide, so the grid fills
-    // every resident slot
+    // CTAs resident per SM: a narrow layer's output rows are short chains of
+    // copies, MMAs and a read-out whose latency one CTA per SM cannot hide, so
+    // the grid fills every resident slot.  The slots are counted here from the
+    // kernel's registers and shared memory (and the tensor-memory padding
+    // above) because the runtime's occupancy query answered one CTA per SM for
+    // plans of which two were measured resident together on GB300 (47 and
+    // 110 KB of shared memory, about 100 registers).
     static int nsm = 0, per_sm = 1;
     if (!nsm) {
-        int dev = 0;
+        int dev = 0, smem_sm = 0, regs_sm = 0;
+        cudaFuncAttributes fa;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(conv3x3_tcp_kernel<BN, CIN, DG>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, conv3x3_tcp_kernel<BN, CIN, DG>, kTcpThreads, kSmem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv3x3_tcp_kernel<BN, CIN, DG>);
         if (e != cudaSuccess) {
             nsm = 0;
             return e;
         }
-        per_sm = std::max(1, std::min(per_sm, kPerSm));
+        per_sm = tcp_slots_per_sm(fa.numRegs, (int)fa.sharedSizeBytes + kSmem, smem_sm, regs_sm,
+                                  kPerSm);
     }
     const int nblk = cout / BN;
     const long units = (long)nb * h * (wd / 128);
