@@ -159,13 +159,13 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
 }
 // The same with each descriptor given as its two 32-bit words (low words
 // differing, high words shared).
-__device__ __forceinline__ void tc_mma_lo(uint32_t dtmem, uint32_t alo, uint32_t blo, uint32_t hi,
-                                          uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma_lo(uint32_t dtmem, uint32_t alo, uint32_t ahi, uint32_t blo,
+                                          uint32_t bhi, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
-        "{\n .reg .pred p;\n .reg .b64 ad, bd;\n setp.ne.b32 p, %5, 0;\n"
-        " mov.b64 ad, {%1, %3};\n mov.b64 bd, {%2, %3};\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %4, p;\n}\n" ::"r"(dtmem),
-        "r"(alo), "r"(blo), "r"(hi), "r"(idesc), "r"(accumulate)
+        "{\n .reg .pred p;\n .reg .b64 ad, bd;\n setp.ne.b32 p, %6, 0;\n"
+        " mov.b64 ad, {%1, %2};\n mov.b64 bd, {%3, %4};\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n}\n" ::"r"(dtmem),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
@@ -631,7 +631,7 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
                                 const uint32_t ob =
                                     (uint32_t)((3 * dy + dx) * C::TAP_BYTES + (j / C::KS) * C::LBO_B +
                                                (j % C::KS) * 32) >> 4;
-                                tc_mma_lo(acc, arow[dy] + oa, b_lo + ob, DHI, IDESC,
+                                tc_mma_lo(acc, arow[dy] + oa, DHI, b_lo + ob, DHI, IDESC,
                                           (dy > 0 || dx > 0 || j > 0) ? 1u : 0u);
                             }
                         }
@@ -943,16 +943,13 @@ constexpr int kWgtThreads = 192;
 // apart (SBO), layout type 6 / 4 / 2 for 32 / 64 / 128 bytes; starting at
 // pixel row `row`.  As for the K-major operands, the swizzle follows the
 // absolute shared-memory address, so any start row works with the base
-// offset field at 0.
+// offset field at 0.  The high word is desc_sw_hi<SP>(); the low word at row
+// 0 is mn_desc_lo, and starting `row` rows further adds row SP / 16 to it
+// (the start-address field cannot carry for shared addresses below 2^18).
 template <int SP>
-__device__ __forceinline__ uint64_t mn_desc(uint32_t base, int row, int rows) {
+__device__ __forceinline__ uint32_t mn_desc_lo(uint32_t base, int rows) {
     static_assert(SP == 32 || SP == 64 || SP == 128, "swizzle span");
-    uint64_t d = (uint64_t)(((base + (uint32_t)(row * SP)) & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((((uint32_t)(rows * SP)) >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((8u * SP) >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)(SP == 128 ? 2 : SP == 64 ? 4 : 6) << 61;
-    return d;
+    return ((base & 0x3FFFFu) >> 4) | ((((uint32_t)(rows * SP) >> 4) & 0x3FFFu) << 16);
 }
 
 // tm_x / tm_xh: x as [nb*H][W][Cin], boxes of XB channels x 128 / 8 pixels;
@@ -1052,33 +1049,41 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant_
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            int nfreed[S];
-            for (int i = 0; i < S; ++i) nfreed[i] = 0;
+            // descriptor low words built once per tile, a constant added per MMA
+            constexpr uint32_t DHI = desc_sw_hi<C::DSP>(), XHI = desc_sw_hi<C::XSP>();
+            constexpr int NQ = TP == 9 ? 3 : 1;
+            int ncommit = 0;   // tiles whose slot release was committed (in order)
             bool ok = true;
             for (int t = 0; t < n && ok; ++t) {
                 const int slot = t % S;
                 ok = mbar_wait_ab(&full[slot], (uint32_t)((t / S) & 1), limit, abort);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t db = smem_u32(dreg(slot));
+                const uint32_t d_lo = mn_desc_lo<C::DSP>(smem_u32(dreg(slot)), C::DROW);
+                uint32_t x_lo[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) x_lo[q] = mn_desc_lo<C::XSP>(smem_u32(xreg(slot, q)), C::XROW);
                 // K steps outer, taps inner: consecutive MMAs go to different
                 // accumulators, so none waits for the one before it
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const uint64_t dd = mn_desc<C::DSP>(db, 16 * j, C::DROW);
+                    const uint32_t dd = d_lo + (uint32_t)((16 * j * C::DSP) >> 4);
 #pragma unroll
                     for (int tl = 0; tl < TP; ++tl) {
                         // pixels 16j .. 16j+15 of the tile; x shifted by the tap
                         // (staged row 8 is pixel x0, so the tap's row 7 + dx + p)
                         const int q = TP == 9 ? tl / 3 : 0, dx = tl % 3;
-                        const uint64_t xd =
-                            mn_desc<C::XSP>(smem_u32(xreg(slot, q)), 7 + dx + 16 * j, C::XROW);
-                        tc_mma(tmem + (uint32_t)(tl * NC), AX ? xd : dd, AX ? dd : xd, IDESC,
-                               (t > 0 || j > 0) ? 1u : 0u);
+                        const uint32_t xd = x_lo[q] + (uint32_t)(((7 + dx + 16 * j) * C::XSP) >> 4);
+                        if constexpr (AX)
+                            tc_mma_lo(tmem + (uint32_t)(tl * NC), xd, XHI, dd, DHI, IDESC,
+                                      (t > 0 || j > 0) ? 1u : 0u);
+                        else
+                            tc_mma_lo(tmem + (uint32_t)(tl * NC), dd, DHI, xd, XHI, IDESC,
+                                      (t > 0 || j > 0) ? 1u : 0u);
                     }
                 }
                 tc_commit(&slot_free[slot]);
-                ++nfreed[slot];
+                ++ncommit;
             }
             if (!ok) {
                 *abort = 1;
@@ -1087,12 +1092,13 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant_
             // done: every MMA issued has finished (also after an abort, so that
             // tensor memory is freed only then); wait for it and for the last
             // arrival on each slot barrier before the CTA may exit
+            // (slot i took (ncommit - 1 - i) / S + 1 of the slot releases)
             tc_commit(&done);
             bool drained = mbar_wait(&done, 0, kTcWaitNs);
-            for (int i = 0; i < S; ++i)
-                if (nfreed[i] > 0)
-                    drained = mbar_wait(&slot_free[i], (uint32_t)((nfreed[i] - 1) & 1), kTcWaitNs) &&
-                              drained;
+            for (int i = 0; i < S && i < ncommit; ++i) {
+                const int k = (ncommit - 1 - i) / S + 1;
+                drained = mbar_wait(&slot_free[i], (uint32_t)((k - 1) & 1), kTcWaitNs) && drained;
+            }
             if (!drained) {
                 s_drained = 0;
                 atomicOr(&g_nn_status, 2);
