@@ -728,13 +728,17 @@ conv3x3_tcp_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_consta
 }
 
 // Resident CTAs of kTcpThreads threads per SM: registers are allocated per
-// warp in units of 256 and each of the SM's four schedulers holds a quarter
-// of the register file and at most ceil(warps / 4) of a CTA's warps; every
-// CTA also takes its shared memory plus 1 KB reserved by the system.
+// warp in units of 256, and the warps of B resident CTAs are spread over the
+// SM's four schedulers, each holding a quarter of the register file, so B
+// fits while ceil(B warps / 4) warps' registers fit a quarter; every CTA also
+// takes its shared memory plus 1 KB reserved by the system.  (This reproduces
+// the limits the profiler reports for this kernel and for the ensemble's
+// persistent kernel.)
 int tcp_slots_per_sm(int regs, int smem_cta, int smem_sm, int regs_sm, int tmem_slots) {
     const int warps = kTcpThreads / 32;
     const int warp_regs = (regs * 32 + 255) / 256 * 256;
-    const int by_regs = (regs_sm / 4) / (warp_regs * ((warps + 3) / 4));
+    int by_regs = 0;
+    while ((((by_regs + 1) * warps + 3) / 4) * warp_regs <= regs_sm / 4) ++by_regs;
     const int by_smem = smem_sm / (smem_cta + 1024);
     return std::max(1, std::min(tmem_slots, std::min(by_regs, by_smem)));
 }
